@@ -1,0 +1,65 @@
+"""Plant plausible mistakes in copies of the oracle source and check that the
+pins catch every one of them (CPU only).
+
+Each mutation edits one expression of ``oracle/u1u1_oracle.c`` (a sign, a
+factor, an index, a dropped term), the copy is compiled with gcc, and the
+pins of ``pins.py`` run against it; at least one must fail.
+"""
+import os
+
+import pytest
+
+import oracle as O
+import pins
+
+MUTATIONS = [
+    # name, original text, replacement
+    ("current_sign", "(-curl + 2.0 * e2 * c * J)", "(-curl - 2.0 * e2 * c * J)"),
+    ("current_factor", "(-curl + 2.0 * e2 * c * J)", "(-curl + e2 * c * J)"),
+    ("curl_sign", "(-curl + 2.0 * e2 * c * J)", "(curl + 2.0 * e2 * c * J)"),
+    ("backward_link_not_conjugated", "cmul(cconj(link_U(p, st, s, i, xm)), get_phi(p, st, s, xm))",
+     "cmul(link_U(p, st, s, i, xm), get_phi(p, st, s, xm))"),
+    ("kappa_sign", "0.5 * p->lambda[s] * r_self - p->kappa * r_other",
+     "0.5 * p->lambda[s] * r_self + p->kappa * r_other"),
+    ("lambda_half", "0.5 * p->lambda[s] * r_self - p->kappa * r_other",
+     "p->lambda[s] * r_self - p->kappa * r_other"),
+    ("scalar_damping_sign", "((1.0 - delta) * pr + p->deta", "((1.0 + delta) * pr + p->deta"),
+    ("omega_definition", "double omega = delta * (1.0 - p->beta);", "double omega = delta * p->beta;"),
+    ("coupling_exponent", "double c = pow(a, 2.0 * p->beta);", "double c = pow(a, p->beta);"),
+    ("delta_factor", "double delta = 0.5 * p->alpha * pm", "double delta = p->alpha * pm"),
+    ("link_convention", "cplx r = {cos(th), -sin(th)};", "cplx r = {cos(th), sin(th)};"),
+    ("plaquette_index", "return (get_A(p, st, s, j, xi) - get_A(p, st, s, j, site)",
+     "return (get_A(p, st, s, i, xi) - get_A(p, st, s, j, site)"),
+    ("curl_neighbour", "long xmj = shift(p, site, j, -1);", "long xmj = shift(p, site, i, -1);"),
+    ("link_drift_sign", "st[f_A(s, i) * V + site] += p->deta * v;", "st[f_A(s, i) * V + site] -= p->deta * v;"),
+    ("winding_orientation", "- edge_chi(p, st, s, i, xj, &cut) - edge_chi(p, st, s, j, site, &cut);",
+     "+ edge_chi(p, st, s, i, xj, &cut) - edge_chi(p, st, s, j, site, &cut);"),
+    ("winding_without_links", "tot += p->dx * (get_A(p, st, s, i, site)", "tot += 0.0 * (get_A(p, st, s, i, site)"),
+    ("cell_wrong_face", "abs(w[0 * V + site]) + abs(w[0 * V + zp])", "abs(w[0 * V + site]) + abs(w[0 * V + site])"),
+    ("overlap_one_sided", "for (int dz = -tol; dz <= tol && !hit; ++dz)", "for (int dz = 0; dz <= tol && !hit; ++dz)"),
+    ("kinetic_not_averaged", "kin[s] = 0.5 * (pm2 + pp2);", "kin[s] = pp2;"),
+    ("magnetic_factor", "mag[s] = g * f2;", "mag[s] = 0.5 * g * f2;"),
+    ("lagrangian_potential_sign", "+ (kin[1] - grad[1] + el[1] - mag[1]) - pot;",
+     "+ (kin[1] - grad[1] + el[1] - mag[1]) + pot;"),
+    ("gradient_difference", "cplx d = {(fwd.re - f.re) / p->dx, (fwd.im - f.im) / p->dx};",
+     "cplx d = {(fwd.re + f.re) / p->dx, (fwd.im + f.im) / p->dx};"),
+    ("gauss_charge_factor", "double ct_prev = have_prev ? cfm[5] : 0.0;", "double ct_prev = have_prev ? cfm[2] : 0.0;"),
+    ("ic_phase_range", "double th = (2.0 * M_PI) * u;", "double th = M_PI * u;"),
+    ("electric_energy_factor", "e2sum += 0.5 * (em * em + ep * ep);", "e2sum += (em * em + ep * ep);"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutation_is_caught(name, old, new, tmp_path):
+    src = O.source()
+    assert src.count(old) == 1, f"mutation anchor for {name} must occur exactly once"
+    lib = O.compile_variant(src.replace(old, new), os.path.join(str(tmp_path), f"lib_{name}.so"))
+    caught = []
+    with O.use_library(lib):
+        for pin in pins.ALL_PINS:
+            try:
+                pin()
+            except Exception as exc:  # noqa: BLE001 - any failure counts as detection
+                caught.append((pin.__name__, type(exc).__name__))
+                break
+    assert caught, f"mutation {name} passed every pin"
