@@ -1,0 +1,343 @@
+"""Benchmark of the U(1)xU(1) hot path: site-updates/s and HBM roofline.
+
+Workload (default): the 1024^3 single-GPU machine of the paper's model in the
+radiation era, dx = 0.5, deta = 0.1, beta = 1, lambda = 2, e = 1, sigma = 1,
+kappa = 0.9, seeded random-phase initial conditions, FP32 bulk, winding
+detection every 16 steps.  One benchmark "step" is one detection period: 16
+leapfrog steps, the first fused with plaquette-winding detection and the
+diagnostic sums, followed by the cell-overlap pass and the reduction
+finalize (every row of the hot path).  value = site-updates/s over the timed
+periods (one site-update advances all 20 real fields of both sectors by one
+deta); inputs (86 GB) are far larger than L2, so no flush is needed.
+
+Also reported: the step kernel's roofline (algorithmic 160 B/site over its
+CUDA-event time against the measured HBM copy bandwidth), an end-to-end
+number through the public API with host buffers (state uploaded from pinned
+memory, per-period record reads, state downloaded), the FP64 step, and the
+FP64 CPU oracle on a bounded sample of the same workload (cpu_baseline).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s & % HBM roofline, FP32 vs FP64, U(1)xU(1) step at 1024^3"
+BYTES_PER_SITE = {"fp32": 160, "fp64": 320}  # read 20 + write 20 words
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def workload_params(U, n, precision, beta=1.0, seed=2024):
+    # 2560 steps to eta = 257 for the 1024^3 box; a = 1 at the end of the run
+    return U.Params.cube(n, m=0.5, beta=beta, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=seed,
+                         precision=precision)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f if ln.strip()]
+        os.unlink(self.f.name)
+        mine = [r for r in rows if self.uuid is None or self.uuid in r[0]] or rows
+        sm = [float(r[1].split()[0]) for r in mine if len(r) > 2 and r[1].split()[0].replace(".", "").isdigit()]
+        mx = [float(r[2].split()[0]) for r in mine if len(r) > 2 and r[2].split()[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in mine:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n=128, nsteps=16, detect=True):
+    """The FP64 oracle, as it stands, on all host cores: one detection period
+    (16 leapfrog steps plus windings, cells, overlap and diagnostics) on an
+    n^3 box of the same model.  Returns (site-updates/s, seconds, cores)."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    p = O.Params(n, n, n, m=0.5, beta=1.0, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=2024)
+    st = O.init(p)
+    t0 = time.perf_counter()
+    if detect:
+        O.strings(p, st, tol=1)
+        O.diagnostics(p, st, 0)
+    O.step(p, st, 0, nsteps)
+    dt = time.perf_counter() - t0
+    return nsteps * n ** 3 / dt, dt, O.max_threads()
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on the host cores, each
+    step one detection period on a 96^3 sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    n = args.ref_n
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    p = O.Params(n, n, n, m=0.5, beta=1.0, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=2024)
+    st = O.init(p)
+    step_n = 0
+
+    def one_period():
+        nonlocal step_n
+        O.strings(p, st, tol=1)
+        O.diagnostics(p, st, step_n)
+        O.step(p, st, step_n, args.detect_every)
+        step_n += args.detect_every
+
+    for _ in range(args.warmup):
+        one_period()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_period()
+    dt = time.perf_counter() - t0
+    value = args.steps * args.detect_every * n ** 3 / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"U(1)xU(1) leapfrog + detection every {args.detect_every} steps, radiation, "
+                               f"beta=1, {n}^3 sample of the 1024^3 box (CPU oracle)",
+                   "lattice": n, "detect_every": args.detect_every},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": O.max_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} detection periods of {args.detect_every} steps on {n}^3"},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2208_01525_gb300 as U
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n = args.n
+    prec = U.FP64 if args.precision == "fp64" else U.FP32
+    tag = "fp64" if prec == U.FP64 else "fp32"
+    # independent realisations per rank (replicas: the path has no exchange step)
+    p = workload_params(U, n, prec, seed=2024 + rank)
+    lat = U.Lattice(p, device=dev, kernel=args.kernel)
+    de = args.detect_every
+    V = p.nsites
+    stream = torch.cuda.current_stream()
+
+    # warm-up periods
+    for _ in range(args.warmup):
+        lat.step(de, detect_every=de)
+    torch.cuda.synchronize()
+    lat.read_records()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "")) or None
+    sampler = ClockSampler(uuid)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        lat.step(1, detect_every=de)          # fused step + detection, overlap, finalize
+        ev[k][1].record(stream)
+        lat.step(de - 1, detect_every=de)     # plain fused kick-drift steps
+        ev[k][2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    recs, lost = lat.read_records()
+    plain_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / (args.steps * (de - 1))
+    det_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    site_updates = args.steps * de * V * world
+    value = site_updates / (ms * 1e-3)
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_SITE[tag] * V / (plain_ms * 1e-3) / 1e9
+    last = recs[-1] if recs else None
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if args.e2e:
+        host = [torch.empty(V, dtype=lat.dtype, pin_memory=True) for _ in range(20)]
+        lat.download(host)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        lat.upload(host)
+        for _ in range(args.steps):
+            lat.step(de, detect_every=de)
+            lat.read_records()                # D2H of the period's record + host epilogue
+        lat.download(host)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        state_bytes = 20 * V * lat.dtype.itemsize
+        rec_bytes = 312  # one detection record copied per period
+        e2e = {"value": site_updates / e2e_s, "unit": "site-updates/s",
+               "h2d_bytes_per_step": state_bytes / args.steps,
+               "d2h_bytes_per_step": state_bytes / args.steps + rec_bytes,
+               "what": "upload state from pinned host, K periods each followed by a record read, "
+                       "download state"}
+        del host
+
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    # FP64 step throughput (same box when it fits)
+    fp64 = None
+    if args.fp64_n > 0 and prec == U.FP32:
+        n64 = args.fp64_n
+        p64 = workload_params(U, n64, U.FP64, seed=2024 + rank)
+        need = 30 * p64.nsites * 8 * 1.05
+        if torch.cuda.mem_get_info(dev)[0] > need:
+            lat64 = U.Lattice(p64, device=dev, kernel=args.kernel)
+            lat64.step(2)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lat64.step(args.fp64_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64 = a.elapsed_time(b) / args.fp64_steps
+            fp64 = {"lattice": n64, "value": p64.nsites / (t64 * 1e-3), "unit": "site-updates/s",
+                    "ms_per_step": t64,
+                    "hbm_frac": BYTES_PER_SITE["fp64"] * p64.nsites / (t64 * 1e-3) / 1e9 / peak,
+                    "steps": args.fp64_steps}
+            lat64.close()
+            del lat64
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and args.cpu:
+        v, dt, cores = cpu_baseline(args.cpu_n)
+        cpu = {"value": v, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"one detection period (16 steps + windings, overlap, diagnostics) on "
+                         f"{args.cpu_n}^3, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if tag == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"U(1)xU(1) {n}^3 leapfrog, radiation era, beta=1, detection every {de} "
+                                   f"steps (one step = {de} leapfrog steps)",
+                       "lattice": n, "dx": 0.5, "deta": 0.1, "detect_every": de,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "leapfrog step", "bytes_per_site": BYTES_PER_SITE[tag],
+                         "ms_per_launch": plain_ms},
+            "detect_ms_per_period": det_ms,
+            "clocks": clocks,
+            "gpu_launches": args.steps * (de + 2),
+            "e2e": e2e,
+            "fp64": fp64,
+            "cpu_baseline": cpu,
+            "records_lost": lost,
+            "last_record": None if last is None else {
+                "n": last[0]["n"], "xi_w": last[0]["xi_w"], "f_total": last[0]["f_total"],
+                "xi_l": last[1]["xi_l"], "v2_l": last[1]["v2_l"]},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--detect-every", type=int, default=16)
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--fp64-n", type=int, default=1024)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--ref-n", type=int, default=96)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

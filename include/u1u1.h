@@ -1,0 +1,273 @@
+/*
+ * u1u1.h -- C ABI of libu1u1, a single-GPU (sm_103a) implementation of the
+ * lattice time step and string diagnostics of the U(1)xU(1) model of
+ * Correia & Martins, "Multitension strings in high-resolution U(1)xU(1)
+ * simulations" (arXiv:2208.01525).
+ *
+ * Model (Sec. II): two complex scalars phi (sector p) and psi (sector q),
+ * each with its own U(1) gauge field, A for p and B for q, coupled only
+ * through the potential of Eq. 4,
+ *   V = lambda_p/4 (|phi|^2 - sigma_p^2)^2 + lambda_q/4 (|psi|^2 - sigma_q^2)^2
+ *       - kappa (|phi|^2 - sigma_p^2)(|psi|^2 - sigma_q^2).
+ * Background (Sec. III): comoving periodic lattice, temporal gauge, power-law
+ * FLRW expansion a ~ t^m, couplings scaled as lambda, kappa ~ a^{-2(1-beta)}
+ * and e ~ a^{-(1-beta)} (Eq. 12).  Time step: the damped leapfrog of
+ * Eqs. 17-26 (scalar kick, gauge kick, drift).
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - link variable U_i(x) = exp(-i dx A_i(x)); the gauge coupling is
+ *     absorbed into A, so e^2 appears only in the current of Eq. 20 and in
+ *     the 1/(2 e^2) gauge energy;
+ *   - F_ij(x) = (A_j(x+i) - A_j(x) - A_i(x+j) + A_i(x)) / dx and the curl
+ *     term of Eq. 20 is -sum_{j != i} (F_ij(x) - F_ij(x-j)) / dx;
+ *   - a(eta) = (eta / eta_ref)^{m/(1-m)}, c_n = a_n^{2 beta},
+ *     delta_n = (alpha/2) m/(1-m) deta/eta_n (Eq. 19), omega_n = delta_n (1-beta)
+ *     (Eq. 22), eta_n = eta0 + n deta.
+ *
+ * Data layout.  A lattice of nx*ny*nz sites; every field is a separate
+ * contiguous array of nx*ny*nz elements of the lattice precision (float or
+ * double), site (x, y, z) at index x + nx*(y + ny*z).  Twenty fields make the
+ * state: ten "position" fields at integer time n and ten momenta at n-1/2,
+ * in the order of the U1U1_POS_* and U1U1_MOM_* constants below.  Position
+ * fields are double-buffered (ping-pong): a step reads buffer `current` and
+ * writes buffer `1 - current`; momenta are updated in place.
+ *
+ * Ownership.  The caller allocates and owns every field array (device
+ * memory; 256-byte aligned base addresses) and must keep them alive, and not
+ * write them, while a lattice handle uses them.  The handle owns only
+ * metadata and its scratch memory (2 bytes per site for plaquette-winding
+ * bytes plus small reduction buffers), released by u1u1_destroy.
+ *
+ * Errors.  Every int-returning call returns U1U1_OK (0) or a negative
+ * U1U1_ERR_* code and never throws; u1u1_last_error() returns a message for
+ * the calling thread's last failure.  A CUDA failure is reported as
+ * U1U1_ERR_CUDA with the CUDA error string in the message.
+ *
+ * Streams.  `stream` arguments are cudaStream_t values passed as void*
+ * (NULL = the legacy default stream).  Calls that only enqueue work return
+ * before it runs; calls that fill host structs synchronise that stream.
+ */
+#ifndef U1U1_H
+#define U1U1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define U1U1_OK 0
+#define U1U1_ERR_INVALID_ARG (-1)   /* a parameter is out of its documented range */
+#define U1U1_ERR_BAD_BUFFER (-2)    /* NULL or misaligned field array, or size mismatch */
+#define U1U1_ERR_OUT_OF_MEMORY (-3) /* scratch allocation failed */
+#define U1U1_ERR_CUDA (-4)          /* a CUDA runtime call or kernel launch failed */
+#define U1U1_ERR_TIMEOUT (-5)       /* a bounded device-side wait ran out */
+#define U1U1_ERR_NAN (-6)           /* a diagnostic pass found NaN in the state */
+#define U1U1_ERR_NOT_SUPPORTED (-7) /* request valid but not implemented for this configuration */
+#define U1U1_ERR_STATE (-8)         /* call not valid in the handle's current state */
+#define U1U1_ERR_IO (-9)            /* file could not be read or written */
+
+/* ---- precision --------------------------------------------------------- */
+#define U1U1_FP32 0 /* float fields, FP32 arithmetic, compensated FP64 global sums */
+#define U1U1_FP64 1 /* double fields and arithmetic throughout */
+
+/* ---- field order ------------------------------------------------------- */
+enum {
+  U1U1_POS_PHI_RE = 0, U1U1_POS_PHI_IM, U1U1_POS_PSI_RE, U1U1_POS_PSI_IM,
+  U1U1_POS_A0, U1U1_POS_A1, U1U1_POS_A2, U1U1_POS_B0, U1U1_POS_B1, U1U1_POS_B2,
+  U1U1_NPOS
+};
+enum {
+  U1U1_MOM_PI_RE = 0, U1U1_MOM_PI_IM, U1U1_MOM_PSI_RE, U1U1_MOM_PSI_IM,
+  U1U1_MOM_E0, U1U1_MOM_E1, U1U1_MOM_E2, U1U1_MOM_H0, U1U1_MOM_H1, U1U1_MOM_H2,
+  U1U1_NMOM
+};
+#define U1U1_NFIELDS (U1U1_NPOS + U1U1_NMOM)
+
+/* ---- parameters (names follow the paper's symbols) ---------------------- */
+typedef struct {
+  int nx, ny, nz;       /* lattice sides; nx % 4 == 0; each >= 4 */
+  double dx;            /* comoving lattice spacing Delta x (> 0) */
+  double deta;          /* conformal time step Delta eta (> 0) */
+  double eta0;          /* conformal time of step 0 (> 0 when m != 0) */
+  double m;             /* a ~ t^m: 0 flat (a = 1), 1/2 radiation, 2/3 matter; 0 <= m < 1 */
+  double eta_ref;       /* a(eta_ref) = 1 (> 0) */
+  double beta;          /* Eq. 12: 1 physical, 0 constant comoving width, < 0 core growth */
+  double alpha;         /* Hubble damping factor of Eq. 19 (the paper uses 2) */
+  double lambda_p, lambda_q; /* lambda_0 per sector */
+  double e_p, e_q;      /* e_0 per sector (> 0) */
+  double sigma_p, sigma_q;   /* vacuum expectation values */
+  double kappa;         /* kappa_0 of Eq. 4 */
+  uint64_t seed;        /* random-phase initial conditions */
+  int precision;        /* U1U1_FP32 or U1U1_FP64 */
+} u1u1_params;
+
+/* Caller-owned device field arrays (see "Data layout"). */
+typedef struct {
+  void* pos[2][U1U1_NPOS]; /* ping-pong position buffers */
+  void* mom[U1U1_NMOM];    /* momenta, updated in place */
+} u1u1_buffers;
+
+/* Result of the fast string detection (Sec. III.A-B). */
+typedef struct {
+  int64_t n;            /* step index of the detected state */
+  double eta;           /* its conformal time */
+  int64_t n_p, n_q;     /* sum over plaquettes of |W| per sector */
+  int64_t nonzero_p, nonzero_q; /* plaquettes with W != 0 per sector */
+  int64_t n_pq_plaq;    /* plaquettes with W_p != 0 and W_q != 0 (exact overlap) */
+  int64_t n_pq_cell;    /* p-pierced cells with a q-pierced cell within overlap_tol */
+  int64_t n_pq_cell_q;  /* the same anchored on q-pierced cells (symmetry check) */
+  int64_t n_flagged;    /* plaquette windings within 1e-4 of the +-pi branch cut */
+  int32_t max_abs_w;    /* largest |W| seen */
+  int32_t overlap_tol;  /* cell displacement allowed by the overlap (0 or 1) */
+  double L_p, L_q, L_pq;      /* dx * counts, L_s with L_pq subtracted */
+  double xi_p, xi_q, xi_pq;   /* Eq. 31; +inf when the length is 0 */
+  double xi_w;                /* Eq. 32 */
+  double f_total, f_p;        /* Eqs. 34-35; NaN when undefined */
+} u1u1_strings;
+
+/* Network diagnostics of Sec. III.A on the state at integer time n.  The
+ * momenta enter as the mean of their squares at n-1/2 and n+1/2. */
+typedef struct {
+  int64_t n;
+  double eta, a;
+  double kin_p, kin_q, grad_p, grad_q, el_p, el_q, mag_p, mag_q; /* lattice sums */
+  double pot, vint;     /* sum c_n V and sum kappa(|phi|^2-sigma_p^2)(|psi|^2-sigma_q^2) */
+  double lag, energy;   /* sum of the Lagrangian and of the energy density */
+  double rl_num, rl_den, rpq_num, rpq_den; /* Eq. 37 sums, W = L and W = V_int */
+  double lag_total, energy_total; /* the sums times dx^3 */
+  double xi_l;          /* Eq. 33 with mu = 2 pi sigma_p^2 */
+  double R_l, v2_l, R_pq, v2_pq; /* Eqs. 36-37 */
+  int32_t has_gauss;    /* 1 when the Gauss fields below were computed */
+  double gauss_sum_p, gauss_sum_q, charge_sum_p, charge_sum_q;
+  double gauss_max_p, gauss_max_q, gauss_rel_p, gauss_rel_q; /* rel = sum|G| / sum|rho| */
+  double phi_min_p, phi_max_p, phi_min_q, phi_max_q;
+  int64_t nan_count;    /* NaN entries among the 20 fields */
+} u1u1_diag;
+
+typedef struct u1u1_lattice u1u1_lattice;
+typedef struct u1u1_ensemble u1u1_ensemble;
+
+/* ---- library information ------------------------------------------------ */
+
+/* Version string "major.minor.patch"; static storage. */
+const char* u1u1_version(void);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* u1u1_last_error(void);
+
+/* ---- host-only helpers (no GPU needed) ---------------------------------- */
+
+/* Fill *p with the paper's equal-tension values (Sec. IV): lambda = 2,
+ * e = 1, sigma = 1, kappa = 0.9, alpha = 2, dx = 0.5, deta = 0.1,
+ * radiation era (m = 1/2), beta = 1, eta0 = 1, eta_ref = 1, 64^3, FP32. */
+int u1u1_params_default(u1u1_params* p);
+
+/* Validate *p; U1U1_ERR_INVALID_ARG with a message naming the field. */
+int u1u1_check_params(const u1u1_params* p);
+
+/* Step coefficients of step n (Eqs. 12, 19, 22): out[0] = eta_n, out[1] = a_n,
+ * out[2] = c_n = a_n^{2 beta}, out[3] = delta_n, out[4] = omega_n,
+ * out[5] = c_n (1 + delta_n)/(1 + omega_n) (Gauss-law charge factor). */
+int u1u1_coefficients(const u1u1_params* p, int64_t n, double out[6]);
+
+/* Bytes of one field array for *p (nx*ny*nz times the element size);
+ * 0 for a NULL or empty lattice. */
+size_t u1u1_field_bytes(const u1u1_params* p);
+
+/* sizeof of the public structs, for bindings to check their mirrors:
+ * out[0] u1u1_params, out[1] u1u1_buffers, out[2] u1u1_strings,
+ * out[3] u1u1_diag. */
+void u1u1_abi_sizes(size_t out[4]);
+
+/* ---- single lattice ----------------------------------------------------- */
+
+/* Create a handle over caller buffers *b and enqueue the random-phase
+ * initial conditions of Sec. III on `stream`: phi_s = sigma_s e^{i theta},
+ * theta = 2 pi u, u the top 53 bits (times 2^-53) of draw number `site` of
+ * the SplitMix64 generator (Steele, Lea & Flood 2014) whose state starts at
+ * seed ^ (s << 62) (s = 0 for p, 1 for q); every other field zero, in both
+ * position buffers.  The state is then at step n = 0 in buffer 0.
+ * Errors: INVALID_ARG, BAD_BUFFER, OUT_OF_MEMORY, CUDA. */
+int u1u1_init_lattice(const u1u1_params* p, const u1u1_buffers* b, void* stream,
+                      u1u1_lattice** out);
+
+/* Create a handle over buffers that already hold a state at step n in
+ * position buffer `current` (0 or 1).  Enqueues nothing. */
+int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, int64_t n, int current,
+                        u1u1_lattice** out);
+
+/* Release the handle and its scratch (not the caller's buffers). */
+void u1u1_destroy(u1u1_lattice* h);
+
+/* Current step index and position buffer of the handle's state. */
+int u1u1_current(const u1u1_lattice* h, int64_t* n, int* current);
+
+/* Enqueue nsteps (>= 0) leapfrog steps (Eqs. 17-26).  Each step whose input
+ * index n satisfies detect_every > 0 and n % detect_every == 0 is fused with
+ * the detection of that input state: plaquette windings of both sectors
+ * (Sec. III.A), the fast cell overlap (Sec. III.B, tolerance set by
+ * u1u1_set_overlap_tol, default 1) and the diagnostic sums (Eqs. 33, 36-37,
+ * without the Gauss-law fields); the result is appended to the handle's
+ * record ring (read with u1u1_read_records).  Asynchronous; safe to capture
+ * in a CUDA graph.  Errors: INVALID_ARG, CUDA. */
+int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* stream);
+
+/* Overlap tolerance (0: same cell, 1: one cell in any of the 26 directions)
+ * used by fused detection steps. */
+int u1u1_set_overlap_tol(u1u1_lattice* h, int tol);
+
+/* Fast string detection on the current state without stepping (Sec. III.A-B).
+ * Optional device outputs (NULL to skip): cell_p, cell_q (uint8 per site:
+ * sum over the cell's six faces of |W|, each |W| counted up to 3),
+ * windings (int8, 6 arrays of nx*ny*nz: sector-major, plane (x,y), (x,z),
+ * (y,z), the plaquette anchored at each site).  *out is filled on the host
+ * (synchronises `stream`).  Errors: INVALID_ARG, CUDA. */
+int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
+                        int8_t* windings, u1u1_strings* out, void* stream);
+
+/* All diagnostics of Sec. III.A on the current state, including the Gauss
+ * law residual per sector at n-1/2 (Eqs. 9-10), without stepping.  Fills
+ * *out on the host (synchronises `stream`).  Errors: CUDA. */
+int u1u1_diagnostics(u1u1_lattice* h, u1u1_diag* out, void* stream);
+
+/* Copy up to max records of fused detection steps not read yet, oldest
+ * first, into s_out[] and d_out[] (either may be NULL); *count receives the
+ * number copied and *lost (may be NULL) the number overwritten in the
+ * device ring (capacity 1024) before they were read.  Synchronises `stream`. */
+int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag* d_out, int max, int* count,
+                      int64_t* lost, void* stream);
+
+/* Copy the whole state between the handle's device buffers and 20 host
+ * arrays (field order POS then MOM; each u1u1_field_bytes long; pinned
+ * memory recommended).  Upload writes the current position buffer.  Both
+ * are asynchronous on `stream`; the host arrays must stay valid until the
+ * stream reaches them. */
+int u1u1_upload_state(u1u1_lattice* h, const void* const host[U1U1_NFIELDS], void* stream);
+int u1u1_download_state(const u1u1_lattice* h, void* const host[U1U1_NFIELDS], void* stream);
+
+/* Checkpoint / resume: write or read the parameters, step index and all 20
+ * fields to or from a file; resuming continues bit for bit.  Synchronous.
+ * u1u1_load requires a handle whose parameters match the file's lattice.
+ * Errors: IO, INVALID_ARG, CUDA. */
+int u1u1_save(const u1u1_lattice* h, const char* path, void* stream);
+int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
+
+/* ---- kernel selection ---------------------------------------------------- */
+
+/* Step kernel used by a handle: U1U1_KERNEL_AUTO picks the tuned one,
+ * U1U1_KERNEL_SIMPLE is one thread per site with cached global loads,
+ * U1U1_KERNEL_TILED the z-marching shared-memory kernel. */
+#define U1U1_KERNEL_AUTO 0
+#define U1U1_KERNEL_SIMPLE 1
+#define U1U1_KERNEL_TILED 2
+int u1u1_set_kernel(u1u1_lattice* h, int kernel);
+int u1u1_get_kernel(const u1u1_lattice* h, int* kernel);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* U1U1_H */

@@ -1,0 +1,250 @@
+"""GB300-native U(1)xU(1) lattice strings (arXiv:2208.01525) -- Python binding.
+
+A thin layer over the C ABI of ``libu1u1`` (include/u1u1.h): PyTorch only
+allocates the device field arrays and supplies CUDA streams; initial
+conditions, leapfrog steps, winding detection, cell overlap and diagnostics
+all run in the library's CUDA kernels.  There is no CPU fallback: without the
+built library and a CUDA device, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, fields
+
+from . import _abi
+from ._abi import (FP32, FP64, KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, NFIELDS, NMOM, NPOS,  # noqa: F401
+                   U1U1Error, check, lib)
+
+__all__ = ["Params", "Lattice", "U1U1Error", "FP32", "FP64", "KERNEL_AUTO", "KERNEL_SIMPLE",
+           "KERNEL_TILED", "coefficients", "version", "lib"]
+
+
+@dataclass
+class Params:
+    """Model and lattice parameters (u1u1_params), named after the paper."""
+    nx: int = 64
+    ny: int = 64
+    nz: int = 64
+    dx: float = 0.5
+    deta: float = 0.1
+    eta0: float = 1.0
+    m: float = 0.5
+    eta_ref: float = 1.0
+    beta: float = 1.0
+    alpha: float = 2.0
+    lambda_p: float = 2.0
+    lambda_q: float = 2.0
+    e_p: float = 1.0
+    e_q: float = 1.0
+    sigma_p: float = 1.0
+    sigma_q: float = 1.0
+    kappa: float = 0.9
+    seed: int = 1
+    precision: int = FP32
+
+    @classmethod
+    def cube(cls, n: int, **kw) -> "Params":
+        return cls(nx=n, ny=n, nz=n, **kw)
+
+    @property
+    def nsites(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def c(self) -> _abi.CParams:
+        cp = _abi.CParams()
+        for f in fields(self):
+            v = getattr(self, f.name)
+            if f.name == "seed":
+                v = int(v) & 0xFFFFFFFFFFFFFFFF
+            setattr(cp, f.name, v)
+        return cp
+
+
+def version() -> str:
+    return lib().u1u1_version().decode()
+
+
+def coefficients(p: Params, n: int) -> dict:
+    """Host-side step coefficients of step n (Eqs. 12, 19, 22)."""
+    out = (ctypes.c_double * 6)()
+    check(lib().u1u1_coefficients(ctypes.byref(p.c()), int(n), out))
+    return dict(eta=out[0], a=out[1], c=out[2], delta=out[3], omega=out[4], ctilde=out[5])
+
+
+def check_params(p: Params) -> None:
+    check(lib().u1u1_check_params(ctypes.byref(p.c())))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Lattice:
+    """One lattice on one GPU: caller-owned field tensors plus a library handle.
+
+    ``pos[k][f]`` (k = ping-pong buffer, f = U1U1_POS_* order) and ``mom[f]``
+    are flat torch tensors of nx*ny*nz elements on the device.
+    """
+
+    def __init__(self, params: Params, device="cuda", init: bool = True, stream=None,
+                 kernel: int = KERNEL_AUTO):
+        import torch
+        check_params(params)
+        if not torch.cuda.is_available():
+            raise U1U1Error(-4, "no CUDA device: libu1u1 has no CPU path")
+        self.params = params
+        self.device = torch.device(device)
+        self.dtype = torch.float64 if params.precision == FP64 else torch.float32
+        V = params.nsites
+        self.pos = [[torch.empty(V, dtype=self.dtype, device=self.device) for _ in range(NPOS)]
+                    for _ in range(2)]
+        self.mom = [torch.empty(V, dtype=self.dtype, device=self.device) for _ in range(NMOM)]
+        self._bufs = _abi.CBuffers()
+        for k in range(2):
+            for f in range(NPOS):
+                self._bufs.pos[k][f] = self.pos[k][f].data_ptr()
+        for f in range(NMOM):
+            self._bufs.mom[f] = self.mom[f].data_ptr()
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            if init:
+                check(lib().u1u1_init_lattice(ctypes.byref(params.c()), ctypes.byref(self._bufs),
+                                              _stream_ptr(stream), ctypes.byref(self._h)))
+            else:
+                check(lib().u1u1_attach_lattice(ctypes.byref(params.c()), ctypes.byref(self._bufs),
+                                                0, 0, ctypes.byref(self._h)))
+        if kernel != KERNEL_AUTO:
+            self.set_kernel(kernel)
+
+    # -- lifecycle --
+    def close(self):
+        if self._h:
+            lib().u1u1_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state --
+    def current(self):
+        n = ctypes.c_int64()
+        cur = ctypes.c_int()
+        check(lib().u1u1_current(self._h, ctypes.byref(n), ctypes.byref(cur)))
+        return n.value, cur.value
+
+    @property
+    def n(self) -> int:
+        return self.current()[0]
+
+    def fields(self):
+        """The 20 current field tensors (positions of the current buffer, then momenta)."""
+        cur = self.current()[1]
+        return list(self.pos[cur]) + list(self.mom)
+
+    def state(self):
+        """Copy of the whole state as a (20, nz, ny, nx) tensor on the device."""
+        import torch
+        return torch.stack(self.fields()).view(NFIELDS, *self.params.shape)
+
+    def set_state(self, st, n: int = 0):
+        """Write a (20, nz, ny, nx) array (torch or numpy) into buffer 0 and reset
+        the step index to n (the handle is re-attached)."""
+        import torch
+        t = torch.as_tensor(st).to(device=self.device, dtype=self.dtype).reshape(NFIELDS, -1)
+        for f in range(NPOS):
+            self.pos[0][f].copy_(t[f])
+        for f in range(NMOM):
+            self.mom[f].copy_(t[NPOS + f])
+        torch.cuda.synchronize(self.device)
+        kern = self.kernel()
+        self.close()
+        check(lib().u1u1_attach_lattice(ctypes.byref(self.params.c()), ctypes.byref(self._bufs), int(n), 0,
+                                        ctypes.byref(self._h)))
+        self.set_kernel(kern)
+
+    def set_kernel(self, kernel: int):
+        check(lib().u1u1_set_kernel(self._h, int(kernel)))
+
+    def kernel(self) -> int:
+        k = ctypes.c_int()
+        check(lib().u1u1_get_kernel(self._h, ctypes.byref(k)))
+        return k.value
+
+    # -- the hot path --
+    def step(self, nsteps: int = 1, detect_every: int = 0, stream=None):
+        check(lib().u1u1_step(self._h, int(nsteps), int(detect_every), _stream_ptr(stream)))
+
+    def set_overlap_tol(self, tol: int):
+        check(lib().u1u1_set_overlap_tol(self._h, int(tol)))
+
+    def detect_strings(self, tol: int = 1, cells: bool = False, windings: bool = False, stream=None) -> dict:
+        import torch
+        V = self.params.nsites
+        cp = cq = w = None
+        if cells:
+            cp = torch.empty(V, dtype=torch.uint8, device=self.device)
+            cq = torch.empty(V, dtype=torch.uint8, device=self.device)
+        if windings:
+            w = torch.empty(6 * V, dtype=torch.int8, device=self.device)
+        out = _abi.CStrings()
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        check(lib().u1u1_detect_strings(self._h, int(tol), ptr(cp), ptr(cq), ptr(w), ctypes.byref(out),
+                                        _stream_ptr(stream)))
+        res = _abi.struct_to_dict(out)
+        if cells:
+            res["cells"] = torch.stack([cp, cq]).view(2, *self.params.shape)
+        if windings:
+            res["windings"] = w.view(2, 3, *self.params.shape)
+        return res
+
+    def diagnostics(self, stream=None) -> dict:
+        out = _abi.CDiag()
+        check(lib().u1u1_diagnostics(self._h, ctypes.byref(out), _stream_ptr(stream)))
+        return _abi.struct_to_dict(out)
+
+    def read_records(self, max_records: int = 1024, stream=None):
+        s = (_abi.CStrings * max_records)()
+        d = (_abi.CDiag * max_records)()
+        cnt = ctypes.c_int()
+        lost = ctypes.c_int64()
+        check(lib().u1u1_read_records(self._h, s, d, int(max_records), ctypes.byref(cnt), ctypes.byref(lost),
+                                      _stream_ptr(stream)))
+        recs = [(_abi.struct_to_dict(s[k]), _abi.struct_to_dict(d[k])) for k in range(cnt.value)]
+        return recs, lost.value
+
+    # -- host transfer and checkpoints --
+    def upload(self, host_fields, stream=None):
+        """Enqueue host -> device copies of 20 host tensors (pinned recommended)."""
+        arr = (ctypes.c_void_p * NFIELDS)(*[t.data_ptr() for t in host_fields])
+        check(lib().u1u1_upload_state(self._h, arr, _stream_ptr(stream)))
+
+    def download(self, host_fields, stream=None):
+        arr = (ctypes.c_void_p * NFIELDS)(*[t.data_ptr() for t in host_fields])
+        check(lib().u1u1_download_state(self._h, arr, _stream_ptr(stream)))
+
+    def save(self, path: str, stream=None):
+        check(lib().u1u1_save(self._h, str(path).encode(), _stream_ptr(stream)))
+
+    def load(self, path: str, stream=None):
+        check(lib().u1u1_load(self._h, str(path).encode(), _stream_ptr(stream)))
+
+
+def nan_to_none(d: dict) -> dict:
+    return {k: (None if isinstance(v, float) and math.isnan(v) else v) for k, v in d.items()}

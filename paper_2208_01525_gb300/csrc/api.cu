@@ -1,0 +1,682 @@
+// C ABI of libu1u1 (include/u1u1.h): parameter handling, lattice handles,
+// the step loop, detection and diagnostics orchestration, record ring,
+// host epilogue of Sec. III.A (Eqs. 31-37) and checkpoint I/O.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/u1u1.h"
+#include "u1u1_internal.cuh"
+
+using namespace u1u1;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(U1U1_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define U1U1_CUDA_TRY(expr, where)          \
+  do {                                      \
+    cudaError_t e_ = (expr);                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+constexpr int RING_CAP = 1024;
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+}  // namespace
+
+struct u1u1_lattice {
+  u1u1_params p;
+  size_t V;
+  size_t esize;
+  void* pos[2][U1U1_NPOS];
+  void* mom[U1U1_NMOM];
+  int cur;
+  int64_t n;
+  int kernel;       // U1U1_KERNEL_*
+  int overlap_tol;
+  // scratch (owned)
+  uint8_t* faces;
+  BlockPartial* partials;
+  int npartials;
+  CellPartial* cpartials;
+  int ncpartials;
+  RawRecord* ring;
+  RawRecord* scratch_rec;
+  RawRecord* host_rec;  // pinned, RING_CAP entries
+  int64_t rec_written;
+  int64_t rec_read;
+};
+
+// ---------------------------------------------------------------------------
+// parameters and coefficients
+// ---------------------------------------------------------------------------
+
+extern "C" const char* u1u1_version(void) { return "0.1.0"; }
+
+extern "C" const char* u1u1_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int u1u1_params_default(u1u1_params* p) {
+  if (!p) return fail(U1U1_ERR_INVALID_ARG, "params pointer is NULL");
+  memset(p, 0, sizeof(*p));
+  p->nx = p->ny = p->nz = 64;
+  p->dx = 0.5;
+  p->deta = 0.1;
+  p->eta0 = 1.0;
+  p->m = 0.5;
+  p->eta_ref = 1.0;
+  p->beta = 1.0;
+  p->alpha = 2.0;
+  p->lambda_p = p->lambda_q = 2.0;
+  p->e_p = p->e_q = 1.0;
+  p->sigma_p = p->sigma_q = 1.0;
+  p->kappa = 0.9;
+  p->seed = 1;
+  p->precision = U1U1_FP32;
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_check_params(const u1u1_params* p) {
+  if (!p) return fail(U1U1_ERR_INVALID_ARG, "params pointer is NULL");
+  if (p->nx < 4 || p->ny < 4 || p->nz < 4)
+    return fail(U1U1_ERR_INVALID_ARG, "lattice sides must be >= 4 (got %d x %d x %d)", p->nx, p->ny, p->nz);
+  if (p->nx % 4 != 0) return fail(U1U1_ERR_INVALID_ARG, "nx must be a multiple of 4 (got %d)", p->nx);
+  if ((double)p->nx * p->ny * p->nz > 9.0e18)
+    return fail(U1U1_ERR_INVALID_ARG, "lattice too large");
+  if (!(p->dx > 0.0) || !isfinite(p->dx)) return fail(U1U1_ERR_INVALID_ARG, "dx must be > 0");
+  if (!(p->deta > 0.0) || !isfinite(p->deta)) return fail(U1U1_ERR_INVALID_ARG, "deta must be > 0");
+  if (!(p->m >= 0.0 && p->m < 1.0)) return fail(U1U1_ERR_INVALID_ARG, "m must be in [0, 1)");
+  if (p->m != 0.0 && !(p->eta0 > 0.0)) return fail(U1U1_ERR_INVALID_ARG, "eta0 must be > 0 in an expanding background");
+  if (!(p->eta_ref > 0.0) || !isfinite(p->eta_ref)) return fail(U1U1_ERR_INVALID_ARG, "eta_ref must be > 0");
+  if (!isfinite(p->beta) || !isfinite(p->alpha)) return fail(U1U1_ERR_INVALID_ARG, "beta and alpha must be finite");
+  if (!(p->e_p > 0.0) || !(p->e_q > 0.0)) return fail(U1U1_ERR_INVALID_ARG, "e_p and e_q must be > 0");
+  if (!isfinite(p->lambda_p) || !isfinite(p->lambda_q) || !isfinite(p->kappa) || !isfinite(p->sigma_p) ||
+      !isfinite(p->sigma_q))
+    return fail(U1U1_ERR_INVALID_ARG, "couplings must be finite");
+  if (p->precision != U1U1_FP32 && p->precision != U1U1_FP64)
+    return fail(U1U1_ERR_INVALID_ARG, "precision must be U1U1_FP32 or U1U1_FP64");
+  return U1U1_OK;
+}
+
+static void coeffs(const u1u1_params* p, int64_t n, double out[6]) {
+  double eta = p->eta0 + (double)n * p->deta;
+  double pm = (p->m == 0.0) ? 0.0 : p->m / (1.0 - p->m);
+  double a = (pm == 0.0) ? 1.0 : pow(eta / p->eta_ref, pm);
+  double c = pow(a, 2.0 * p->beta);
+  double delta = 0.5 * p->alpha * pm * p->deta / eta;
+  double omega = delta * (1.0 - p->beta);
+  out[0] = eta;
+  out[1] = a;
+  out[2] = c;
+  out[3] = delta;
+  out[4] = omega;
+  out[5] = c * (1.0 + delta) / (1.0 + omega);
+}
+
+extern "C" int u1u1_coefficients(const u1u1_params* p, int64_t n, double out[6]) {
+  int rc = u1u1_check_params(p);
+  if (rc) return rc;
+  if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
+  double eta = p->eta0 + (double)n * p->deta;
+  if (p->m != 0.0 && !(eta > 0.0)) return fail(U1U1_ERR_INVALID_ARG, "eta_n <= 0 at step %lld", (long long)n);
+  coeffs(p, n, out);
+  return U1U1_OK;
+}
+
+extern "C" size_t u1u1_field_bytes(const u1u1_params* p) {
+  if (!p || p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return 0;
+  size_t es = p->precision == U1U1_FP64 ? 8 : 4;
+  return (size_t)p->nx * p->ny * p->nz * es;
+}
+
+extern "C" void u1u1_abi_sizes(size_t out[4]) {
+  if (!out) return;
+  out[0] = sizeof(u1u1_params);
+  out[1] = sizeof(u1u1_buffers);
+  out[2] = sizeof(u1u1_strings);
+  out[3] = sizeof(u1u1_diag);
+}
+
+template <typename T>
+static Coef<T> make_coef(const u1u1_params* p, int64_t n) {
+  double cf[6];
+  coeffs(p, n, cf);
+  const double c = cf[2], delta = cf[3], omega = cf[4];
+  const double dx = p->dx, deta = p->deta;
+  const double lam[2] = {p->lambda_p, p->lambda_q};
+  const double e[2] = {p->e_p, p->e_q};
+  const double sig[2] = {p->sigma_p, p->sigma_q};
+  Coef<T> k;
+  const double kPb = deta / (1.0 + delta);
+  k.kPa = (T)((1.0 - delta) / (1.0 + delta));
+  k.kP1 = (T)(kPb / (dx * dx));
+  for (int s = 0; s < 2; ++s) k.kgl[s] = (T)(kPb * c * 0.5 * lam[s]);
+  k.kgk = (T)(kPb * c * p->kappa);
+  const double kEb = deta / (1.0 + omega);
+  k.kEa = (T)((1.0 - omega) / (1.0 + omega));
+  k.kE1 = (T)(kEb / (dx * dx));
+  for (int s = 0; s < 2; ++s) k.kE2[s] = (T)(kEb * 2.0 * e[s] * e[s] * c / dx);
+  k.deta = (T)deta;
+  k.dx = (T)dx;
+  k.inv_dx2 = (T)(1.0 / (dx * dx));
+  k.inv_dx = (T)(1.0 / dx);
+  for (int s = 0; s < 2; ++s) {
+    k.el_f[s] = (T)(1.0 / (2.0 * e[s] * e[s] * c));
+    k.mag_f[s] = (T)(1.0 / (2.0 * e[s] * e[s] * c * dx * dx));
+    k.lam4[s] = (T)(0.25 * lam[s]);
+    k.sig2[s] = (T)(sig[s] * sig[s]);
+  }
+  k.cV = (T)c;
+  k.kappa = (T)p->kappa;
+  double etam = p->eta0 + (double)(n - 1) * p->deta;
+  double ct = 0.0;
+  if (p->m == 0.0 || etam > 0.0) {
+    double cm[6];
+    coeffs(p, n - 1, cm);
+    ct = cm[5];
+  }
+  for (int s = 0; s < 2; ++s) k.qG[s] = (T)(2.0 * e[s] * e[s] * ct);
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// handle lifecycle
+// ---------------------------------------------------------------------------
+
+static int check_buffers(const u1u1_params* p, const u1u1_buffers* b) {
+  if (!b) return fail(U1U1_ERR_BAD_BUFFER, "buffers pointer is NULL");
+  for (int k = 0; k < 2; ++k)
+    for (int f = 0; f < U1U1_NPOS; ++f) {
+      if (!b->pos[k][f]) return fail(U1U1_ERR_BAD_BUFFER, "pos[%d][%d] is NULL", k, f);
+      if ((uintptr_t)b->pos[k][f] % 256 != 0) return fail(U1U1_ERR_BAD_BUFFER, "pos[%d][%d] is not 256-byte aligned", k, f);
+    }
+  for (int f = 0; f < U1U1_NMOM; ++f) {
+    if (!b->mom[f]) return fail(U1U1_ERR_BAD_BUFFER, "mom[%d] is NULL", f);
+    if ((uintptr_t)b->mom[f] % 256 != 0) return fail(U1U1_ERR_BAD_BUFFER, "mom[%d] is not 256-byte aligned", f);
+  }
+  (void)p;
+  return U1U1_OK;
+}
+
+static void free_scratch(u1u1_lattice* h) {
+  if (!h) return;
+  cudaFree(h->faces);
+  cudaFree(h->partials);
+  cudaFree(h->cpartials);
+  cudaFree(h->ring);
+  cudaFree(h->scratch_rec);
+  cudaFreeHost(h->host_rec);
+}
+
+static int create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out) {
+  int rc = u1u1_check_params(p);
+  if (rc) return rc;
+  if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
+  rc = check_buffers(p, b);
+  if (rc) return rc;
+  u1u1_lattice* h = (u1u1_lattice*)calloc(1, sizeof(u1u1_lattice));
+  if (!h) return fail(U1U1_ERR_OUT_OF_MEMORY, "host allocation failed");
+  h->p = *p;
+  h->V = (size_t)p->nx * p->ny * p->nz;
+  h->esize = p->precision == U1U1_FP64 ? 8 : 4;
+  memcpy(h->pos, b->pos, sizeof(h->pos));
+  memcpy(h->mom, b->mom, sizeof(h->mom));
+  h->kernel = U1U1_KERNEL_AUTO;
+  h->overlap_tol = 1;
+  h->npartials = simple_grid_blocks();
+  int tb = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)h->esize);
+  if (tb > h->npartials) h->npartials = tb;
+  h->ncpartials = cells_grid_blocks();
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->faces, 2 * h->V);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(BlockPartial) * (size_t)h->npartials);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->cpartials, sizeof(CellPartial) * (size_t)h->ncpartials);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->ring, sizeof(RawRecord) * RING_CAP);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->scratch_rec, sizeof(RawRecord));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_rec, sizeof(RawRecord) * RING_CAP);
+  if (e != cudaSuccess) {
+    free_scratch(h);
+    free(h);
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? U1U1_ERR_OUT_OF_MEMORY : U1U1_ERR_CUDA,
+                "scratch allocation: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return U1U1_OK;
+}
+
+template <typename T>
+static LatticeView<T> view(const u1u1_lattice* h) {
+  LatticeView<T> v;
+  for (int f = 0; f < U1U1_NPOS; ++f) {
+    v.pin[f] = (const T*)h->pos[h->cur][f];
+    v.pout[f] = (T*)h->pos[1 - h->cur][f];
+  }
+  for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = (T*)h->mom[f];
+  v.nx = h->p.nx;
+  v.ny = h->p.ny;
+  v.nz = h->p.nz;
+  return v;
+}
+
+template <typename T>
+static cudaError_t init_fields(u1u1_lattice* h, cudaStream_t st) {
+  LatticeView<T> v = view<T>(h);
+  T* pos1[U1U1_NPOS];
+  for (int f = 0; f < U1U1_NPOS; ++f) pos1[f] = (T*)h->pos[1][f];
+  return launch_init<T>(v, pos1, h->p.seed, h->p.sigma_p, h->p.sigma_q, st);
+}
+
+extern "C" int u1u1_init_lattice(const u1u1_params* p, const u1u1_buffers* b, void* stream,
+                                 u1u1_lattice** out) {
+  u1u1_lattice* h = nullptr;
+  int rc = create(p, b, &h);
+  if (rc) return rc;
+  h->cur = 0;
+  h->n = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = h->esize == 8 ? init_fields<double>(h, st) : init_fields<float>(h, st);
+  if (e != cudaSuccess) {
+    free_scratch(h);
+    free(h);
+    return cuda_fail(e, "initial conditions");
+  }
+  *out = h;
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, int64_t n, int current,
+                                   u1u1_lattice** out) {
+  if (current != 0 && current != 1) return fail(U1U1_ERR_INVALID_ARG, "current must be 0 or 1");
+  u1u1_lattice* h = nullptr;
+  int rc = create(p, b, &h);
+  if (rc) return rc;
+  h->cur = current;
+  h->n = n;
+  *out = h;
+  return U1U1_OK;
+}
+
+extern "C" void u1u1_destroy(u1u1_lattice* h) {
+  if (!h) return;
+  free_scratch(h);
+  free(h);
+}
+
+extern "C" int u1u1_current(const u1u1_lattice* h, int64_t* n, int* current) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (n) *n = h->n;
+  if (current) *current = h->cur;
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_set_kernel(u1u1_lattice* h, int kernel) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (kernel < U1U1_KERNEL_AUTO || kernel > U1U1_KERNEL_TILED) return fail(U1U1_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+  h->kernel = kernel;
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_get_kernel(const u1u1_lattice* h, int* kernel) {
+  if (!h || !kernel) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  *kernel = h->kernel;
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_set_overlap_tol(u1u1_lattice* h, int tol) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (tol < 0 || tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
+  h->overlap_tol = tol;
+  return U1U1_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stepping and measuring
+// ---------------------------------------------------------------------------
+
+static bool use_tiled(const u1u1_lattice* h) {
+  if (h->kernel == U1U1_KERNEL_SIMPLE) return false;
+  return tiled_grid_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize) > 0;
+}
+
+template <typename T>
+static cudaError_t run_kernel(u1u1_lattice* h, int mode, const MeasureOut& mo, cudaStream_t st) {
+  LatticeView<T> v = view<T>(h);
+  Coef<T> c = make_coef<T>(&h->p, h->n);
+  if (use_tiled(h)) return launch_tiled<T>(mode, v, c, mo, st);
+  return launch_simple<T>(mode, v, c, mo, st);
+}
+
+static int measure_blocks(const u1u1_lattice* h) {
+  return use_tiled(h) ? tiled_grid_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize) : simple_grid_blocks();
+}
+
+static cudaError_t dispatch(u1u1_lattice* h, int mode, const MeasureOut& mo, cudaStream_t st) {
+  return h->esize == 8 ? run_kernel<double>(h, mode, mo, st) : run_kernel<float>(h, mode, mo, st);
+}
+
+extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* stream) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (nsteps < 0) return fail(U1U1_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (detect_every < 0) return fail(U1U1_ERR_INVALID_ARG, "detect_every must be >= 0");
+  if (h->p.m != 0.0) {
+    double eta_last = h->p.eta0 + (double)(h->n + nsteps) * h->p.deta;
+    double eta_first = h->p.eta0 + (double)h->n * h->p.deta;
+    if (!(eta_first > 0.0) || !(eta_last > 0.0)) return fail(U1U1_ERR_INVALID_ARG, "conformal time must stay > 0");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < nsteps; ++k) {
+    bool det = detect_every > 0 && (h->n % detect_every) == 0;
+    MeasureOut mo{nullptr, nullptr, nullptr};
+    int mode = MODE_WRITE;
+    if (det) {
+      mode |= MODE_MEASURE;
+      mo.partial = h->partials;
+      mo.faces = h->faces;
+    }
+    cudaError_t e = dispatch(h, mode, mo, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+    if (det) {
+      e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, h->overlap_tol, nullptr, nullptr, h->cpartials, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
+      RawRecord* slot = h->ring + (h->rec_written % RING_CAP);
+      e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, slot, (long long)h->n,
+                          1, 0, 1, h->overlap_tol, st);
+      if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+      h->rec_written++;
+    }
+    h->cur ^= 1;
+    h->n++;
+  }
+  return U1U1_OK;
+}
+
+// host epilogue (Sec. III.A): raw sums and counts -> estimators
+static double sqrt_ratio(double num, double den) {
+  if (den == 0.0) return INFINITY;
+  double r = num / den;
+  return r >= 0.0 ? sqrt(r) : NAN;
+}
+
+static void to_strings(const u1u1_params* p, const RawRecord& r, u1u1_strings* s) {
+  memset(s, 0, sizeof(*s));
+  double cf[6];
+  coeffs(p, r.n, cf);
+  s->n = r.n;
+  s->eta = cf[0];
+  s->n_p = r.cnt[C_NP];
+  s->n_q = r.cnt[C_NQ];
+  s->nonzero_p = r.cnt[C_NZP];
+  s->nonzero_q = r.cnt[C_NZQ];
+  s->n_pq_plaq = r.cnt[C_NPQ_PLAQ];
+  s->n_pq_cell = r.cells[0];
+  s->n_pq_cell_q = r.cells[1];
+  s->n_flagged = r.cnt[C_FLAGGED];
+  s->max_abs_w = (int32_t)r.cnt[C_MAXW];
+  s->overlap_tol = r.tol;
+  const double dx = p->dx;
+  const double vol = (double)p->nx * p->ny * p->nz * dx * dx * dx;
+  s->L_pq = dx * (double)s->n_pq_cell;
+  s->L_p = dx * (double)s->n_p - s->L_pq;
+  s->L_q = dx * (double)s->n_q - s->L_pq;
+  double tot = s->L_p + s->L_q + s->L_pq;
+  s->xi_p = sqrt_ratio(vol, s->L_p);
+  s->xi_q = sqrt_ratio(vol, s->L_q);
+  s->xi_pq = sqrt_ratio(vol, s->L_pq);
+  s->xi_w = sqrt_ratio(vol, tot);
+  s->f_total = tot != 0.0 ? s->L_pq / tot : NAN;
+  s->f_p = s->L_p != 0.0 ? s->L_pq / s->L_p : NAN;
+}
+
+static void to_diag(const u1u1_params* p, const RawRecord& r, u1u1_diag* d) {
+  memset(d, 0, sizeof(*d));
+  double cf[6];
+  coeffs(p, r.n, cf);
+  d->n = r.n;
+  d->eta = cf[0];
+  d->a = cf[1];
+  d->kin_p = r.sum[S_KIN_P];
+  d->kin_q = r.sum[S_KIN_Q];
+  d->grad_p = r.sum[S_GRAD_P];
+  d->grad_q = r.sum[S_GRAD_Q];
+  d->el_p = r.sum[S_EL_P];
+  d->el_q = r.sum[S_EL_Q];
+  d->mag_p = r.sum[S_MAG_P];
+  d->mag_q = r.sum[S_MAG_Q];
+  d->pot = r.sum[S_POT];
+  d->vint = r.sum[S_VINT];
+  d->lag = r.sum[S_LAG];
+  d->energy = r.sum[S_ENERGY];
+  d->rl_num = r.sum[S_RL_NUM];
+  d->rl_den = r.sum[S_RL_DEN];
+  d->rpq_num = r.sum[S_RPQ_NUM];
+  d->rpq_den = r.sum[S_RPQ_DEN];
+  const double dx3 = p->dx * p->dx * p->dx;
+  const double vol = (double)p->nx * p->ny * p->nz * dx3;
+  const double mu = TWO_PI * p->sigma_p * p->sigma_p;
+  d->lag_total = dx3 * d->lag;
+  d->energy_total = dx3 * d->energy;
+  d->xi_l = sqrt_ratio(-mu * vol, d->lag_total);
+  d->R_l = d->rl_den != 0.0 ? d->rl_num / d->rl_den : NAN;
+  d->v2_l = 2.0 * d->R_l / (1.0 + d->R_l);
+  d->R_pq = d->rpq_den != 0.0 ? d->rpq_num / d->rpq_den : NAN;
+  d->v2_pq = 2.0 * d->R_pq / (1.0 + d->R_pq);
+  d->has_gauss = r.has_gauss;
+  if (r.has_gauss) {
+    d->gauss_sum_p = r.sum[S_GAUSS_P];
+    d->gauss_sum_q = r.sum[S_GAUSS_Q];
+    d->charge_sum_p = r.sum[S_CHARGE_P];
+    d->charge_sum_q = r.sum[S_CHARGE_Q];
+    d->gauss_max_p = r.mx[M_GAUSS_P];
+    d->gauss_max_q = r.mx[M_GAUSS_Q];
+    d->gauss_rel_p = d->charge_sum_p != 0.0 ? d->gauss_sum_p / d->charge_sum_p : NAN;
+    d->gauss_rel_q = d->charge_sum_q != 0.0 ? d->gauss_sum_q / d->charge_sum_q : NAN;
+  } else {
+    d->gauss_sum_p = d->gauss_sum_q = d->charge_sum_p = d->charge_sum_q = NAN;
+    d->gauss_max_p = d->gauss_max_q = d->gauss_rel_p = d->gauss_rel_q = NAN;
+  }
+  d->phi_min_p = -r.mx[M_NEG_PHIMIN_P];
+  d->phi_max_p = r.mx[M_PHIMAX_P];
+  d->phi_min_q = -r.mx[M_NEG_PHIMIN_Q];
+  d->phi_max_q = r.mx[M_PHIMAX_Q];
+  d->nan_count = r.cnt[C_NAN];
+}
+
+static int read_scratch(u1u1_lattice* h, RawRecord* r, cudaStream_t st) {
+  U1U1_CUDA_TRY(cudaMemcpyAsync(h->host_rec, h->scratch_rec, sizeof(RawRecord), cudaMemcpyDeviceToHost, st),
+                "record copy");
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  *r = h->host_rec[0];
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
+                                   int8_t* windings, u1u1_strings* out, void* stream) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (overlap_tol < 0 || overlap_tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
+  if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  MeasureOut mo{h->partials, h->faces, windings};
+  cudaError_t e = dispatch(h, MODE_MEASURE, mo, st);
+  if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
+  e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->cpartials, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
+  e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, h->scratch_rec,
+                      (long long)h->n, 1, 0, 1, overlap_tol, st);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+  RawRecord r;
+  int rc = read_scratch(h, &r, st);
+  if (rc) return rc;
+  to_strings(&h->p, r, out);
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_diagnostics(u1u1_lattice* h, u1u1_diag* out, void* stream) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  MeasureOut mo{h->partials, h->faces, nullptr};
+  cudaError_t e = dispatch(h, MODE_MEASURE | MODE_GAUSS, mo, st);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics kernel");
+  e = launch_finalize(h->partials, measure_blocks(h), nullptr, 0, h->scratch_rec, (long long)h->n, 1, 1, 0,
+                      0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+  RawRecord r;
+  int rc = read_scratch(h, &r, st);
+  if (rc) return rc;
+  to_diag(&h->p, r, out);
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag* d_out, int max, int* count,
+                                 int64_t* lost, void* stream) {
+  if (!h || !count) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  if (max < 0) return fail(U1U1_ERR_INVALID_ARG, "max must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t avail = h->rec_written - h->rec_read;
+  int64_t dropped = 0;
+  if (avail > RING_CAP) {
+    dropped = avail - RING_CAP;
+    h->rec_read += dropped;
+    avail = RING_CAP;
+  }
+  int64_t take = avail < max ? avail : max;
+  // copy only the records being read: one contiguous run, or two when the
+  // run wraps around the end of the ring
+  int64_t first = h->rec_read % RING_CAP;
+  int64_t run1 = take < RING_CAP - first ? take : RING_CAP - first;
+  if (run1 > 0)
+    U1U1_CUDA_TRY(cudaMemcpyAsync(h->host_rec + first, h->ring + first, sizeof(RawRecord) * run1,
+                                  cudaMemcpyDeviceToHost, st), "record ring copy");
+  if (take > run1)
+    U1U1_CUDA_TRY(cudaMemcpyAsync(h->host_rec, h->ring, sizeof(RawRecord) * (take - run1),
+                                  cudaMemcpyDeviceToHost, st), "record ring copy");
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  for (int64_t k = 0; k < take; ++k) {
+    const RawRecord& r = h->host_rec[(h->rec_read + k) % RING_CAP];
+    if (s_out) to_strings(&h->p, r, &s_out[k]);
+    if (d_out) to_diag(&h->p, r, &d_out[k]);
+  }
+  h->rec_read += take;
+  *count = (int)take;
+  if (lost) *lost = dropped;
+  return U1U1_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state transfer and checkpoints
+// ---------------------------------------------------------------------------
+
+extern "C" int u1u1_upload_state(u1u1_lattice* h, const void* const host[U1U1_NFIELDS], void* stream) {
+  if (!h || !host) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  size_t bytes = h->V * h->esize;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int f = 0; f < U1U1_NFIELDS; ++f) {
+    if (!host[f]) return fail(U1U1_ERR_INVALID_ARG, "host[%d] is NULL", f);
+    void* dst = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
+    U1U1_CUDA_TRY(cudaMemcpyAsync(dst, host[f], bytes, cudaMemcpyHostToDevice, st), "state upload");
+  }
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_download_state(const u1u1_lattice* h, void* const host[U1U1_NFIELDS], void* stream) {
+  if (!h || !host) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  size_t bytes = h->V * h->esize;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int f = 0; f < U1U1_NFIELDS; ++f) {
+    if (!host[f]) return fail(U1U1_ERR_INVALID_ARG, "host[%d] is NULL", f);
+    const void* src = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
+    U1U1_CUDA_TRY(cudaMemcpyAsync(host[f], src, bytes, cudaMemcpyDeviceToHost, st), "state download");
+  }
+  return U1U1_OK;
+}
+
+namespace {
+const char CKPT_MAGIC[8] = {'U', '1', 'U', '1', 'C', 'K', 'P', '1'};
+}
+
+extern "C" int u1u1_save(const u1u1_lattice* h, const char* path, void* stream) {
+  if (!h || !path) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(U1U1_ERR_IO, "cannot open %s for writing", path);
+  size_t bytes = h->V * h->esize;
+  void* buf = malloc(bytes);
+  if (!buf) {
+    fclose(f);
+    return fail(U1U1_ERR_OUT_OF_MEMORY, "host buffer of %zu bytes", bytes);
+  }
+  int rc = U1U1_OK;
+  int64_t n = h->n;
+  if (fwrite(CKPT_MAGIC, 8, 1, f) != 1 || fwrite(&h->p, sizeof(h->p), 1, f) != 1 || fwrite(&n, 8, 1, f) != 1)
+    rc = fail(U1U1_ERR_IO, "write failed on %s", path);
+  for (int k = 0; k < U1U1_NFIELDS && rc == U1U1_OK; ++k) {
+    const void* src = k < U1U1_NPOS ? h->pos[h->cur][k] : h->mom[k - U1U1_NPOS];
+    cudaError_t e = cudaMemcpy(buf, src, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "checkpoint download");
+    else if (fwrite(buf, 1, bytes, f) != bytes) rc = fail(U1U1_ERR_IO, "write failed on %s", path);
+  }
+  free(buf);
+  if (fclose(f) != 0 && rc == U1U1_OK) rc = fail(U1U1_ERR_IO, "close failed on %s", path);
+  return rc;
+}
+
+extern "C" int u1u1_load(u1u1_lattice* h, const char* path, void* stream) {
+  if (!h || !path) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(U1U1_ERR_IO, "cannot open %s", path);
+  char magic[8];
+  u1u1_params p;
+  int64_t n;
+  if (fread(magic, 8, 1, f) != 1 || memcmp(magic, CKPT_MAGIC, 8) != 0 || fread(&p, sizeof(p), 1, f) != 1 ||
+      fread(&n, 8, 1, f) != 1) {
+    fclose(f);
+    return fail(U1U1_ERR_IO, "%s is not a u1u1 checkpoint", path);
+  }
+  if (p.nx != h->p.nx || p.ny != h->p.ny || p.nz != h->p.nz || p.precision != h->p.precision) {
+    fclose(f);
+    return fail(U1U1_ERR_INVALID_ARG, "checkpoint lattice %dx%dx%d/%d does not match the handle", p.nx, p.ny, p.nz,
+                p.precision);
+  }
+  size_t bytes = h->V * h->esize;
+  void* buf = malloc(bytes);
+  if (!buf) {
+    fclose(f);
+    return fail(U1U1_ERR_OUT_OF_MEMORY, "host buffer of %zu bytes", bytes);
+  }
+  int rc = U1U1_OK;
+  for (int k = 0; k < U1U1_NFIELDS && rc == U1U1_OK; ++k) {
+    void* dst = k < U1U1_NPOS ? h->pos[h->cur][k] : h->mom[k - U1U1_NPOS];
+    if (fread(buf, 1, bytes, f) != bytes) rc = fail(U1U1_ERR_IO, "short read on %s", path);
+    else {
+      cudaError_t e = cudaMemcpy(dst, buf, bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) rc = cuda_fail(e, "checkpoint upload");
+    }
+  }
+  free(buf);
+  fclose(f);
+  if (rc == U1U1_OK) h->n = n;
+  return rc;
+}

@@ -1,0 +1,597 @@
+// Tiled z-marching kernel for the fused leapfrog step (Sec. III, Eqs. 17-26),
+// optionally fused with plaquette-winding detection (Sec. III.A) and the
+// diagnostic sums (Eqs. 33, 36-37).
+//
+// Each CTA owns a TX x TY column of sites and marches up a chunk of z-planes.
+// The ten position fields of planes z, z+1 (read) and z+2 (in flight) sit
+// in a three-plane shared-memory ring with a one-site halo in x and y, filled
+// with cp.async (16-byte chunks for the interior, element copies for the x
+// halo).  Per plane, phase 1 computes every site-local quantity a neighbour
+// needs -- the backward-transported scalars conj(U_i) phi, the plaquette
+// curls dx F_ij and, when detecting, the gauge-invariant edge phases -- once,
+// including the halo points, into shared memory; phase 2 assembles the kicks
+// and the drift from those and streams momenta (in place) and positions (to
+// the other ping-pong buffer) out.  Quantities of the plane below the
+// current one (z-direction backward terms) are carried in registers, so each
+// position value is read from HBM once per step and each link phase is
+// evaluated once.
+#include <stdint.h>
+
+#include "reduce.cuh"
+#include "site_math.cuh"
+#include "u1u1_internal.cuh"
+
+namespace u1u1 {
+
+namespace {
+
+__device__ __forceinline__ int wrapm(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Per-thread accumulation of the diagnostic sums: compensated FP32 pairs for
+// the FP32 kernel (cheap on the FP32 pipes; converted to FP64 at the end of
+// the chunk), plain FP64 for the FP64 kernel.
+template <typename T>
+struct SumAcc;
+template <>
+struct SumAcc<float> {
+  float s[16], c[16];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = c[k] = 0.f;
+  }
+  __device__ __forceinline__ void add(int k, float v) {
+    float y = v - c[k];
+    float t = s[k] + y;
+    c[k] = (t - s[k]) - y;
+    s[k] = t;
+  }
+  __device__ double get(int k) const { return (double)s[k] - (double)c[k]; }
+};
+template <>
+struct SumAcc<double> {
+  double s[16];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int k, double v) { s[k] += v; }
+  __device__ double get(int k) const { return s[k]; }
+};
+
+template <typename T, int TX, int TY>
+struct Tile {
+  static constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte chunk
+  static constexpr int RS = TX + 2 * VEC;     // smem row stride (elements)
+  static constexpr int ROWS = TY + 2;         // rows ly = -1 .. TY
+  static constexpr int PLANE = ROWS * RS;     // one field, one plane
+  static constexpr int OFF = VEC;             // column of lx = 0
+  static constexpr int NT = TX * TY;
+  static constexpr int CH = TX / VEC;         // interior chunks per row
+  static_assert(TX % VEC == 0, "TX must be a multiple of the 16-byte vector");
+  static __device__ __forceinline__ int at(int ly, int lx) { return (ly + 1) * RS + OFF + lx; }
+};
+
+// Shared memory of one CTA; the detection and Gauss arrays shrink to one
+// element when the kernel variant does not use them.
+template <typename T, int TX, int TY, bool MEAS = true, bool GAUSS = true>
+struct Smem {
+  using TL = Tile<T, TX, TY>;
+  static constexpr int PM = MEAS ? TL::PLANE : 1;
+  static constexpr int PG = GAUSS ? TL::PLANE : 1;
+  T pos[3][U1U1_NPOS][TL::PLANE];      // position ring
+  T P[2][2][2][TL::PLANE];             // [sector][dir 0,1][re,im] conj(U_i) phi
+  T Ft[2][3][TL::PLANE];               // [sector][plane] dx F at this plane
+  T chi[2][3][PM];                     // [sector][dir] edge phases (detection)
+  T Eg[2][2][PG];                      // [sector][dir 0,1] E for the Gauss divergence
+  uint8_t chif[2][PM];                 // [sector] branch-cut flags, bit i per dir
+};
+
+template <typename SM, typename T, int TX, int TY>
+__device__ __forceinline__ void load_plane(SM& sm, int b, const LatticeView<T>& v, int z,
+                                           int x0, int y0) {
+  using TL = Tile<T, TX, TY>;
+  constexpr int PER_ROW = TL::CH + 2;
+  constexpr int JOBS = U1U1_NPOS * TL::ROWS * PER_ROW;
+  const int zz = wrapm(z, v.nz);
+  for (int job = threadIdx.x; job < JOBS; job += TL::NT) {
+    const int f = job / (TL::ROWS * PER_ROW);
+    const int r = (job / PER_ROW) % TL::ROWS;
+    const int c = job % PER_ROW;
+    const int gy = wrapm(y0 + r - 1, v.ny);
+    const T* row = v.pin[f] + ((long long)zz * v.ny + gy) * v.nx;
+    T* srow = &sm.pos[b][f][r * TL::RS];
+    if (c < TL::CH) {
+      const int gx = (x0 + c * TL::VEC) % v.nx;
+      cp_async16(srow + TL::OFF + c * TL::VEC, row + gx);
+    } else if (c == TL::CH) {
+      const int gx = wrapm(x0 - 1, v.nx);
+      cp_async_small<sizeof(T)>(srow + TL::OFF - 1, row + gx);
+    } else {
+      const int gx = (x0 + TX) % v.nx;
+      cp_async_small<sizeof(T)>(srow + TL::OFF + TX, row + gx);
+    }
+  }
+}
+
+// Edge phase of link d at smem point (ly, lx) of plane buffer b, to the
+// neighbour (ly + oy, lx + ox) of plane buffer bn (which is b except for d = 2).
+template <typename SM, typename T, int TX, int TY>
+__device__ __forceinline__ T chi_at(const SM& sm, int s, int d, int b, int bn, int ly, int lx,
+                                    int oy, int ox, T dx, bool* cut) {
+  using TL = Tile<T, TX, TY>;
+  const int a = TL::at(ly, lx), nb = TL::at(ly + oy, lx + ox);
+  T sn, cs;
+  sincos_t<T>(dx * sm.pos[b][4 + 3 * s + d][a], &sn, &cs);
+  T fr, fi;
+  transport_fwd<T>(cs, sn, sm.pos[bn][2 * s][nb], sm.pos[bn][2 * s + 1][nb], &fr, &fi);
+  const T ar = sm.pos[b][2 * s][a], ai = sm.pos[b][2 * s + 1][a];
+  return edge_chi<T>(ar * fr + ai * fi, ar * fi - ai * fr, cut);
+}
+
+template <typename T, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(TX* TY)
+k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
+  using TL = Tile<T, TX, TY>;
+  constexpr bool WRITE = (MODE & MODE_WRITE) != 0;
+  constexpr bool MEAS = (MODE & MODE_MEASURE) != 0;
+  constexpr bool GAUSS = (MODE & MODE_GAUSS) != 0;
+  static_assert(!(WRITE && GAUSS), "Gauss needs unmodified neighbour momenta");
+  using SM = Smem<T, TX, TY, MEAS, GAUSS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM& sm = *reinterpret_cast<SM*>(smem_raw);
+
+  const int tid = threadIdx.x;
+  const int lx = tid % TX, ly = tid / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * lz;
+  const int z1 = min(z0 + lz, v.nz);
+  const int gx = x0 + lx, gy = y0 + ly;
+  const bool active = gx < v.nx && gy < v.ny;
+  const long long plane = (long long)v.nx * v.ny;
+  const long long V = plane * v.nz;
+  const T dx = c.dx;
+
+  SumAcc<T> acc;
+  double mx[NMAX];
+  int cnt[NCNT];
+  double gauss_abs[2] = {0.0, 0.0}, charge_abs[2] = {0.0, 0.0};
+  if (MEAS) {
+    acc.zero();
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
+  }
+
+  // ---- prologue: planes z0-1, z0, z0+1 in flight; backward-z carries ----
+  load_plane<SM, T, TX, TY>(sm, 0, v, z0 - 1, x0, y0);
+  cp_async_commit();
+  load_plane<SM, T, TX, TY>(sm, 1, v, z0, x0, y0);
+  cp_async_commit();
+  load_plane<SM, T, TX, TY>(sm, 2, v, z0 + 1, x0, y0);
+  cp_async_commit();
+  cp_async_wait1();
+  __syncthreads();
+
+  // carries: conj(U_2) phi, dx F_02, dx F_12 at (x, z-1), and E_2(x, z-1)
+  T cP2r[2], cP2i[2], cF02[2], cF12[2], cE2[2];
+  {
+    const int a = TL::at(ly, lx);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      T sn, cs;
+      sincos_t<T>(dx * sm.pos[0][6 + 3 * s][a], &sn, &cs);
+      transport_bwd<T>(cs, sn, sm.pos[0][2 * s][a], sm.pos[0][2 * s + 1][a], &cP2r[s], &cP2i[s]);
+      const T* A0 = sm.pos[0][4 + 3 * s];
+      const T* A1 = sm.pos[0][5 + 3 * s];
+      const T* A2 = sm.pos[0][6 + 3 * s];
+      cF02[s] = curl_ft<T>(A2[TL::at(ly, lx + 1)], A2[a], sm.pos[1][4 + 3 * s][a], A0[a]);
+      cF12[s] = curl_ft<T>(A2[TL::at(ly + 1, lx)], A2[a], sm.pos[1][5 + 3 * s][a], A1[a]);
+      cE2[s] = T(0);
+      if (GAUSS && active) cE2[s] = v.mom[6 + 3 * s][(long long)wrapm(z0 - 1, v.nz) * plane + (long long)gy * v.nx + gx];
+    }
+  }
+
+  for (int z = z0; z < z1; ++z) {
+    const int it = z - z0;
+    const int bc = (it + 1) % 3, bn = (it + 2) % 3, bf = it % 3;
+    __syncthreads();  // everyone is done with buffer bf (plane z-1)
+    if (z + 2 <= z1) load_plane<SM, T, TX, TY>(sm, bf, v, z + 2, x0, y0);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+
+    const long long gsite = (long long)z * plane + (long long)gy * v.nx + gx;
+    // momenta of the own site (plain loads; consumed after phase 1)
+    T pr[2], pim[2], E[2][3];
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        pr[s] = v.mom[2 * s][gsite];
+        pim[s] = v.mom[2 * s + 1][gsite];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) E[s][i] = v.mom[4 + 3 * s + i][gsite];
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        pr[s] = pim[s] = T(0);
+        E[s][0] = E[s][1] = E[s][2] = T(0);
+      }
+    }
+
+    // ---- phase 1: site-local quantities of plane z ----
+    const int a = TL::at(ly, lx);
+    T cs_[2][3], sn_[2][3], F[2][3], P2r[2], P2i[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T* fr = sm.pos[bc][2 * s];
+      const T* fi = sm.pos[bc][2 * s + 1];
+      const T* A0 = sm.pos[bc][4 + 3 * s];
+      const T* A1 = sm.pos[bc][5 + 3 * s];
+      const T* A2 = sm.pos[bc][6 + 3 * s];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sincos_t<T>(dx * sm.pos[bc][4 + 3 * s + i][a], &sn_[s][i], &cs_[s][i]);
+      T pr0, pi0, pr1, pi1;
+      transport_bwd<T>(cs_[s][0], sn_[s][0], fr[a], fi[a], &pr0, &pi0);
+      transport_bwd<T>(cs_[s][1], sn_[s][1], fr[a], fi[a], &pr1, &pi1);
+      transport_bwd<T>(cs_[s][2], sn_[s][2], fr[a], fi[a], &P2r[s], &P2i[s]);
+      sm.P[s][0][0][a] = pr0;
+      sm.P[s][0][1][a] = pi0;
+      sm.P[s][1][0][a] = pr1;
+      sm.P[s][1][1][a] = pi1;
+      F[s][0] = curl_ft<T>(A1[TL::at(ly, lx + 1)], A1[a], A0[TL::at(ly + 1, lx)], A0[a]);
+      F[s][1] = curl_ft<T>(A2[TL::at(ly, lx + 1)], A2[a], sm.pos[bn][4 + 3 * s][a], A0[a]);
+      F[s][2] = curl_ft<T>(A2[TL::at(ly + 1, lx)], A2[a], sm.pos[bn][5 + 3 * s][a], A1[a]);
+      sm.Ft[s][0][a] = F[s][0];
+      sm.Ft[s][1][a] = F[s][1];
+      sm.Ft[s][2][a] = F[s][2];
+      if (GAUSS) {
+        sm.Eg[s][0][a] = E[s][0];
+        sm.Eg[s][1][a] = E[s][1];
+      }
+    }
+    // halo points: left column (lx = -1) and bottom row (ly = -1)
+    for (int h = tid; h < TX + TY; h += TL::NT) {
+      const bool left = h < TY;
+      const int hy = left ? h : -1;
+      const int hx = left ? -1 : h - TY;
+      const int ha = TL::at(hy, hx);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T* fr = sm.pos[bc][2 * s];
+        const T* fi = sm.pos[bc][2 * s + 1];
+        const T* A0 = sm.pos[bc][4 + 3 * s];
+        const T* A1 = sm.pos[bc][5 + 3 * s];
+        const T* A2 = sm.pos[bc][6 + 3 * s];
+        const int d = left ? 0 : 1;
+        T sn, cs, br, bi;
+        sincos_t<T>(dx * sm.pos[bc][4 + 3 * s + d][ha], &sn, &cs);
+        transport_bwd<T>(cs, sn, fr[ha], fi[ha], &br, &bi);
+        sm.P[s][d][0][ha] = br;
+        sm.P[s][d][1][ha] = bi;
+        sm.Ft[s][0][ha] = curl_ft<T>(A1[TL::at(hy, hx + 1)], A1[ha], A0[TL::at(hy + 1, hx)], A0[ha]);
+        if (left)
+          sm.Ft[s][1][ha] = curl_ft<T>(A2[TL::at(hy, hx + 1)], A2[ha], sm.pos[bn][4 + 3 * s][ha], A0[ha]);
+        else
+          sm.Ft[s][2][ha] = curl_ft<T>(A2[TL::at(hy + 1, hx)], A2[ha], sm.pos[bn][5 + 3 * s][ha], A1[ha]);
+        if (GAUSS) {
+          const long long hs = (long long)z * plane + (long long)wrapm(y0 + hy, v.ny) * v.nx + wrapm(x0 + hx, v.nx);
+          sm.Eg[s][d][ha] = v.mom[4 + 3 * s + d][hs];
+        }
+      }
+    }
+
+    // forward transports U_i phi(x+i) of the own site
+    SectorIn<T> in[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      SectorIn<T>& q = in[s];
+      q.fr = sm.pos[bc][2 * s][a];
+      q.fi = sm.pos[bc][2 * s + 1][a];
+      const int ax = TL::at(ly, lx + 1), ay = TL::at(ly + 1, lx);
+      transport_fwd<T>(cs_[s][0], sn_[s][0], sm.pos[bc][2 * s][ax], sm.pos[bc][2 * s + 1][ax], &q.fwr[0], &q.fwi[0]);
+      transport_fwd<T>(cs_[s][1], sn_[s][1], sm.pos[bc][2 * s][ay], sm.pos[bc][2 * s + 1][ay], &q.fwr[1], &q.fwi[1]);
+      transport_fwd<T>(cs_[s][2], sn_[s][2], sm.pos[bn][2 * s][a], sm.pos[bn][2 * s + 1][a], &q.fwr[2], &q.fwi[2]);
+      q.A[0] = sm.pos[bc][4 + 3 * s][a];
+      q.A[1] = sm.pos[bc][5 + 3 * s][a];
+      q.A[2] = sm.pos[bc][6 + 3 * s][a];
+      q.F[0] = F[s][0];
+      q.F[1] = F[s][1];
+      q.F[2] = F[s][2];
+    }
+
+    if (MEAS) {
+      // edge phases of the own site, and of the right column / top row halo
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        uint8_t fl = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          bool cut = false;
+          sm.chi[s][i][a] = edge_chi<T>(current_re(in[s], i), current_im(in[s], i), &cut);
+          fl |= cut ? (1u << i) : 0u;
+        }
+        sm.chif[s][a] = fl;
+      }
+      for (int h = tid; h < TX + TY; h += TL::NT) {
+        const bool right = h < TY;
+        const int hy = right ? h : TY;
+        const int hx = right ? TX : h - TY;
+        const int ha = TL::at(hy, hx);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          bool c1 = false, c2 = false;
+          const int d1 = right ? 1 : 0;  // right column needs chi_1, top row chi_0
+          T ch1 = right ? chi_at<SM, T, TX, TY>(sm, s, 1, bc, bc, hy, hx, 1, 0, dx, &c1)
+                        : chi_at<SM, T, TX, TY>(sm, s, 0, bc, bc, hy, hx, 0, 1, dx, &c1);
+          T ch2 = chi_at<SM, T, TX, TY>(sm, s, 2, bc, bn, hy, hx, 0, 0, dx, &c2);
+          sm.chi[s][d1][ha] = ch1;
+          sm.chi[s][2][ha] = ch2;
+          sm.chif[s][ha] = (uint8_t)((c1 ? (1u << d1) : 0u) | (c2 ? 4u : 0u));
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 2: assemble the update of the own site ----
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        SectorIn<T>& q = in[s];
+        const int axm = TL::at(ly, lx - 1), aym = TL::at(ly - 1, lx);
+        q.bwr[0] = sm.P[s][0][0][axm];
+        q.bwi[0] = sm.P[s][0][1][axm];
+        q.bwr[1] = sm.P[s][1][0][aym];
+        q.bwi[1] = sm.P[s][1][1][aym];
+        q.bwr[2] = cP2r[s];
+        q.bwi[2] = cP2i[s];
+        q.Fm[0] = sm.Ft[s][0][aym];
+        q.Fm[1] = sm.Ft[s][0][axm];
+        q.Fm[2] = cF02[s];
+        q.Fm[3] = sm.Ft[s][1][axm];
+        q.Fm[4] = cF12[s];
+        q.Fm[5] = sm.Ft[s][2][aym];
+      }
+      T mod2[2] = {in[0].fr * in[0].fr + in[0].fi * in[0].fi, in[1].fr * in[1].fr + in[1].fi * in[1].fi};
+      T rr[2] = {mod2[0] - c.sig2[0], mod2[1] - c.sig2[1]};
+      T prn[2], pin_[2], En[2][3];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        scalar_kick<T>(in[s], rr[s], rr[1 - s], pr[s], pim[s], c, s, &prn[s], &pin_[s]);
+        gauge_kick<T>(in[s], E[s], c, s, En[s]);
+      }
+      if (WRITE) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          v.mom[2 * s][gsite] = prn[s];
+          v.mom[2 * s + 1][gsite] = pin_[s];
+          v.pout[2 * s][gsite] = in[s].fr + c.deta * prn[s];
+          v.pout[2 * s + 1][gsite] = in[s].fi + c.deta * pin_[s];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            v.mom[4 + 3 * s + i][gsite] = En[s][i];
+            v.pout[4 + 3 * s + i][gsite] = in[s].A[i] + c.deta * En[s][i];
+          }
+        }
+      }
+      if (MEAS) {
+        SectorDiag<T> d[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) d[s] = sector_diag<T>(in[s], pr[s], pim[s], prn[s], pin_[s], E[s], En[s], c, s);
+        const T rp = rr[0], rq = rr[1];
+        const T pot = c.cV * (c.lam4[0] * rp * rp + c.lam4[1] * rq * rq - c.kappa * rp * rq);
+        const T vint = c.kappa * rp * rq;
+        const T L = (d[0].kin - d[0].grad + d[0].el - d[0].mag) + (d[1].kin - d[1].grad + d[1].el - d[1].mag) - pot;
+        const T H = (d[0].kin + d[0].grad + d[0].el + d[0].mag) + (d[1].kin + d[1].grad + d[1].el + d[1].mag) + pot;
+        const T kt = d[0].kin + d[1].kin, gt = d[0].grad + d[1].grad;
+        acc.add(S_KIN_P, d[0].kin);
+        acc.add(S_KIN_Q, d[1].kin);
+        acc.add(S_GRAD_P, d[0].grad);
+        acc.add(S_GRAD_Q, d[1].grad);
+        acc.add(S_EL_P, d[0].el);
+        acc.add(S_EL_Q, d[1].el);
+        acc.add(S_MAG_P, d[0].mag);
+        acc.add(S_MAG_Q, d[1].mag);
+        acc.add(S_POT, pot);
+        acc.add(S_VINT, vint);
+        acc.add(S_LAG, L);
+        acc.add(S_ENERGY, H);
+        acc.add(S_RL_NUM, kt * L);
+        acc.add(S_RL_DEN, gt * L);
+        acc.add(S_RPQ_NUM, kt * vint);
+        acc.add(S_RPQ_DEN, gt * vint);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const double m = (double)sqrt(mod2[s]);
+          mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q] = fmax(mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q], -m);
+          mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q] = fmax(mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q], m);
+        }
+        int nan = 0;
+#pragma unroll
+        for (int f = 0; f < U1U1_NPOS; ++f) nan += isnan(sm.pos[bc][f][a]) ? 1 : 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          nan += isnan(pr[s]) + isnan(pim[s]) + isnan(E[s][0]) + isnan(E[s][1]) + isnan(E[s][2]);
+        }
+        cnt[C_NAN] += nan;
+
+        if (GAUSS) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            T div = (E[s][0] - sm.Eg[s][0][TL::at(ly, lx - 1)]) + (E[s][1] - sm.Eg[s][1][TL::at(ly - 1, lx)]) +
+                    (E[s][2] - cE2[s]);
+            div *= c.inv_dx;
+            const T rho = c.qG[s] * (in[s].fr * pim[s] - in[s].fi * pr[s]);
+            const T G = div - rho;
+            mx[s == 0 ? M_GAUSS_P : M_GAUSS_Q] = fmax(mx[s == 0 ? M_GAUSS_P : M_GAUSS_Q], fabs((double)G));
+            gauss_abs[s] += fabs((double)G);
+            charge_abs[s] += fabs((double)rho);
+          }
+        }
+
+        // plaquette windings (Sec. III.A)
+        int W[2][3];
+        bool cutk[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const T c0 = sm.chi[s][0][a], c1 = sm.chi[s][1][a], c2 = sm.chi[s][2][a];
+          const uint8_t f0 = sm.chif[s][a];
+          const int ax = TL::at(ly, lx + 1), ay = TL::at(ly + 1, lx);
+          bool n0 = false, n1 = false;
+          const T c0z = chi_at<SM, T, TX, TY>(sm, s, 0, bn, bn, ly, lx, 0, 1, dx, &n0);
+          const T c1z = chi_at<SM, T, TX, TY>(sm, s, 1, bn, bn, ly, lx, 1, 0, dx, &n1);
+          W[s][0] = plaquette_winding<T>(c0, sm.chi[s][1][ax], sm.chi[s][0][ay], c1, dx, in[s].F[0]);
+          W[s][1] = plaquette_winding<T>(c0, sm.chi[s][2][ax], c0z, c2, dx, in[s].F[1]);
+          W[s][2] = plaquette_winding<T>(c1, sm.chi[s][2][ay], c1z, c2, dx, in[s].F[2]);
+          const uint8_t fx = sm.chif[s][ax], fy = sm.chif[s][ay];
+          cutk[s][0] = (f0 & 3u) || (fx & 2u) || (fy & 1u);
+          cutk[s][1] = (f0 & 5u) || (fx & 4u) || n0;
+          cutk[s][2] = (f0 & 6u) || (fy & 4u) || n1;
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          unsigned byte = 0;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int aw = abs(W[s][k]);
+            cnt[s == 0 ? C_NP : C_NQ] += aw;
+            cnt[s == 0 ? C_NZP : C_NZQ] += (aw != 0);
+            cnt[C_FLAGGED] += cutk[s][k] ? 1 : 0;
+            cnt[C_MAXW] = max(cnt[C_MAXW], aw);
+            byte |= (unsigned)min(aw, 3) << FACE_SHIFT(k);
+            if (cutk[s][k]) byte |= FACE_FLAG;
+            if (mo.windings) mo.windings[(3 * s + k) * V + gsite] = (int8_t)max(-127, min(127, W[s][k]));
+          }
+          if (mo.faces) mo.faces[s * V + gsite] = (uint8_t)byte;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cnt[C_NPQ_PLAQ] += (W[0][k] != 0 && W[1][k] != 0) ? 1 : 0;
+      }
+    }
+    // carries for plane z+1
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      cP2r[s] = P2r[s];
+      cP2i[s] = P2i[s];
+      cF02[s] = F[s][1];
+      cF12[s] = F[s][2];
+      cE2[s] = E[s][2];
+    }
+  }
+  cp_async_wait0();
+
+  if (MEAS) {
+    ThreadAcc ta;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) ta.s[k] = acc.get(k);
+    ta.s[S_GAUSS_P] = gauss_abs[0];
+    ta.s[S_GAUSS_Q] = gauss_abs[1];
+    ta.s[S_CHARGE_P] = charge_abs[0];
+    ta.s[S_CHARGE_Q] = charge_abs[1];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) ta.mx[k] = mx[k];
+#pragma unroll
+    for (int k = 0; k < NCNT; ++k) ta.cnt[k] = cnt[k];
+    __syncthreads();
+    ReduceSmem<TL::NT / 32>& rs = *reinterpret_cast<ReduceSmem<TL::NT / 32>*>(smem_raw);
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    block_reduce<TL::NT / 32>(ta, rs, mo.partial + bid);
+  }
+}
+
+template <typename T>
+struct TileShape {
+  static constexpr int TX = 32, TY = 8;
+};
+
+constexpr int TARGET_CTAS = 152 * 3 * 8;  // about eight waves at three CTAs per SM
+
+struct Grid {
+  int gx, gy, gz, lz;
+};
+
+template <typename T>
+Grid tiled_grid(int nx, int ny, int nz) {
+  constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
+  Grid g;
+  g.gx = (nx + TX - 1) / TX;
+  g.gy = (ny + TY - 1) / TY;
+  const int tiles = g.gx * g.gy;
+  int chunks = (TARGET_CTAS + tiles - 1) / tiles;
+  int lz = (nz + chunks - 1) / chunks;
+  if (lz < 8) lz = 8;
+  if (lz > nz) lz = nz;
+  g.lz = lz;
+  g.gz = (nz + lz - 1) / lz;
+  return g;
+}
+
+template <typename T, int MODE>
+cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo, cudaStream_t st) {
+  constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
+  constexpr bool MEAS = (MODE & MODE_MEASURE) != 0;
+  constexpr bool GAUSS = (MODE & MODE_GAUSS) != 0;
+  const size_t bytes = sizeof(Smem<T, TX, TY, MEAS, GAUSS>);
+  // the dynamic shared-memory limit is a per-device function attribute
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    e = cudaFuncSetAttribute(k_tiled<T, TX, TY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  Grid g = tiled_grid<T>(v.nx, v.ny, v.nz);
+  dim3 grid(g.gx, g.gy, g.gz);
+  k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t) {
+  Grid g = sizeof_t == 8 ? tiled_grid<double>(nx, ny, nz) : tiled_grid<float>(nx, ny, nz);
+  return g.gx * g.gy * g.gz;
+}
+
+template <typename T>
+cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
+                         cudaStream_t st) {
+  switch (mode) {
+    case MODE_WRITE:
+      return launch_mode<T, MODE_WRITE>(v, c, mo, st);
+    case MODE_WRITE | MODE_MEASURE:
+      return launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st);
+    case MODE_MEASURE:
+      return launch_mode<T, MODE_MEASURE>(v, c, mo, st);
+    case MODE_MEASURE | MODE_GAUSS:
+      return launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_tiled<float>(int, const LatticeView<float>&, const Coef<float>&, const MeasureOut&,
+                                         cudaStream_t);
+template cudaError_t launch_tiled<double>(int, const LatticeView<double>&, const Coef<double>&,
+                                          const MeasureOut&, cudaStream_t);
+
+}  // namespace u1u1

@@ -1,0 +1,143 @@
+// Per-site arithmetic of the U(1)xU(1) leapfrog (Sec. III, Eqs. 17-26), of
+// the gauge-invariant plaquette windings (Sec. III.A) and of the diagnostic
+// densities (Eqs. 33, 36-37), shared by every kernel variant.  The callers
+// gather the neighbourhood values (from global memory, shared memory or
+// registers) and these functions only compute.
+#pragma once
+
+#include <math.h>
+
+#include "u1u1_internal.cuh"
+
+namespace u1u1 {
+
+template <typename T> __device__ __forceinline__ void sincos_t(T x, T* s, T* c);
+template <> __device__ __forceinline__ void sincos_t<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void sincos_t<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename T> __device__ __forceinline__ T atan2_t(T y, T x);
+template <> __device__ __forceinline__ float atan2_t<float>(float y, float x) { return atan2f(y, x); }
+template <> __device__ __forceinline__ double atan2_t<double>(double y, double x) { return atan2(y, x); }
+
+template <typename T> __device__ __forceinline__ T rint_t(T x);
+template <> __device__ __forceinline__ float rint_t<float>(float x) { return rintf(x); }
+template <> __device__ __forceinline__ double rint_t<double>(double x) { return rint(x); }
+
+template <typename T> struct Consts;
+template <> struct Consts<float> {
+  static __device__ __forceinline__ float pi() { return 3.14159265358979323846f; }
+  static __device__ __forceinline__ float inv_two_pi() { return 0.159154943091895335769f; }
+};
+template <> struct Consts<double> {
+  static __device__ __forceinline__ double pi() { return 3.14159265358979323846; }
+  static __device__ __forceinline__ double inv_two_pi() { return 0.159154943091895335769; }
+};
+
+// U phi with U = exp(-i theta) = (c, -s):  (c + (-s) i)(a + b i)
+template <typename T>
+__device__ __forceinline__ void transport_fwd(T c, T s, T a, T b, T* re, T* im) {
+  *re = c * a + s * b;
+  *im = c * b - s * a;
+}
+// conj(U) phi = (c + s i)(a + b i)
+template <typename T>
+__device__ __forceinline__ void transport_bwd(T c, T s, T a, T b, T* re, T* im) {
+  *re = c * a - s * b;
+  *im = c * b + s * a;
+}
+
+// Everything one sector's site update needs.
+template <typename T>
+struct SectorIn {
+  T fr, fi;            // phi(x)
+  T fwr[3], fwi[3];    // U_i(x) phi(x+i)
+  T bwr[3], bwi[3];    // conj(U_i(x-i)) phi(x-i)
+  T F[3];              // dx F_01, dx F_02, dx F_12 at x
+  T Fm[6];             // dx F at: 01(x-y), 01(x-x), 02(x-z), 02(x-x), 12(x-z), 12(x-y)
+  T A[3];              // A_i(x)
+};
+
+// plaquette curl dx*F_ij(x) = A_j(x+i) - A_j(x) - A_i(x+j) + A_i(x)
+template <typename T>
+__device__ __forceinline__ T curl_ft(T Aj_xpi, T Aj_x, T Ai_xpj, T Ai_x) {
+  return (Aj_xpi - Aj_x) - (Ai_xpj - Ai_x);
+}
+
+// Scalar kick, Eq. 17/18, for sector s; r_self and r_other are
+// |phi_s|^2 - sigma_s^2 and |phi_o|^2 - sigma_o^2.
+template <typename T>
+__device__ __forceinline__ void scalar_kick(const SectorIn<T>& in, T r_self, T r_other, T pr, T pi,
+                                            const Coef<T>& c, int s, T* pr_new, T* pi_new) {
+  T sr = (in.fwr[0] + in.bwr[0]) + (in.fwr[1] + in.bwr[1]) + (in.fwr[2] + in.bwr[2]) - T(6) * in.fr;
+  T si = (in.fwi[0] + in.bwi[0]) + (in.fwi[1] + in.bwi[1]) + (in.fwi[2] + in.bwi[2]) - T(6) * in.fi;
+  T g = c.kgl[s] * r_self - c.kgk * r_other;
+  *pr_new = c.kPa * pr + c.kP1 * sr - g * in.fr;
+  *pi_new = c.kPa * pi + c.kP1 * si - g * in.fi;
+}
+
+// Im[phi^*(x) U_i(x) phi(x+i)] for each direction.
+template <typename T>
+__device__ __forceinline__ T current_im(const SectorIn<T>& in, int i) {
+  return in.fr * in.fwi[i] - in.fi * in.fwr[i];
+}
+template <typename T>
+__device__ __forceinline__ T current_re(const SectorIn<T>& in, int i) {
+  return in.fr * in.fwr[i] + in.fi * in.fwi[i];
+}
+
+// Gauge kick, Eq. 20/21, for sector s.
+template <typename T>
+__device__ __forceinline__ void gauge_kick(const SectorIn<T>& in, const T E[3], const Coef<T>& c,
+                                           int s, T En[3]) {
+  T C0 = (in.F[0] - in.Fm[0]) + (in.F[1] - in.Fm[2]);
+  T C1 = (in.F[2] - in.Fm[4]) - (in.F[0] - in.Fm[1]);
+  T C2 = -(in.F[1] - in.Fm[3]) - (in.F[2] - in.Fm[5]);
+  En[0] = c.kEa * E[0] - c.kE1 * C0 + c.kE2[s] * current_im(in, 0);
+  En[1] = c.kEa * E[1] - c.kE1 * C1 + c.kE2[s] * current_im(in, 1);
+  En[2] = c.kEa * E[2] - c.kE1 * C2 + c.kE2[s] * current_im(in, 2);
+}
+
+// Edge phase chi = arg(Re + i Im) and its branch-cut flag (pi - |chi| < 1e-4
+// or a zero product).
+template <typename T>
+__device__ __forceinline__ T edge_chi(T re, T im, bool* cut) {
+  T chi = atan2_t<T>(im, re);
+  if (Consts<T>::pi() - fabs(chi) < T(1e-4) || (re == T(0) && im == T(0))) *cut = true;
+  return chi;
+}
+
+// Winding of one plaquette from its four edge phases and dx F.
+template <typename T>
+__device__ __forceinline__ int plaquette_winding(T chi_i_x, T chi_j_xpi, T chi_i_xpj, T chi_j_x,
+                                                 T dx, T Ft) {
+  T tot = (chi_i_x + chi_j_xpi) - (chi_i_xpj + chi_j_x) + dx * Ft;
+  return (int)rint_t<T>(tot * Consts<T>::inv_two_pi());
+}
+
+// Diagnostic densities of one sector (Sec. III.A):
+// kin = (|pi-|^2 + |pi+|^2)/2, grad = sum |D+ phi|^2,
+// el = sum (E-^2 + E+^2)/2 / (2 e^2 c), mag = sum F^2 / (2 e^2 c).
+template <typename T>
+struct SectorDiag {
+  T kin, grad, el, mag;
+};
+template <typename T>
+__device__ __forceinline__ SectorDiag<T> sector_diag(const SectorIn<T>& in, T pr, T pi, T prn,
+                                                     T pin, const T E[3], const T En[3],
+                                                     const Coef<T>& c, int s) {
+  SectorDiag<T> d;
+  d.kin = T(0.5) * ((pr * pr + pi * pi) + (prn * prn + pin * pin));
+  T g = T(0);
+  for (int i = 0; i < 3; ++i) {
+    T a = in.fwr[i] - in.fr, b = in.fwi[i] - in.fi;
+    g += a * a + b * b;
+  }
+  d.grad = c.inv_dx2 * g;
+  T e2 = T(0.5) * ((E[0] * E[0] + En[0] * En[0]) + (E[1] * E[1] + En[1] * En[1]) +
+                   (E[2] * E[2] + En[2] * En[2]));
+  d.el = c.el_f[s] * e2;
+  d.mag = c.mag_f[s] * (in.F[0] * in.F[0] + in.F[1] * in.F[1] + in.F[2] * in.F[2]);
+  return d;
+}
+
+}  // namespace u1u1

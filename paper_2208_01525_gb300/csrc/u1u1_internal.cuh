@@ -1,0 +1,126 @@
+// Internal declarations shared by the kernels and the C-ABI host code of
+// libu1u1.  Nothing here is part of the public interface (include/u1u1.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/u1u1.h"
+
+namespace u1u1 {
+
+// ---------------------------------------------------------------------------
+// Reduction record layout.  Every measuring kernel writes one partial per
+// block; a single-block finalize kernel merges them in a fixed order into a
+// RawRecord, so results are bit-reproducible for a given launch shape.
+// ---------------------------------------------------------------------------
+enum SumIdx {
+  S_KIN_P, S_KIN_Q, S_GRAD_P, S_GRAD_Q, S_EL_P, S_EL_Q, S_MAG_P, S_MAG_Q, S_POT, S_VINT,
+  S_LAG, S_ENERGY, S_RL_NUM, S_RL_DEN, S_RPQ_NUM, S_RPQ_DEN,
+  S_GAUSS_P, S_GAUSS_Q, S_CHARGE_P, S_CHARGE_Q,
+  NSUM
+};
+enum MaxIdx {
+  M_GAUSS_P, M_GAUSS_Q, M_NEG_PHIMIN_P, M_PHIMAX_P, M_NEG_PHIMIN_Q, M_PHIMAX_Q,
+  NMAX
+};
+enum CntIdx {
+  C_NP, C_NQ, C_NZP, C_NZQ, C_NPQ_PLAQ, C_FLAGGED, C_MAXW, C_NAN,
+  NCNT
+};
+
+struct BlockPartial {
+  double sum[NSUM];
+  double comp[NSUM];  // Neumaier compensation terms of the block's sums
+  double mx[NMAX];
+  long long cnt[NCNT];
+};
+
+struct CellPartial {
+  long long pq[2];  // p-anchored and q-anchored overlap counts
+};
+
+struct RawRecord {
+  double sum[NSUM];
+  double mx[NMAX];
+  long long cnt[NCNT];
+  long long cells[2];
+  long long n;
+  int has_diag, has_gauss, has_strings, tol;
+};
+// bytes moved device -> host per detection record read
+static_assert(sizeof(RawRecord) == 312, "record layout changed: update the benchmark's byte count");
+
+// Bits of a per-site, per-sector "face byte": |W| (saturated at 3) of the
+// three plaquettes anchored at the site, plus a branch-cut flag.
+__host__ __device__ constexpr int FACE_SHIFT(int k) { return 2 * k; }
+constexpr unsigned FACE_FLAG = 0x40u;
+
+// ---------------------------------------------------------------------------
+// Per-step coefficients, evaluated on the host in FP64 and rounded to T.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Coef {
+  // scalar kick: pi+ = kPa pi + kP1 (sum(fwd + bwd) - 6 phi) - g phi,
+  // g = kgl[s] (|phi_s|^2 - sigma_s^2) - kgk (|phi_o|^2 - sigma_o^2)
+  T kPa, kP1, kgl[2], kgk;
+  // gauge kick: E+ = kEa E - kE1 C + kE2 Im[phi^* U phi(x+i)]
+  T kEa, kE1, kE2[2];
+  T deta, dx;
+  // diagnostics
+  T inv_dx2;        // 1/dx^2 (gradient energy)
+  T el_f[2];        // 1/(2 e^2 c_n)
+  T mag_f[2];       // 1/(2 e^2 c_n dx^2) (F is stored times dx)
+  T cV;             // c_n
+  T lam4[2], sig2[2], kappa;
+  T inv_dx;         // Gauss divergence
+  T qG[2];          // 2 e^2 c~_{n-1}, Gauss charge factor
+};
+
+// Raw field pointers of one lattice (positions double-buffered).
+template <typename T>
+struct LatticeView {
+  const T* pin[U1U1_NPOS];  // positions at step n
+  T* pout[U1U1_NPOS];       // positions at step n+1 (other buffer)
+  T* mom[U1U1_NMOM];        // momenta, in place
+  int nx, ny, nz;
+};
+
+// Outputs of a measuring kernel.
+struct MeasureOut {
+  BlockPartial* partial;  // one per block
+  uint8_t* faces;         // 2 * V bytes (sector-major) or nullptr
+  int8_t* windings;       // 6 * V signed windings or nullptr
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files, called by the host API).
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_init(const LatticeView<T>& v, T* pos1[U1U1_NPOS], uint64_t seed, double sigma_p,
+                        double sigma_q, cudaStream_t st);
+
+// Simple kernel family: mode bits
+enum { MODE_WRITE = 1, MODE_MEASURE = 2, MODE_GAUSS = 4 };
+int simple_grid_blocks();  // fixed grid of the simple kernels (partials needed)
+template <typename T>
+cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
+                          cudaStream_t st);
+
+// Tiled z-marching kernel (FP32 and FP64).
+int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t);
+template <typename T>
+cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
+                         cudaStream_t st);
+
+// Cells and overlap from face bytes.
+int cells_grid_blocks();
+cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p,
+                         uint8_t* cell_q, CellPartial* part, cudaStream_t st);
+
+// Merge partials into a record.
+cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart,
+                            int ncblocks, RawRecord* rec, long long n, int has_diag, int has_gauss,
+                            int has_strings, int tol, cudaStream_t st);
+
+}  // namespace u1u1

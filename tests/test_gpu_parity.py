@@ -1,0 +1,341 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Bars: FP64 GPU within 1e-10 of the oracle (summation order only),
+FP32 within the field max-rel 1e-5 after 20 steps, windings and counts bit
+exact on an identical snapshot except plaquettes flagged within 1e-4 of the
+branch cut (Sec. III.A), diagnostics within the stated relative tolerances.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2208_01525_gb300 as U
+import synth
+from gpu_helpers import field_maxrel, gather_sites, host_state, patches, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+KERNELS = [U.KERNEL_SIMPLE, U.KERNEL_AUTO]
+
+
+def radiation(n, nsteps, **kw):
+    """The 64^3-style configuration: dx 0.5, deta 0.1, radiation, beta = 1,
+    lambda = 2, e = 1, sigma = 1, kappa = 0.9, eta0 = 1, a = 1 at the end."""
+    d = dict(m=0.5, beta=1.0, eta0=1.0, eta_ref=1.0 + 0.1 * nsteps)
+    d.update(kw)
+    if isinstance(n, int):
+        return U.Params.cube(n, **d)
+    return U.Params(nx=n[0], ny=n[1], nz=n[2], **d)
+
+
+@pytest.mark.parametrize("prec", [U.FP64, U.FP32])
+def test_initial_conditions_match_oracle(prec):
+    p = U.Params(nx=20, ny=12, nz=8, seed=77, sigma_p=1.0, sigma_q=0.8, precision=prec)
+    lat = U.Lattice(p)
+    st = host_state(lat)
+    ref = O.init(to_oracle(p))
+    tol = 4e-16 if prec == U.FP64 else 1.2e-7
+    assert np.abs(st - ref).max() <= tol
+    # the other ping-pong buffer is zeroed too
+    other = torch.stack(lat.pos[1]).double().abs().max().item()
+    assert other == 0.0
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp64_matches_oracle_full_run(kernel):
+    """64^3, 160 steps to eta = 17 (radiation, beta = 1), FP64 vs oracle."""
+    p = radiation(64, 160, precision=U.FP64, seed=1)
+    lat = U.Lattice(p, kernel=kernel)
+    lat.step(160)
+    ref = O.init(to_oracle(p))
+    O.step(to_oracle(p), ref, 0, 160)
+    err = field_maxrel(host_state(lat), ref)
+    assert err.max() < 1e-10, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(36, 20, 12), (4, 4, 4), (8, 12, 36)])
+@pytest.mark.parametrize("cfg", [dict(m=2.0 / 3.0, beta=0.0), dict(m=0.5, beta=-1.0, eta_ref=1.0),
+                                 dict(m=0.0, beta=1.0)])
+def test_fp64_ragged_boxes_all_eras(kernel, shape, cfg):
+    p = radiation(shape, 12, precision=U.FP64, seed=5, **cfg)
+    lat = U.Lattice(p, kernel=kernel)
+    st0 = synth.random_state(p.shape, seed=9, a_amp=1.0, mom_amp=0.5)
+    lat.set_state(st0, n=3)
+    lat.step(12)
+    ref = st0.copy()
+    O.step(to_oracle(p), ref, 3, 12)
+    err = field_maxrel(host_state(lat), ref)
+    assert err.max() < 1e-11, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("cfg", [dict(m=0.5, beta=1.0), dict(m=2.0 / 3.0, beta=0.0),
+                                 dict(m=0.5, beta=-1.0, eta_ref=1.0)])
+def test_fp32_matches_oracle_20_steps(kernel, cfg):
+    """FP32 bulk vs FP64 oracle: field max-rel <= 1e-5 after 20 steps."""
+    p = radiation(64, 640, precision=U.FP32, seed=2, **cfg)
+    lat = U.Lattice(p, kernel=kernel)
+    lat.step(20)
+    ref = O.init(to_oracle(p))
+    O.step(to_oracle(p), ref, 0, 20)
+    err = field_maxrel(host_state(lat), ref)
+    assert err.max() <= 1e-5, err
+
+
+def _windings_compare(p, st_gpu_lat):
+    res = st_gpu_lat.detect_strings(tol=1, cells=True, windings=True)
+    snap = host_state(st_gpu_lat)
+    op = to_oracle(p)
+    W, F = O.windings(op, snap)
+    Wg = res["windings"].cpu().numpy().astype(np.int64)
+    flag = F != 0
+    ok = ~flag
+    assert np.array_equal(Wg[ok], W[ok].astype(np.int64))
+    ores = O.strings(op, snap, tol=1)
+    nflag = int(flag.sum())
+    assert abs(res["n_p"] - ores["n_p"]) <= nflag and abs(res["n_q"] - ores["n_q"]) <= nflag
+    if nflag == 0:
+        for k in ("n_p", "n_q", "nonzero_p", "nonzero_q", "n_pq_plaq", "n_pq_cell", "n_pq_cell_q",
+                  "max_abs_w"):
+            assert res[k] == ores[k], (k, res[k], ores[k])
+        assert np.array_equal(res["cells"].cpu().numpy(), ores["cells"])
+        for k in ("L_p", "L_q", "L_pq", "xi_p", "xi_q", "xi_pq", "xi_w", "f_total", "f_p"):
+            assert res[k] == ores[k] or (math.isnan(res[k]) and math.isnan(ores[k])), k
+    return res, ores, nflag
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_windings_bit_exact_on_snapshot(prec, kernel):
+    p = radiation(64, 640, precision=prec, seed=3)
+    lat = U.Lattice(p, kernel=kernel)
+    lat.step(30)
+    res, ores, nflag = _windings_compare(p, lat)
+    assert res["n_p"] > 100  # the early network is dense
+    assert res["n_flagged"] == ores["n_flagged"] or prec == U.FP32
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_windings_rough_random_state(kernel):
+    """Windings of every sign and large link angles (rough synthetic state)."""
+    p = U.Params(nx=24, ny=16, nz=12, m=0.0, precision=U.FP64)
+    lat = U.Lattice(p, kernel=kernel)
+    lat.set_state(synth.random_state(p.shape, seed=4, a_amp=4.0))
+    res, ores, nflag = _windings_compare(p, lat)
+    assert res["max_abs_w"] >= 1
+
+
+def test_planted_vortices_detected():
+    """Four planted strings: |W| = 1 once per z-plane at the expected
+    plaquettes, cell value 2 (Sec. III.B), overlap counts by displacement."""
+    shape = (6, 12, 16)
+    nz, ny, nx = shape
+    for shift, want0, want1 in ((0, 4 * nz, 4 * nz), (1, 0, 4 * nz), (2, 0, 0)):
+        p = U.Params(nx=nx, ny=ny, nz=nz, m=0.0, precision=U.FP32)
+        st = np.zeros((20,) + shape)
+        vm = synth.vortex_map(shape)
+        st[0], st[1] = vm.real, vm.imag
+        vq = np.roll(vm, shift, axis=2)
+        st[2], st[3] = vq.real, vq.imag
+        lat = U.Lattice(p)
+        lat.set_state(st)
+        r0 = lat.detect_strings(tol=0, cells=True)
+        r1 = lat.detect_strings(tol=1)
+        assert r0["n_p"] == 4 * nz and r0["n_q"] == 4 * nz and r0["n_flagged"] == 0
+        assert r0["n_pq_cell"] == want0 and r1["n_pq_cell"] == want1
+        assert int(r0["cells"][0].sum().item()) == 2 * 4 * nz
+
+
+@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-10), (U.FP32, 2e-5)])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_diagnostics_match_oracle(prec, tol, kernel):
+    p = radiation((32, 24, 16), 100, precision=prec, seed=6)
+    lat = U.Lattice(p, kernel=kernel)
+    lat.step(25)
+    d = lat.diagnostics()
+    snap = host_state(lat)
+    od = O.diagnostics(to_oracle(p), snap, 25)
+    scale = abs(od["energy"])
+    for k in ("kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q", "pot", "vint",
+              "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den"):
+        ref = od[k]
+        s = scale if k in ("lag", "pot", "vint") else max(abs(ref), 1e-300)
+        if k.startswith("r"):
+            s = max(abs(od["rl_den"]), abs(od["rl_num"]), abs(ref))
+        assert abs(d[k] - ref) <= tol * s, (k, d[k], ref)
+    for k in ("xi_l", "v2_l", "v2_pq"):
+        if math.isnan(od[k]):  # xi_L is undefined while the Lagrangian sum is positive
+            assert math.isnan(d[k]), k
+        else:
+            assert abs(d[k] - od[k]) <= 50 * tol * abs(od[k]), (k, d[k], od[k])
+    assert d["has_gauss"] == 1
+    for sec in "pq":
+        gscale = od["charge_sum_" + sec] / p.nsites + 1e-300
+        assert d["gauss_max_" + sec] <= max(od["gauss_max_" + sec], 0) + tol * 10 * max(1.0, gscale)
+    for k in ("phi_min_p", "phi_max_p", "phi_min_q", "phi_max_q"):
+        assert abs(d[k] - od[k]) <= tol * 10, k
+    assert d["nan_count"] == 0
+
+
+@pytest.mark.parametrize("prec", [U.FP64, U.FP32])
+def test_gauss_law_preserved(prec):
+    """Sec. IV: Gauss's law holds to round-off from the random-phase start."""
+    p = radiation(48, 200, precision=prec, seed=8)
+    lat = U.Lattice(p)
+    for _ in range(4):
+        lat.step(10)
+        d = lat.diagnostics()
+        for sec in "pq":
+            bound = 1e-12 if prec == U.FP64 else 2e-5
+            assert d["gauss_max_" + sec] < bound, (lat.n, sec, d["gauss_max_" + sec])
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fused_detection_equals_standalone(kernel):
+    """A step fused with detection records exactly what the standalone
+    detection and diagnostics report on the same input state."""
+    p = radiation(40, 400, precision=U.FP32, seed=10)
+    a = U.Lattice(p, kernel=kernel)
+    b = U.Lattice(p, kernel=kernel)
+    a.step(16)
+    b.step(16)
+    s_ref = a.detect_strings(tol=1)
+    d_ref = a.diagnostics()
+    b.step(32, detect_every=16)
+    recs, lost = b.read_records()
+    assert lost == 0 and [r[0]["n"] for r in recs] == [16, 32]
+    s, d = recs[0]
+    for k, v in s_ref.items():
+        assert s[k] == v or (isinstance(v, float) and math.isnan(v) and math.isnan(s[k])), k
+    for k in ("kin_p", "grad_q", "el_p", "mag_q", "pot", "vint", "lag", "energy", "rl_num", "rpq_den",
+              "xi_l", "v2_l", "v2_pq", "phi_min_p", "phi_max_q"):
+        assert d[k] == d_ref[k], (k, d[k], d_ref[k])
+    assert d["has_gauss"] == 0
+    # the run continued: both handles are at the same step and agree
+    a.step(32)
+    assert torch.equal(a.state(), b.state())
+
+
+def test_fp32_vs_fp64_gpu_256():
+    """The 256^3 configuration: FP32 step vs FP64 GPU step over the first 20
+    steps (the oracle is compared at sampled sites in the full-size test)."""
+    p32 = radiation(256, 640, precision=U.FP32, seed=1)
+    p64 = radiation(256, 640, precision=U.FP64, seed=1)
+    a = U.Lattice(p32)
+    a.step(20)
+    sa = a.state().double().cpu().numpy()
+    del a
+    b = U.Lattice(p64)
+    b.step(20)
+    sb = host_state(b)
+    err = field_maxrel(sa, sb)
+    assert err.max() <= 1e-5, err
+
+
+@pytest.mark.parametrize("n,prec", [(256, U.FP32), (1024, U.FP32), (256, U.FP64)])
+def test_full_size_sampled_sites(n, prec):
+    """Full-size lattice in the benchmark's launch configuration: after 20
+    steps, one more step at 192 random sites equals the oracle's step of a
+    5^3 periodic patch around each site (the centre update depends only on
+    its radius-1 neighbourhood), and the windings there match; any-size
+    properties (even cells, sum of cells = 2 sum |W|) hold everywhere."""
+    if n == 1024:
+        free = torch.cuda.mem_get_info()[0]
+        if free < 150e9:
+            pytest.skip("needs ~140 GB of free device memory")
+    p = radiation(n, 2560 if n == 1024 else 640, precision=prec, seed=4)
+    lat = U.Lattice(p)
+    lat.step(20)
+    sites = synth.site_sample(p.shape, 192, seed=n)
+    pt = patches(lat.fields(), p.shape, sites, radius=2)
+    lat.step(1)
+    got = gather_sites(lat.fields(), p.shape, sites)
+    op = to_oracle(p)
+    op.nx = op.ny = op.nz = 5
+    want = np.zeros_like(got)
+    for k in range(len(sites)):
+        st = np.ascontiguousarray(pt[k])
+        O.step(op, st, 20, 1)
+        want[k] = st[:, 2, 2, 2]
+    scale = np.abs(want).max(axis=0)
+    rel = (np.abs(got - want).max(axis=0) / np.where(scale > 0, scale, 1.0))
+    assert rel.max() <= (1e-6 if prec == U.FP32 else 1e-12), rel
+    # windings at the sampled sites on the current snapshot
+    res = lat.detect_strings(tol=1, cells=True, windings=True)
+    pt = patches(lat.fields(), p.shape, sites, radius=2)
+    Wg = res["windings"]
+    s = torch.as_tensor(sites, device=Wg.device)
+    wg = Wg[:, :, s[:, 0], s[:, 1], s[:, 2]].cpu().numpy()
+    for k in range(len(sites)):
+        W, F = O.windings(op, np.ascontiguousarray(pt[k]))
+        ok = F[:, :, 2, 2, 2] == 0
+        assert np.array_equal(wg[:, :, k][ok], W[:, :, 2, 2, 2][ok].astype(wg.dtype))
+    cells = res["cells"]
+    assert not (cells % 2).any().item()
+    for sec in range(2):
+        assert int(cells[sec].sum(dtype=torch.int64).item()) == 2 * int(Wg[sec].abs().sum(dtype=torch.int64).item())
+    assert res["n_p"] == int(Wg[0].abs().sum(dtype=torch.int64).item())
+
+
+def test_checkpoint_resume_bit_exact(tmp_path):
+    p = radiation(24, 50, precision=U.FP32, seed=12)
+    a = U.Lattice(p)
+    a.step(7)
+    path = str(tmp_path / "ckpt.u1u1")
+    a.save(path)
+    a.step(9)
+    b = U.Lattice(p, init=False)
+    b.load(path)
+    assert b.n == 7
+    b.step(9)
+    assert torch.equal(a.state(), b.state())
+
+
+def test_upload_download_roundtrip():
+    p = U.Params(nx=16, ny=8, nz=8, precision=U.FP64)
+    lat = U.Lattice(p)
+    st = torch.from_numpy(synth.random_state(p.shape, seed=1)).reshape(20, -1)
+    host_in = [st[f].contiguous().pin_memory() for f in range(20)]
+    lat.upload(host_in)
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    lat.download(host_out)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(host_in, host_out))
+
+
+def test_vacuum_special_values():
+    p = U.Params(nx=8, ny=8, nz=8, precision=U.FP64)
+    lat = U.Lattice(p)
+    st = np.zeros((20,) + p.shape)
+    st[0] = 1.0
+    st[2] = 1.0
+    lat.set_state(st)
+    r = lat.detect_strings()
+    assert r["n_p"] == 0 and math.isinf(r["xi_w"]) and math.isnan(r["f_total"])
+    lat.step(3)
+    assert torch.equal(lat.state().cpu(), torch.from_numpy(st))
+
+
+def test_edge_cases_and_errors():
+    p = U.Params(nx=8, ny=8, nz=8, m=0.0)
+    lat = U.Lattice(p)
+    s0 = lat.state().clone()
+    lat.step(0)
+    assert lat.n == 0 and torch.equal(lat.state(), s0)
+    with pytest.raises(U.U1U1Error):
+        lat.step(-1)
+    with pytest.raises(U.U1U1Error):
+        lat.detect_strings(tol=2)
+    with pytest.raises(U.U1U1Error):
+        U.Lattice(U.Params(nx=6, ny=8, nz=8))
+    recs, lost = lat.read_records()
+    assert recs == [] and lost == 0
+    # detection ring overflow is reported, not silent
+    lat.step(1100, detect_every=1)
+    recs, lost = lat.read_records(max_records=2000)
+    assert len(recs) == 1024 and lost == 1100 - 1024
+    assert recs[-1][0]["n"] == 1099
