@@ -266,6 +266,15 @@ int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
 int u1u1_set_kernel(u1u1_lattice* h, int kernel);
 int u1u1_get_kernel(const u1u1_lattice* h, int* kernel);
 
+/* ---- check entry points ---------------------------------------------------- */
+
+/* Evaluate, on n device values theta, the FP32 routine the kernels use for
+ * the link variable U = exp(-i theta) (sin and cos of theta, Cody-Waite
+ * reduction plus Taylor series), writing sin_out[k] and cos_out[k] (device
+ * arrays).  Lets tests bound its error against a double-precision
+ * reference.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+int u1u1_eval_link_phase(const float* theta, float* sin_out, float* cos_out, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,7 @@ PROTOTYPES = {
     "u1u1_load": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "u1u1_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
     "u1u1_get_kernel": (ctypes.c_int, [_vp, _P(ctypes.c_int)]),
+    "u1u1_eval_link_phase": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
 }
 
 _lib = None

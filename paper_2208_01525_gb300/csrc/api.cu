@@ -56,6 +56,7 @@ struct u1u1_lattice {
   int overlap_tol;
   // scratch (owned)
   uint8_t* faces;
+  uint32_t* masks;  // packed pierced-cell bits, two sectors
   BlockPartial* partials;
   int npartials;
   CellPartial* cpartials;
@@ -220,6 +221,7 @@ static int check_buffers(const u1u1_params* p, const u1u1_buffers* b) {
 static void free_scratch(u1u1_lattice* h) {
   if (!h) return;
   cudaFree(h->faces);
+  cudaFree(h->masks);
   cudaFree(h->partials);
   cudaFree(h->cpartials);
   cudaFree(h->ring);
@@ -248,6 +250,8 @@ static int create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** ou
   h->ncpartials = cells_grid_blocks();
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->faces, 2 * h->V);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&h->masks, 2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(BlockPartial) * (size_t)h->npartials);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->cpartials, sizeof(CellPartial) * (size_t)h->ncpartials);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ring, sizeof(RawRecord) * RING_CAP);
@@ -396,7 +400,8 @@ extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* st
     cudaError_t e = dispatch(h, mode, mo, st);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel");
     if (det) {
-      e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, h->overlap_tol, nullptr, nullptr, h->cpartials, st);
+      e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, h->overlap_tol, nullptr, nullptr, h->masks,
+                       h->cpartials, st);
       if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
       RawRecord* slot = h->ring + (h->rec_written % RING_CAP);
       e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, slot, (long long)h->n,
@@ -518,7 +523,7 @@ extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* ce
   MeasureOut mo{h->partials, h->faces, windings};
   cudaError_t e = dispatch(h, MODE_MEASURE, mo, st);
   if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
-  e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->cpartials, st);
+  e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->masks, h->cpartials, st);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
   e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, h->scratch_rec,
                       (long long)h->n, 1, 0, 1, overlap_tol, st);
@@ -679,4 +684,17 @@ extern "C" int u1u1_load(u1u1_lattice* h, const char* path, void* stream) {
   fclose(f);
   if (rc == U1U1_OK) h->n = n;
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// check entry points
+// ---------------------------------------------------------------------------
+
+extern "C" int u1u1_eval_link_phase(const float* theta, float* sin_out, float* cos_out, int64_t n, void* stream) {
+  if (n < 0) return fail(U1U1_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return U1U1_OK;
+  if (!theta || !sin_out || !cos_out) return fail(U1U1_ERR_INVALID_ARG, "NULL array");
+  cudaError_t e = launch_link_phase(theta, sin_out, cos_out, (long long)n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "link phase kernel");
+  return U1U1_OK;
 }

@@ -1,0 +1,227 @@
+// Cell arrays, fast bound-state overlap (Sec. III.B) and the deterministic
+// reduction finalize.
+//
+// Pass 1 (k_cellbits) turns the per-site face bytes written by the measuring
+// kernels into cell values c_s(x) = sum over the six faces of cell x of |W|
+// (optionally stored as uint8 cell arrays) and into one bit per cell and
+// sector ("pierced"), packed 32 cells of a lattice row per word with a warp
+// ballot.  Pass 2 (k_overlap) counts p-pierced cells that have a q-pierced
+// cell in their (2 tol + 1)^3 neighbourhood -- a box, so the neighbourhood
+// test is an OR of shifted words over 3 x 3 rows -- and the same with the
+// roles swapped, with popcounts.
+#include <stdint.h>
+
+#include "reduce.cuh"
+#include "u1u1_internal.cuh"
+
+namespace u1u1 {
+
+namespace {
+
+constexpr int ROWS_PER_BLOCK = 8;
+constexpr int BITS_BLOCKS_Y = 2048;
+constexpr int OVL_THREADS = 256;
+constexpr int OVL_BLOCKS = 152 * 8;
+
+__device__ __forceinline__ int face_w(const uint8_t* f, long long i, int k) { return (f[i] >> FACE_SHIFT(k)) & 3; }
+
+__global__ void __launch_bounds__(32 * ROWS_PER_BLOCK)
+k_cellbits(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words, uint8_t* cell_p, uint8_t* cell_q,
+           uint32_t* mp, uint32_t* mq) {
+  const long long V = (long long)nx * ny * nz;
+  const long long nrows = (long long)ny * nz;
+  const int lane = threadIdx.x;
+  const int w = blockIdx.x;
+  const int x = w * 32 + lane;
+  for (long long row = (long long)blockIdx.y * ROWS_PER_BLOCK + threadIdx.y; row < nrows;
+       row += (long long)gridDim.y * ROWS_PER_BLOCK) {
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    int c[2] = {0, 0};
+    if (x < nx) {
+      const long long i = row * nx + x;
+      const long long ix = row * nx + (x + 1 == nx ? 0 : x + 1);
+      const long long iy = ((long long)z * ny + (y + 1 == ny ? 0 : y + 1)) * nx + x;
+      const long long iz = ((long long)(z + 1 == nz ? 0 : z + 1) * ny + y) * nx + x;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const uint8_t* f = faces + s * V;
+        c[s] = face_w(f, i, 0) + face_w(f, iz, 0) + face_w(f, i, 1) + face_w(f, iy, 1) + face_w(f, i, 2) +
+               face_w(f, ix, 2);
+      }
+      if (cell_p) cell_p[i] = (uint8_t)c[0];
+      if (cell_q) cell_q[i] = (uint8_t)c[1];
+    }
+    const uint32_t bp = __ballot_sync(0xffffffffu, c[0] > 0);
+    const uint32_t bq = __ballot_sync(0xffffffffu, c[1] > 0);
+    if (lane == 0) {
+      mp[row * words + w] = bp;
+      mq[row * words + w] = bq;
+    }
+  }
+}
+
+// Bits of the row (y, z) dilated by one cell in x, periodic in x.
+__device__ __forceinline__ uint32_t xdilate(const uint32_t* m, long long rowbase, int w, int words, int nx) {
+  const uint32_t cur = m[rowbase + w];
+  const int last_bit_row = (nx - 1) & 31;                  // bit of x = nx-1 in the last word
+  const uint32_t left_in = (w > 0) ? (m[rowbase + w - 1] >> 31) & 1u
+                                   : (m[rowbase + words - 1] >> last_bit_row) & 1u;
+  const int top = (w < words - 1) ? 31 : last_bit_row;      // last valid bit of this word
+  const uint32_t right_in = (w < words - 1) ? (m[rowbase + w + 1] & 1u) : (m[rowbase] & 1u);
+  uint32_t d = cur | (cur << 1) | (cur >> 1) | left_in | (right_in << top);
+  const uint32_t valid = (top == 31) ? 0xffffffffu : ((1u << (top + 1)) - 1u);
+  return d & valid;
+}
+
+__global__ void __launch_bounds__(OVL_THREADS)
+k_overlap(const uint32_t* __restrict__ mp, const uint32_t* __restrict__ mq, int nx, int ny, int nz, int words,
+          int tol, CellPartial* part) {
+  const long long nw = (long long)ny * nz * words;
+  long long cnt[2] = {0, 0};
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nw;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(idx % words);
+    const long long row = idx / words;
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const uint32_t p = mp[idx], q = mq[idx];
+    if (tol == 0) {
+      cnt[0] += __popc(p & q);
+      cnt[1] += __popc(p & q);
+      continue;
+    }
+    if ((p | q) == 0) continue;
+    uint32_t dq = 0, dp = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = z + dz < 0 ? nz - 1 : (z + dz >= nz ? 0 : z + dz);
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy < 0 ? ny - 1 : (y + dy >= ny ? 0 : y + dy);
+        const long long rb = ((long long)zz * ny + yy) * words;
+        if (p) dq |= xdilate(mq, rb, w, words, nx);
+        if (q) dp |= xdilate(mp, rb, w, words, nx);
+      }
+    }
+    cnt[0] += __popc(p & dq);
+    cnt[1] += __popc(q & dp);
+  }
+  __shared__ long long sm[OVL_THREADS / 32][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int a = 0; a < 2; ++a) {
+    const long long v = warp_sum_ll(cnt[a]);
+    if (lane == 0) sm[warp][a] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    long long v = 0;
+    for (int k = 0; k < OVL_THREADS / 32; ++k) v += sm[k][threadIdx.x];
+    part[blockIdx.x].pq[threadIdx.x] = v;
+  }
+}
+
+// ---- finalize: fixed-order compensated merge of the block partials --------
+
+constexpr int FIN_THREADS = 256;
+
+__device__ __forceinline__ void merge_pair(double& s, double& c, double s2, double c2) {
+  neumaier_add(s, c, s2);
+  c += c2;
+}
+
+__global__ void __launch_bounds__(FIN_THREADS)
+k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __restrict__ cpart, int ncb,
+           RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol) {
+  __shared__ double ss[FIN_THREADS], sc[FIN_THREADS];
+  __shared__ long long sl[FIN_THREADS];
+  const int t = threadIdx.x;
+  for (int k = 0; k < NSUM; ++k) {
+    double s = 0.0, c = 0.0;
+    if (part)
+      for (int b = t; b < nb; b += FIN_THREADS) merge_pair(s, c, part[b].sum[k], part[b].comp[k]);
+    ss[t] = s;
+    sc[t] = c;
+    __syncthreads();
+    for (int h = FIN_THREADS / 2; h > 0; h >>= 1) {
+      if (t < h) {
+        double a = ss[t], ac = sc[t];
+        merge_pair(a, ac, ss[t + h], sc[t + h]);
+        ss[t] = a;
+        sc[t] = ac;
+      }
+      __syncthreads();
+    }
+    if (t == 0) rec->sum[k] = ss[0] + sc[0];
+    __syncthreads();
+  }
+  for (int k = 0; k < NMAX; ++k) {
+    double m = -INFINITY;
+    if (part)
+      for (int b = t; b < nb; b += FIN_THREADS) m = fmax(m, part[b].mx[k]);
+    ss[t] = m;
+    __syncthreads();
+    for (int h = FIN_THREADS / 2; h > 0; h >>= 1) {
+      if (t < h) ss[t] = fmax(ss[t], ss[t + h]);
+      __syncthreads();
+    }
+    if (t == 0) rec->mx[k] = ss[0];
+    __syncthreads();
+  }
+  for (int k = 0; k < NCNT + 2; ++k) {
+    long long v = 0;
+    if (k < NCNT) {
+      if (part)
+        for (int b = t; b < nb; b += FIN_THREADS) v = (k == C_MAXW) ? max(v, part[b].cnt[k]) : v + part[b].cnt[k];
+    } else if (cpart) {
+      for (int b = t; b < ncb; b += FIN_THREADS) v += cpart[b].pq[k - NCNT];
+    }
+    sl[t] = v;
+    __syncthreads();
+    for (int h = FIN_THREADS / 2; h > 0; h >>= 1) {
+      if (t < h) sl[t] = (k == C_MAXW) ? max(sl[t], sl[t + h]) : sl[t] + sl[t + h];
+      __syncthreads();
+    }
+    if (t == 0) {
+      if (k < NCNT) rec->cnt[k] = sl[0];
+      else rec->cells[k - NCNT] = sl[0];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    rec->n = n;
+    rec->has_diag = has_diag;
+    rec->has_gauss = has_gauss;
+    rec->has_strings = has_strings;
+    rec->tol = tol;
+  }
+}
+
+}  // namespace
+
+int cells_grid_blocks() { return OVL_BLOCKS; }
+
+size_t cell_mask_words(int nx, int ny, int nz) { return (size_t)((nx + 31) / 32) * ny * nz; }
+
+cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p, uint8_t* cell_q,
+                         uint32_t* masks, CellPartial* part, cudaStream_t st) {
+  const int words = (nx + 31) / 32;
+  const size_t nw = cell_mask_words(nx, ny, nz);
+  uint32_t* mp = masks;
+  uint32_t* mq = masks + nw;
+  const long long nrows = (long long)ny * nz;
+  long long gy = (nrows + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
+  if (gy > BITS_BLOCKS_Y) gy = BITS_BLOCKS_Y;
+  dim3 block(32, ROWS_PER_BLOCK), grid(words, (unsigned)gy);
+  k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart, int ncblocks,
+                            RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol,
+                            cudaStream_t st) {
+  k_finalize<<<1, FIN_THREADS, 0, st>>>(part, nblocks, cpart, ncblocks, rec, n, has_diag, has_gauss, has_strings,
+                                        tol);
+  return cudaGetLastError();
+}
+
+}  // namespace u1u1

@@ -80,7 +80,7 @@ template <typename T>
 __device__ __forceinline__ void edge_product(const LatticeView<T>& v, int s, long long a, long long b,
                                              T Aval, T dx, T* re, T* im) {
   T sn, cs;
-  sincos_t<T>(dx * Aval, &sn, &cs);
+  link_sincos<T>(dx * Aval, &sn, &cs);
   T br, bi;
   transport_fwd<T>(cs, sn, ld(v.pin[2 * s], b), ld(v.pin[2 * s + 1], b), &br, &bi);
   T ar = ld(v.pin[2 * s], a), ai = ld(v.pin[2 * s + 1], a);
@@ -125,9 +125,9 @@ k_simple(LatticeView<T> v, Coef<T> c, MeasureOut mo) {
         const T* Ai = v.pin[4 + 3 * s + i];
         q.A[i] = ld(Ai, site);
         T sn, cs;
-        sincos_t<T>(c.dx * q.A[i], &sn, &cs);
+        link_sincos<T>(c.dx * q.A[i], &sn, &cs);
         transport_fwd<T>(cs, sn, ld(Fr, xp[i]), ld(Fi, xp[i]), &q.fwr[i], &q.fwi[i]);
-        sincos_t<T>(c.dx * ld(Ai, xm[i]), &sn, &cs);
+        link_sincos<T>(c.dx * ld(Ai, xm[i]), &sn, &cs);
         transport_bwd<T>(cs, sn, ld(Fr, xm[i]), ld(Fi, xm[i]), &q.bwr[i], &q.bwi[i]);
       }
       q.F[0] = curl_ft<T>(ld(A1, xp[0]), q.A[1], ld(A0, xp[1]), q.A[0]);
@@ -272,105 +272,17 @@ k_simple(LatticeView<T> v, Coef<T> c, MeasureOut mo) {
   }
 }
 
-// ---- cells and fast overlap (Sec. III.B) --------------------------------
-
-constexpr int CELL_THREADS = 256;
-constexpr int CELL_BLOCKS = 152 * 8;
-
-__device__ __forceinline__ int face_w(const uint8_t* f, long long i, int k) {
-  return (f[i] >> FACE_SHIFT(k)) & 3;
-}
-
-// Cell value at (x,y,z): sum of |W| over its six faces.
-__device__ __forceinline__ int cell_value(const uint8_t* f, const Geo& g, int x, int y, int z) {
-  long long i = g.idx(x, y, z);
-  return face_w(f, i, 0) + face_w(f, g.nb(x, y, z, 0, 0, 1), 0) + face_w(f, i, 1) +
-         face_w(f, g.nb(x, y, z, 0, 1, 0), 1) + face_w(f, i, 2) + face_w(f, g.nb(x, y, z, 1, 0, 0), 2);
-}
-
-__global__ void __launch_bounds__(CELL_THREADS)
-k_cells(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int tol, uint8_t* cell_p,
-        uint8_t* cell_q, CellPartial* part) {
-  const Geo g{nx, ny, nz};
-  const long long V = (long long)nx * ny * nz;
-  const uint8_t* fp = faces;
-  const uint8_t* fq = faces + V;
-  long long cnt[2] = {0, 0};
-  for (long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x; site < V;
-       site += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(site % nx);
-    const int y = (int)((site / nx) % ny);
-    const int z = (int)(site / ((long long)nx * ny));
-    int c[2] = {cell_value(fp, g, x, y, z), cell_value(fq, g, x, y, z)};
-    if (cell_p) cell_p[site] = (uint8_t)c[0];
-    if (cell_q) cell_q[site] = (uint8_t)c[1];
-    for (int a = 0; a < 2; ++a) {
-      if (c[a] == 0) continue;
-      const uint8_t* fo = a == 0 ? fq : fp;
-      bool hit = false;
-      for (int dz = -tol; dz <= tol && !hit; ++dz)
-        for (int dy = -tol; dy <= tol && !hit; ++dy)
-          for (int dx = -tol; dx <= tol && !hit; ++dx)
-            if (cell_value(fo, g, wrapc(x + dx, nx), wrapc(y + dy, ny), wrapc(z + dz, nz)) > 0) hit = true;
-      cnt[a] += hit;
-    }
-  }
-  __shared__ long long sm[CELL_THREADS / 32][2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int a = 0; a < 2; ++a) {
-    long long v = warp_sum_ll(cnt[a]);
-    if (lane == 0) sm[warp][a] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    long long v = 0;
-    for (int w = 0; w < CELL_THREADS / 32; ++w) v += sm[w][threadIdx.x];
-    part[blockIdx.x].pq[threadIdx.x] = v;
-  }
-}
-
-// ---- finalize ---------------------------------------------------------------
-
-__global__ void k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __restrict__ cpart,
-                           int ncb, RawRecord* rec, long long n, int has_diag, int has_gauss,
-                           int has_strings, int tol) {
-  const int t = threadIdx.x;
-  if (t < NSUM) {
-    double s = 0.0, c = 0.0;
-    if (part)
-      for (int b = 0; b < nb; ++b) {
-        neumaier_add(s, c, part[b].sum[t]);
-        neumaier_add(s, c, part[b].comp[t]);
-      }
-    rec->sum[t] = s + c;
-  } else if (t < NSUM + NMAX) {
-    int k = t - NSUM;
-    double m = -INFINITY;
-    if (part)
-      for (int b = 0; b < nb; ++b) m = fmax(m, part[b].mx[k]);
-    rec->mx[k] = m;
-  } else if (t < NSUM + NMAX + NCNT) {
-    int k = t - NSUM - NMAX;
-    long long v = 0;
-    if (part)
-      for (int b = 0; b < nb; ++b) v = (k == C_MAXW) ? max(v, part[b].cnt[k]) : v + part[b].cnt[k];
-    rec->cnt[k] = v;
-  } else if (t < NSUM + NMAX + NCNT + 2) {
-    int k = t - NSUM - NMAX - NCNT;
-    long long v = 0;
-    if (cpart)
-      for (int b = 0; b < ncb; ++b) v += cpart[b].pq[k];
-    rec->cells[k] = v;
-  } else if (t == NSUM + NMAX + NCNT + 2) {
-    rec->n = n;
-    rec->has_diag = has_diag;
-    rec->has_gauss = has_gauss;
-    rec->has_strings = has_strings;
-    rec->tol = tol;
-  }
+__global__ void k_link_phase(const float* __restrict__ th, float* sn, float* cs, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    link_sincos<float>(th[i], &sn[i], &cs[i]);
 }
 
 }  // namespace
+
+cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n, cudaStream_t st) {
+  k_link_phase<<<152 * 4, 256, 0, st>>>(th, sn, cs, n);
+  return cudaGetLastError();
+}
 
 // ---- launchers ---------------------------------------------------------------
 
@@ -404,22 +316,6 @@ cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, c
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-int cells_grid_blocks() { return CELL_BLOCKS; }
-
-cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p,
-                         uint8_t* cell_q, CellPartial* part, cudaStream_t st) {
-  k_cells<<<CELL_BLOCKS, CELL_THREADS, 0, st>>>(faces, nx, ny, nz, tol, cell_p, cell_q, part);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart,
-                            int ncblocks, RawRecord* rec, long long n, int has_diag, int has_gauss,
-                            int has_strings, int tol, cudaStream_t st) {
-  k_finalize<<<1, 64, 0, st>>>(part, nblocks, cpart, ncblocks, rec, n, has_diag, has_gauss,
-                               has_strings, tol);
   return cudaGetLastError();
 }
 

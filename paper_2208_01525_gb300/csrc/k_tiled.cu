@@ -102,33 +102,44 @@ struct Smem {
   uint8_t chif[2][PM];                 // [sector] branch-cut flags, bit i per dir
 };
 
-template <typename SM, typename T, int TX, int TY>
-__device__ __forceinline__ void load_plane(SM& sm, int b, const LatticeView<T>& v, int z,
-                                           int x0, int y0) {
+// Copy plan of one thread: every copy moves one 16-byte chunk of one row of
+// one field.  A row of the smem ring holds TX + 2 VEC elements: the chunk
+// ending at x0-1 (left halo), the TX interior elements and the chunk starting
+// at x0+TX (right halo), so the x halo comes for free with 16-byte copies.
+// The per-plane part of a copy is only the z offset; everything else is
+// computed once per CTA.
+template <typename T, int TX, int TY>
+struct CopyPlan {
   using TL = Tile<T, TX, TY>;
-  constexpr int PER_ROW = TL::CH + 2;
-  constexpr int JOBS = U1U1_NPOS * TL::ROWS * PER_ROW;
-  const int zz = wrapm(z, v.nz);
-  for (int job = threadIdx.x; job < JOBS; job += TL::NT) {
-    const int f = job / (TL::ROWS * PER_ROW);
-    const int r = (job / PER_ROW) % TL::ROWS;
-    const int c = job % PER_ROW;
-    const int gy = wrapm(y0 + r - 1, v.ny);
-    const T* row = v.pin[f] + ((long long)zz * v.ny + gy) * v.nx;
-    T* srow = &sm.pos[b][f][r * TL::RS];
-    if (c < TL::CH) {
-      const int gx = (x0 + c * TL::VEC) % v.nx;
-      cp_async16(srow + TL::OFF + c * TL::VEC, row + gx);
-    } else if (c == TL::CH) {
-      const int gx = wrapm(x0 - 1, v.nx);
-      cp_async_small<sizeof(T)>(srow + TL::OFF - 1, row + gx);
-    } else {
-      const int gx = (x0 + TX) % v.nx;
-      cp_async_small<sizeof(T)>(srow + TL::OFF + TX, row + gx);
+  static constexpr int PER_ROW = TL::CH + 2;
+  static constexpr int JOBS = U1U1_NPOS * TL::ROWS * PER_ROW;
+  static constexpr int NJ = (JOBS + TL::NT - 1) / TL::NT;
+  const T* g[NJ];   // global address of the chunk in plane z = 0
+  int s[NJ];        // element offset inside one ring buffer (-1: no job)
+
+  __device__ void init(const LatticeView<T>& v, int x0, int y0) {
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+      const int job = threadIdx.x + k * TL::NT;
+      s[k] = -1;
+      g[k] = nullptr;
+      if (job < JOBS) {
+        const int f = job / (TL::ROWS * PER_ROW);
+        const int r = (job / PER_ROW) % TL::ROWS;
+        const int c = job % PER_ROW;  // 0: left halo chunk, 1..CH: interior, CH+1: right halo
+        const int gy = wrapm(y0 + r - 1, v.ny);
+        const int gx = wrapm(x0 + (c - 1) * TL::VEC, v.nx);
+        g[k] = v.pin[f] + (long long)gy * v.nx + gx;
+        s[k] = f * TL::PLANE + r * TL::RS + c * TL::VEC;
+      }
     }
   }
-}
-
+  __device__ __forceinline__ void issue(T* ring_buf, long long zoff) const {
+#pragma unroll
+    for (int k = 0; k < NJ; ++k)
+      if (s[k] >= 0) cp_async16(ring_buf + s[k], g[k] + zoff);
+  }
+};
 // Edge phase of link d at smem point (ly, lx) of plane buffer b, to the
 // neighbour (ly + oy, lx + ox) of plane buffer bn (which is b except for d = 2).
 template <typename SM, typename T, int TX, int TY>
@@ -137,7 +148,7 @@ __device__ __forceinline__ T chi_at(const SM& sm, int s, int d, int b, int bn, i
   using TL = Tile<T, TX, TY>;
   const int a = TL::at(ly, lx), nb = TL::at(ly + oy, lx + ox);
   T sn, cs;
-  sincos_t<T>(dx * sm.pos[b][4 + 3 * s + d][a], &sn, &cs);
+  link_sincos<T>(dx * sm.pos[b][4 + 3 * s + d][a], &sn, &cs);
   T fr, fi;
   transport_fwd<T>(cs, sn, sm.pos[bn][2 * s][nb], sm.pos[bn][2 * s + 1][nb], &fr, &fi);
   const T ar = sm.pos[b][2 * s][a], ai = sm.pos[b][2 * s + 1][a];
@@ -145,7 +156,7 @@ __device__ __forceinline__ T chi_at(const SM& sm, int s, int d, int b, int bn, i
 }
 
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(TX* TY, (MODE == MODE_WRITE && sizeof(T) == 4) ? 3 : 1)
 k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
   using TL = Tile<T, TX, TY>;
   constexpr bool WRITE = (MODE & MODE_WRITE) != 0;
@@ -180,11 +191,14 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
   }
 
   // ---- prologue: planes z0-1, z0, z0+1 in flight; backward-z carries ----
-  load_plane<SM, T, TX, TY>(sm, 0, v, z0 - 1, x0, y0);
+  CopyPlan<T, TX, TY> cpl;
+  cpl.init(v, x0, y0);
+  auto zoff = [&](int z) { return (long long)wrapm(z, v.nz) * plane; };
+  cpl.issue(&sm.pos[0][0][0], zoff(z0 - 1));
   cp_async_commit();
-  load_plane<SM, T, TX, TY>(sm, 1, v, z0, x0, y0);
+  cpl.issue(&sm.pos[1][0][0], zoff(z0));
   cp_async_commit();
-  load_plane<SM, T, TX, TY>(sm, 2, v, z0 + 1, x0, y0);
+  cpl.issue(&sm.pos[2][0][0], zoff(z0 + 1));
   cp_async_commit();
   cp_async_wait1();
   __syncthreads();
@@ -196,7 +210,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       T sn, cs;
-      sincos_t<T>(dx * sm.pos[0][6 + 3 * s][a], &sn, &cs);
+      link_sincos<T>(dx * sm.pos[0][6 + 3 * s][a], &sn, &cs);
       transport_bwd<T>(cs, sn, sm.pos[0][2 * s][a], sm.pos[0][2 * s + 1][a], &cP2r[s], &cP2i[s]);
       const T* A0 = sm.pos[0][4 + 3 * s];
       const T* A1 = sm.pos[0][5 + 3 * s];
@@ -212,7 +226,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
     const int it = z - z0;
     const int bc = (it + 1) % 3, bn = (it + 2) % 3, bf = it % 3;
     __syncthreads();  // everyone is done with buffer bf (plane z-1)
-    if (z + 2 <= z1) load_plane<SM, T, TX, TY>(sm, bf, v, z + 2, x0, y0);
+    if (z + 2 <= z1) cpl.issue(&sm.pos[bf][0][0], zoff(z + 2));
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
@@ -247,7 +261,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
       const T* A1 = sm.pos[bc][5 + 3 * s];
       const T* A2 = sm.pos[bc][6 + 3 * s];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) sincos_t<T>(dx * sm.pos[bc][4 + 3 * s + i][a], &sn_[s][i], &cs_[s][i]);
+      for (int i = 0; i < 3; ++i) link_sincos<T>(dx * sm.pos[bc][4 + 3 * s + i][a], &sn_[s][i], &cs_[s][i]);
       T pr0, pi0, pr1, pi1;
       transport_bwd<T>(cs_[s][0], sn_[s][0], fr[a], fi[a], &pr0, &pi0);
       transport_bwd<T>(cs_[s][1], sn_[s][1], fr[a], fi[a], &pr1, &pi1);
@@ -282,7 +296,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
         const T* A2 = sm.pos[bc][6 + 3 * s];
         const int d = left ? 0 : 1;
         T sn, cs, br, bi;
-        sincos_t<T>(dx * sm.pos[bc][4 + 3 * s + d][ha], &sn, &cs);
+        link_sincos<T>(dx * sm.pos[bc][4 + 3 * s + d][ha], &sn, &cs);
         transport_bwd<T>(cs, sn, fr[ha], fi[ha], &br, &bi);
         sm.P[s][d][0][ha] = br;
         sm.P[s][d][1][ha] = bi;

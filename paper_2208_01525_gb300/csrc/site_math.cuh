@@ -15,6 +15,45 @@ template <typename T> __device__ __forceinline__ void sincos_t(T x, T* s, T* c);
 template <> __device__ __forceinline__ void sincos_t<float>(float x, float* s, float* c) { sincosf(x, s, c); }
 template <> __device__ __forceinline__ void sincos_t<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
+// cos and sin of a link angle theta = dx A.  FP32: Cody & Waite (1980)
+// reduction theta = k pi/2 + r, |r| <= pi/4, with pi/2 split into three
+// floats (P1 = fl(pi/2), P2 = fl(pi/2 - P1), P3 = fl(pi/2 - P1 - P2)) and
+// fused multiply-adds, then the Taylor series of sin r to r^9 and cos r to
+// r^10 (truncation below 2e-9) and the quadrant rotation by k mod 4.
+// Angles beyond +-4096 (far outside what a lattice reaches) take the
+// library sincosf.  FP64 uses the library sincos.
+__device__ __forceinline__ void link_sincos_f32(float x, float* sp, float* cp) {
+  if (fabsf(x) > 4096.0f) {
+    sincosf(x, sp, cp);
+    return;
+  }
+  const float k = rintf(x * 0.636619746685028076f);
+  float r = fmaf(-k, 1.57079637050628662f, x);
+  r = fmaf(-k, -4.37113882867379300e-08f, r);
+  r = fmaf(-k, -1.71512451000588190e-15f, r);
+  const float r2 = r * r;
+  const float ps = fmaf(r2, fmaf(r2, fmaf(r2, 2.75573188446287530e-06f, -1.98412701138295233e-04f),
+                                 8.33333376795053482e-03f),
+                        -0.166666671633720398f);
+  const float sr = fmaf(r * r2, ps, r);
+  const float pc = fmaf(r2, fmaf(r2, fmaf(r2, fmaf(r2, -2.75573199814971304e-07f, 2.48015876422869042e-05f),
+                                          -1.38888892251998186e-03f),
+                                 4.16666679084300995e-02f),
+                        -0.5f);
+  const float cr = fmaf(r2, pc, 1.0f);
+  const int q = (int)k;
+  float sv = (q & 1) ? cr : sr;
+  float cv = (q & 1) ? sr : cr;
+  *sp = (q & 2) ? -sv : sv;
+  *cp = ((q + 1) & 2) ? -cv : cv;
+}
+
+template <typename T> __device__ __forceinline__ void link_sincos(T x, T* s, T* c);
+template <> __device__ __forceinline__ void link_sincos<float>(float x, float* s, float* c) {
+  link_sincos_f32(x, s, c);
+}
+template <> __device__ __forceinline__ void link_sincos<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
 template <typename T> __device__ __forceinline__ T atan2_t(T y, T x);
 template <> __device__ __forceinline__ float atan2_t<float>(float y, float x) { return atan2f(y, x); }
 template <> __device__ __forceinline__ double atan2_t<double>(double y, double x) { return atan2(y, x); }

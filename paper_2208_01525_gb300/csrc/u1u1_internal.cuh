@@ -113,10 +113,14 @@ template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
                          cudaStream_t st);
 
-// Cells and overlap from face bytes.
+// Cells and overlap from face bytes; masks holds 2 * cell_mask_words words.
 int cells_grid_blocks();
+size_t cell_mask_words(int nx, int ny, int nz);
 cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p,
-                         uint8_t* cell_q, CellPartial* part, cudaStream_t st);
+                         uint8_t* cell_q, uint32_t* masks, CellPartial* part, cudaStream_t st);
+
+// The FP32 link-phase routine on n values (check entry point).
+cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n, cudaStream_t st);
 
 // Merge partials into a record.
 cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart,

@@ -339,3 +339,24 @@ def test_edge_cases_and_errors():
     recs, lost = lat.read_records(max_records=2000)
     assert len(recs) == 1024 and lost == 1100 - 1024
     assert recs[-1][0]["n"] == 1099
+
+
+def test_link_phase_routine_accuracy():
+    """The FP32 cos/sin of link angles (Cody-Waite reduction + Taylor series)
+    stays within 2 ulp-scale (2.4e-7 absolute) of the double-precision values
+    over the angle range lattices reach, and handles the far-range fallback."""
+    import ctypes
+    th64 = torch.cat([torch.linspace(-50.0, 50.0, 2_000_001, dtype=torch.float64),
+                      torch.tensor([0.0, -0.0, 1e-30, 3.0e3, -4095.0, 4097.0, 1.0e5, -2.5e6],
+                                   dtype=torch.float64)])
+    th = th64.float().cuda()
+    sn = torch.empty_like(th)
+    cs = torch.empty_like(th)
+    U.check(U.lib().u1u1_eval_link_phase(ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(sn.data_ptr()),
+                                         ctypes.c_void_p(cs.data_ptr()), th.numel(),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.cuda.synchronize()
+    ref = th.double()
+    es = (sn.double() - torch.sin(ref)).abs().max().item()
+    ec = (cs.double() - torch.cos(ref)).abs().max().item()
+    assert es < 2.4e-7 and ec < 2.4e-7, (es, ec)
