@@ -469,8 +469,10 @@ static void to_diag(const u1u1_params* p, const RawRecord& r, u1u1_diag* d) {
   d->mag_q = r.sum[S_MAG_Q];
   d->pot = r.sum[S_POT];
   d->vint = r.sum[S_VINT];
-  d->lag = r.sum[S_LAG];
-  d->energy = r.sum[S_ENERGY];
+  // the Lagrangian and energy densities are linear in the component
+  // densities, so their lattice sums are formed from the component sums
+  d->lag = (d->kin_p - d->grad_p + d->el_p - d->mag_p) + (d->kin_q - d->grad_q + d->el_q - d->mag_q) - d->pot;
+  d->energy = (d->kin_p + d->grad_p + d->el_p + d->mag_p) + (d->kin_q + d->grad_q + d->el_q + d->mag_q) + d->pot;
   d->rl_num = r.sum[S_RL_NUM];
   d->rl_den = r.sum[S_RL_DEN];
   d->rpq_num = r.sum[S_RPQ_NUM];

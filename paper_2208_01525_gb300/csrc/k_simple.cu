@@ -173,7 +173,6 @@ k_simple(LatticeView<T> v, Coef<T> c, MeasureOut mo) {
       T pot = c.cV * (c.lam4[0] * rp * rp + c.lam4[1] * rq * rq - c.kappa * rp * rq);
       T vint = c.kappa * rp * rq;
       T L = (d[0].kin - d[0].grad + d[0].el - d[0].mag) + (d[1].kin - d[1].grad + d[1].el - d[1].mag) - pot;
-      T H = (d[0].kin + d[0].grad + d[0].el + d[0].mag) + (d[1].kin + d[1].grad + d[1].el + d[1].mag) + pot;
       T kt = d[0].kin + d[1].kin, gt = d[0].grad + d[1].grad;
       acc.s[S_KIN_P] += (double)d[0].kin;
       acc.s[S_KIN_Q] += (double)d[1].kin;
@@ -185,8 +184,6 @@ k_simple(LatticeView<T> v, Coef<T> c, MeasureOut mo) {
       acc.s[S_MAG_Q] += (double)d[1].mag;
       acc.s[S_POT] += (double)pot;
       acc.s[S_VINT] += (double)vint;
-      acc.s[S_LAG] += (double)L;
-      acc.s[S_ENERGY] += (double)H;
       acc.s[S_RL_NUM] += (double)(kt * L);
       acc.s[S_RL_DEN] += (double)(gt * L);
       acc.s[S_RPQ_NUM] += (double)(kt * vint);

@@ -43,37 +43,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// Per-thread accumulation of the diagnostic sums: compensated FP32 pairs for
-// the FP32 kernel (cheap on the FP32 pipes; converted to FP64 at the end of
-// the chunk), plain FP64 for the FP64 kernel.
-template <typename T>
-struct SumAcc;
-template <>
-struct SumAcc<float> {
-  float s[16], c[16];
-  __device__ void zero() {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) s[k] = c[k] = 0.f;
-  }
-  __device__ __forceinline__ void add(int k, float v) {
-    float y = v - c[k];
-    float t = s[k] + y;
-    c[k] = (t - s[k]) - y;
-    s[k] = t;
-  }
-  __device__ double get(int k) const { return (double)s[k] - (double)c[k]; }
-};
-template <>
-struct SumAcc<double> {
-  double s[16];
-  __device__ void zero() {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) s[k] = 0.0;
-  }
-  __device__ __forceinline__ void add(int k, double v) { s[k] += v; }
-  __device__ double get(int k) const { return s[k]; }
-};
-
 template <typename T, int TX, int TY>
 struct Tile {
   static constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte chunk
@@ -100,6 +69,7 @@ struct Smem {
   T chi[2][3][PM];                     // [sector][dir] edge phases (detection)
   T Eg[2][2][PG];                      // [sector][dir 0,1] E for the Gauss divergence
   uint8_t chif[2][PM];                 // [sector] branch-cut flags, bit i per dir
+  double wsum[MEAS ? TL::NT / 32 : 1][NSUM];  // per-warp FP64 running sums (detection)
 };
 
 // Copy plan of one thread: every copy moves one 16-byte chunk of one row of
@@ -155,8 +125,56 @@ __device__ __forceinline__ T chi_at(const SM& sm, int s, int d, int b, int bn, i
   return edge_chi<T>(ar * fr + ai * fi, ar * fi - ai * fr, cut);
 }
 
+// Finish the windings of the plane below: W_02 and W_12 from their partial
+// sums and the own edge phases chi_0, chi_1 (c0n, c1n, flags f0n) of the
+// plane above, then count and emit all three plaquettes of both sectors.
+template <typename T>
+__device__ __forceinline__ void emit_windings(const int W01[2], const T S02[2], const T S12[2], const unsigned cut[2],
+                                              const T c0n[2], const T c1n[2], const unsigned f0n[2], long long gs,
+                                              int* cnt, const MeasureOut& mo, long long V) {
+  int W[2][3];
+  bool ck[2][3];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    W[s][0] = W01[s];
+    W[s][1] = (int)rint_t<T>((S02[s] - c0n[s]) * Consts<T>::inv_two_pi());
+    W[s][2] = (int)rint_t<T>((S12[s] - c1n[s]) * Consts<T>::inv_two_pi());
+    ck[s][0] = (cut[s] & 1u) != 0;
+    ck[s][1] = (cut[s] & 2u) != 0 || (f0n[s] & 1u) != 0;
+    ck[s][2] = (cut[s] & 4u) != 0 || (f0n[s] & 2u) != 0;
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    unsigned byte = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int aw = abs(W[s][k]);
+      cnt[s == 0 ? C_NP : C_NQ] += aw;
+      cnt[s == 0 ? C_NZP : C_NZQ] += (aw != 0);
+      cnt[C_FLAGGED] += ck[s][k] ? 1 : 0;
+      cnt[C_MAXW] = max(cnt[C_MAXW], aw);
+      byte |= (unsigned)min(aw, 3) << FACE_SHIFT(k);
+      if (ck[s][k]) byte |= FACE_FLAG;
+      if (mo.windings) mo.windings[(3 * s + k) * V + gs] = (int8_t)max(-127, min(127, W[s][k]));
+    }
+    if (mo.faces) mo.faces[s * V + gs] = (uint8_t)byte;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cnt[C_NPQ_PLAQ] += (W[0][k] != 0 && W[1][k] != 0) ? 1 : 0;
+}
+
+// Halo point handled by thread tid, or -1: the TX + TY halo points of a
+// plane are spread evenly over the CTA's warps so that no warp carries all
+// of the extra work between two barriers.
+template <int NT, int NH>
+__device__ __forceinline__ int halo_point(int tid) {
+  static_assert(NH <= NT, "more halo points than threads");
+  const int h = (tid * NH + NT - 1) / NT;
+  return (h < NH && (h * NT) / NH == tid) ? h : -1;
+}
+
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX* TY, (MODE == MODE_WRITE && sizeof(T) == 4) ? 3 : 1)
+__global__ void __launch_bounds__(TX* TY, sizeof(T) == 8 ? 1 : (MODE == MODE_WRITE ? 3 : 2))
 k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
   using TL = Tile<T, TX, TY>;
   constexpr bool WRITE = (MODE & MODE_WRITE) != 0;
@@ -178,14 +196,20 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
   const long long V = plane * v.nz;
   const T dx = c.dx;
 
-  SumAcc<T> acc;
-  double mx[NMAX];
+  T mx[NMAX];
   int cnt[NCNT];
-  double gauss_abs[2] = {0.0, 0.0}, charge_abs[2] = {0.0, 0.0};
+  // windings of plane z-1 whose (x,z) and (y,z) plaquettes still need the
+  // edge phases of plane z: W_01, the partial sums of W_02 and W_12 and the
+  // branch-cut bits, per sector
+  int pW01[2] = {0, 0};
+  T pS02[2] = {T(0), T(0)}, pS12[2] = {T(0), T(0)};
+  unsigned pcut[2] = {0u, 0u};
+  long long pgsite = -1;
   if (MEAS) {
-    acc.zero();
+    if ((tid & 31) == 0)
+      for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = 0.0;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;
+    for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;  // -inf is representable in T
 #pragma unroll
     for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
   }
@@ -225,11 +249,15 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
   for (int z = z0; z < z1; ++z) {
     const int it = z - z0;
     const int bc = (it + 1) % 3, bn = (it + 2) % 3, bf = it % 3;
-    __syncthreads();  // everyone is done with buffer bf (plane z-1)
-    if (z + 2 <= z1) cpl.issue(&sm.pos[bf][0][0], zoff(z + 2));
-    cp_async_commit();
-    cp_async_wait1();
+    // plane z+1 (the only copy group in flight) has landed; after the barrier
+    // every thread is done with iteration z-1, so buffer bf (plane z-1) and
+    // the per-plane shared arrays may be overwritten
+    cp_async_wait0();
     __syncthreads();
+    if (z + 2 <= z1) {
+      cpl.issue(&sm.pos[bf][0][0], zoff(z + 2));
+      cp_async_commit();
+    }
 
     const long long gsite = (long long)z * plane + (long long)gy * v.nx + gx;
     // momenta of the own site (plain loads; consumed after phase 1)
@@ -282,7 +310,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
       }
     }
     // halo points: left column (lx = -1) and bottom row (ly = -1)
-    for (int h = tid; h < TX + TY; h += TL::NT) {
+    if (const int h = halo_point<TL::NT, TX + TY>(tid); h >= 0) {
       const bool left = h < TY;
       const int hy = left ? h : -1;
       const int hx = left ? -1 : h - TY;
@@ -344,7 +372,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
         }
         sm.chif[s][a] = fl;
       }
-      for (int h = tid; h < TX + TY; h += TL::NT) {
+      if (const int h = halo_point<TL::NT, TX + TY>(tid); h >= 0) {
         const bool right = h < TY;
         const int hy = right ? h : TY;
         const int hx = right ? TX : h - TY;
@@ -365,6 +393,11 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
     __syncthreads();
 
     // ---- phase 2: assemble the update of the own site ----
+    T tv[NSUM];  // this site's diagnostic densities (zero when inactive)
+    if (MEAS) {
+#pragma unroll
+      for (int k = 0; k < NSUM; ++k) tv[k] = T(0);
+    }
     if (active) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
@@ -413,27 +446,26 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
         const T pot = c.cV * (c.lam4[0] * rp * rp + c.lam4[1] * rq * rq - c.kappa * rp * rq);
         const T vint = c.kappa * rp * rq;
         const T L = (d[0].kin - d[0].grad + d[0].el - d[0].mag) + (d[1].kin - d[1].grad + d[1].el - d[1].mag) - pot;
-        const T H = (d[0].kin + d[0].grad + d[0].el + d[0].mag) + (d[1].kin + d[1].grad + d[1].el + d[1].mag) + pot;
         const T kt = d[0].kin + d[1].kin, gt = d[0].grad + d[1].grad;
-        acc.add(S_KIN_P, d[0].kin);
-        acc.add(S_KIN_Q, d[1].kin);
-        acc.add(S_GRAD_P, d[0].grad);
-        acc.add(S_GRAD_Q, d[1].grad);
-        acc.add(S_EL_P, d[0].el);
-        acc.add(S_EL_Q, d[1].el);
-        acc.add(S_MAG_P, d[0].mag);
-        acc.add(S_MAG_Q, d[1].mag);
-        acc.add(S_POT, pot);
-        acc.add(S_VINT, vint);
-        acc.add(S_LAG, L);
-        acc.add(S_ENERGY, H);
-        acc.add(S_RL_NUM, kt * L);
-        acc.add(S_RL_DEN, gt * L);
-        acc.add(S_RPQ_NUM, kt * vint);
-        acc.add(S_RPQ_DEN, gt * vint);
+        // the Lagrangian and energy sums are formed from the component sums
+        // on the host; only the weighted sums of Eq. 37 need L per site
+        tv[S_KIN_P] = d[0].kin;
+        tv[S_KIN_Q] = d[1].kin;
+        tv[S_GRAD_P] = d[0].grad;
+        tv[S_GRAD_Q] = d[1].grad;
+        tv[S_EL_P] = d[0].el;
+        tv[S_EL_Q] = d[1].el;
+        tv[S_MAG_P] = d[0].mag;
+        tv[S_MAG_Q] = d[1].mag;
+        tv[S_POT] = pot;
+        tv[S_VINT] = vint;
+        tv[S_RL_NUM] = kt * L;
+        tv[S_RL_DEN] = gt * L;
+        tv[S_RPQ_NUM] = kt * vint;
+        tv[S_RPQ_DEN] = gt * vint;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const double m = (double)sqrt(mod2[s]);
+          const T m = sqrt(mod2[s]);
           mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q] = fmax(mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q], -m);
           mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q] = fmax(mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q], m);
         }
@@ -454,49 +486,46 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
             div *= c.inv_dx;
             const T rho = c.qG[s] * (in[s].fr * pim[s] - in[s].fi * pr[s]);
             const T G = div - rho;
-            mx[s == 0 ? M_GAUSS_P : M_GAUSS_Q] = fmax(mx[s == 0 ? M_GAUSS_P : M_GAUSS_Q], fabs((double)G));
-            gauss_abs[s] += fabs((double)G);
-            charge_abs[s] += fabs((double)rho);
+            mx[s == 0 ? M_GAUSS_P : M_GAUSS_Q] = fmax(mx[s == 0 ? M_GAUSS_P : M_GAUSS_Q], fabs(G));
+            tv[s == 0 ? S_GAUSS_P : S_GAUSS_Q] = fabs(G);
+            tv[s == 0 ? S_CHARGE_P : S_CHARGE_Q] = fabs(rho);
           }
         }
 
-        // plaquette windings (Sec. III.A)
-        int W[2][3];
-        bool cutk[2][3];
+        // plaquette windings (Sec. III.A).  The (x,y) plaquette of plane z is
+        // complete now; the (x,z) and (y,z) ones need the edge phases of
+        // plane z+1, which this thread computes as its own at the next
+        // iteration, so they are finished (and plane z emitted) there.
+        const T c0n[2] = {sm.chi[0][0][a], sm.chi[1][0][a]};
+        const T c1n[2] = {sm.chi[0][1][a], sm.chi[1][1][a]};
+        const unsigned f0n[2] = {sm.chif[0][a], sm.chif[1][a]};
+        if (pgsite >= 0) emit_windings(pW01, pS02, pS12, pcut, c0n, c1n, f0n, pgsite, cnt, mo, V);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const T c0 = sm.chi[s][0][a], c1 = sm.chi[s][1][a], c2 = sm.chi[s][2][a];
-          const uint8_t f0 = sm.chif[s][a];
+          const T c0 = c0n[s], c1 = c1n[s], c2 = sm.chi[s][2][a];
+          const unsigned f0 = f0n[s];
           const int ax = TL::at(ly, lx + 1), ay = TL::at(ly + 1, lx);
-          bool n0 = false, n1 = false;
-          const T c0z = chi_at<SM, T, TX, TY>(sm, s, 0, bn, bn, ly, lx, 0, 1, dx, &n0);
-          const T c1z = chi_at<SM, T, TX, TY>(sm, s, 1, bn, bn, ly, lx, 1, 0, dx, &n1);
-          W[s][0] = plaquette_winding<T>(c0, sm.chi[s][1][ax], sm.chi[s][0][ay], c1, dx, in[s].F[0]);
-          W[s][1] = plaquette_winding<T>(c0, sm.chi[s][2][ax], c0z, c2, dx, in[s].F[1]);
-          W[s][2] = plaquette_winding<T>(c1, sm.chi[s][2][ay], c1z, c2, dx, in[s].F[2]);
-          const uint8_t fx = sm.chif[s][ax], fy = sm.chif[s][ay];
-          cutk[s][0] = (f0 & 3u) || (fx & 2u) || (fy & 1u);
-          cutk[s][1] = (f0 & 5u) || (fx & 4u) || n0;
-          cutk[s][2] = (f0 & 6u) || (fy & 4u) || n1;
+          pW01[s] = plaquette_winding<T>(c0, sm.chi[s][1][ax], sm.chi[s][0][ay], c1, dx, in[s].F[0]);
+          pS02[s] = (c0 + sm.chi[s][2][ax]) - c2 + dx * in[s].F[1];
+          pS12[s] = (c1 + sm.chi[s][2][ay]) - c2 + dx * in[s].F[2];
+          const unsigned fx = sm.chif[s][ax], fy = sm.chif[s][ay];
+          pcut[s] = (((f0 & 3u) || (fx & 2u) || (fy & 1u)) ? 1u : 0u) |
+                    (((f0 & 5u) || (fx & 4u)) ? 2u : 0u) | (((f0 & 6u) || (fy & 4u)) ? 4u : 0u);
         }
+        pgsite = gsite;
+      }
+    }
+    if (MEAS) {
+      // one row of 32 sites per warp: reduce the plane's densities across the
+      // warp in FP32 and add them to the warp's FP64 running sums
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          unsigned byte = 0;
+      for (int k = 0; k < NSUM; ++k) {
+        if (k == S_LAG || k == S_ENERGY) continue;
+        if (!GAUSS && (k == S_GAUSS_P || k == S_GAUSS_Q || k == S_CHARGE_P || k == S_CHARGE_Q)) continue;
+        T v2 = tv[k];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int aw = abs(W[s][k]);
-            cnt[s == 0 ? C_NP : C_NQ] += aw;
-            cnt[s == 0 ? C_NZP : C_NZQ] += (aw != 0);
-            cnt[C_FLAGGED] += cutk[s][k] ? 1 : 0;
-            cnt[C_MAXW] = max(cnt[C_MAXW], aw);
-            byte |= (unsigned)min(aw, 3) << FACE_SHIFT(k);
-            if (cutk[s][k]) byte |= FACE_FLAG;
-            if (mo.windings) mo.windings[(3 * s + k) * V + gsite] = (int8_t)max(-127, min(127, W[s][k]));
-          }
-          if (mo.faces) mo.faces[s * V + gsite] = (uint8_t)byte;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) cnt[C_NPQ_PLAQ] += (W[0][k] != 0 && W[1][k] != 0) ? 1 : 0;
+        for (int o = 16; o > 0; o >>= 1) v2 += __shfl_down_sync(0xffffffffu, v2, o);
+        if ((tid & 31) == 0) sm.wsum[tid >> 5][k] += (double)v2;
       }
     }
     // carries for plane z+1
@@ -512,15 +541,25 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
   cp_async_wait0();
 
   if (MEAS) {
+    if (active && pgsite >= 0) {
+      // edge phases of plane z1 (still in the ring) finish the last plane
+      const int bl = (z1 - z0 + 1) % 3;
+      T c0n[2], c1n[2];
+      unsigned f0n[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        bool n0 = false, n1 = false;
+        c0n[s] = chi_at<SM, T, TX, TY>(sm, s, 0, bl, bl, ly, lx, 0, 1, dx, &n0);
+        c1n[s] = chi_at<SM, T, TX, TY>(sm, s, 1, bl, bl, ly, lx, 1, 0, dx, &n1);
+        f0n[s] = (n0 ? 1u : 0u) | (n1 ? 2u : 0u);
+      }
+      emit_windings(pW01, pS02, pS12, pcut, c0n, c1n, f0n, pgsite, cnt, mo, V);
+    }
     ThreadAcc ta;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) ta.s[k] = acc.get(k);
-    ta.s[S_GAUSS_P] = gauss_abs[0];
-    ta.s[S_GAUSS_Q] = gauss_abs[1];
-    ta.s[S_CHARGE_P] = charge_abs[0];
-    ta.s[S_CHARGE_Q] = charge_abs[1];
+    for (int k = 0; k < NSUM; ++k) ta.s[k] = ((tid & 31) == 0) ? sm.wsum[tid >> 5][k] : 0.0;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) ta.mx[k] = mx[k];
+    for (int k = 0; k < NMAX; ++k) ta.mx[k] = (double)mx[k];
 #pragma unroll
     for (int k = 0; k < NCNT; ++k) ta.cnt[k] = cnt[k];
     __syncthreads();
