@@ -157,6 +157,45 @@ def run_reference(args):
     return 0
 
 
+def ensemble_bench(U, torch, dev):
+    """The batched configuration: 48 independent boxes (16 x 64^3, 16 x 128^3,
+    16 x 192^3), matter era, beta cycling 1, 0, -1, seeds 1000 + b, each run
+    to half its light-crossing time (160 / 320 / 480 steps), FP32.  Each mode
+    is timed on its second run (the first one captures the graph)."""
+    sizes = [64] * 16 + [128] * 16 + [192] * 16
+    steps = [n * 5 // 2 for n in sizes]  # n dx / 2 in units of deta = 0.1
+    ps = []
+    for b, n in enumerate(sizes):
+        beta = (1.0, 0.0, -1.0)[b % 3]
+        eta_end = 1.0 + 0.1 * 2 * steps[b]
+        ps.append(U.Params.cube(n, m=2.0 / 3.0, beta=beta, eta0=1.0, eta_ref=eta_end if beta > 0 else 1.0,
+                                seed=1000 + b, precision=U.FP32))
+    work = sum(s * n ** 3 for s, n in zip(steps, sizes))
+    out = {"boxes": len(sizes), "site_updates_per_run": work, "steps": "160/320/480", "era": "matter",
+           "beta": "1,0,-1 round-robin"}
+    stream = torch.cuda.current_stream()
+    for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True),
+                              ("per_step_graph", U.ENS_PER_STEP, True),
+                              ("unbatched", U.ENS_UNBATCHED, False)):
+        ens = U.Ensemble(ps, device=dev, horizon=2048)
+        ens.run(steps, mode=mode, use_graph=graph)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.run(steps, mode=mode, use_graph=graph)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        status = ens.status()
+        ens.close()
+        del ens
+        torch.cuda.empty_cache()
+        out[name] = {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": status}
+    out["speedup_vs_unbatched"] = out["persistent_graph"]["site_updates_per_s"] / \
+        out["unbatched"]["site_updates_per_s"]
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -279,6 +318,10 @@ def run_ours(args):
             del lat64
             torch.cuda.empty_cache()
 
+    ens = None
+    if args.ensemble:
+        ens = ensemble_bench(U, torch, dev)
+
     cpu = None
     if rank == 0 and args.cpu:
         v, dt, cores = cpu_baseline(args.cpu_n)
@@ -305,6 +348,7 @@ def run_ours(args):
             "gpu_launches": args.steps * (de + 2),
             "e2e": e2e,
             "fp64": fp64,
+            "ensemble": ens,
             "cpu_baseline": cpu,
             "records_lost": lost,
             "last_record": None if last is None else {
@@ -333,6 +377,7 @@ def main():
     ap.add_argument("--ref-n", type=int, default=96)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--no-ensemble", dest="ensemble", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

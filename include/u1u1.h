@@ -266,6 +266,56 @@ int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
 int u1u1_set_kernel(u1u1_lattice* h, int kernel);
 int u1u1_get_kernel(const u1u1_lattice* h, int* kernel);
 
+/* ---- ensembles of independent boxes ---------------------------------------- */
+
+/* How u1u1_ensemble_run schedules the boxes' steps. */
+#define U1U1_ENS_PERSISTENT 0 /* one persistent launch covers every step of every box */
+#define U1U1_ENS_PER_STEP 1   /* one launch per step covering all boxes still running */
+#define U1U1_ENS_UNBATCHED 2  /* one launch per box per step, box after box (reference loop) */
+
+/* Create an ensemble of nboxes independent lattices (SURVEY-style batched
+ * realisations, e.g. uneven box sizes, eras, beta and seeds): per_box[b] and
+ * buffers[b] are as for u1u1_init_lattice, every box gets its random-phase
+ * initial conditions on `stream`, and all boxes share one precision.
+ * horizon (0 = 8192) bounds the step index any box may reach; the per-step
+ * coefficients of every box up to it are tabulated on the device at
+ * creation.  Errors: INVALID_ARG, BAD_BUFFER, OUT_OF_MEMORY, CUDA. */
+int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, const u1u1_buffers* buffers, int horizon,
+                         void* stream, u1u1_ensemble** out);
+
+/* Advance box b by steps[b] >= 0 plain leapfrog steps (Eqs. 17-26), all
+ * boxes together, scheduled by `mode`.  In U1U1_ENS_PERSISTENT mode one
+ * launch of about as many CTAs as fit on the GPU takes (box, step, tile)
+ * work items from an ordered ticket counter; an item of step k of a box waits
+ * until every item of step k-1 of that box is done (bounded wait: after the
+ * limit set by u1u1_ensemble_set_wait_limit the kernel records
+ * U1U1_ERR_TIMEOUT, read with u1u1_ensemble_status, and returns).  With
+ * use_graph != 0 the work of this (steps, mode) pair is captured once into a
+ * CUDA graph and replayed on later calls with the same pair.  Asynchronous
+ * on `stream`.  Errors: INVALID_ARG, STATE (step horizon reached, or an
+ * earlier run timed out), CUDA. */
+int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int mode, int use_graph, void* stream);
+
+/* Borrow the handle of box b (for detection, diagnostics, state transfer);
+ * it stays owned by the ensemble and valid until u1u1_ensemble_destroy. */
+int u1u1_ensemble_lattice(u1u1_ensemble* e, int box, u1u1_lattice** h);
+
+/* Device status word of the last persistent run: U1U1_OK or
+ * U1U1_ERR_TIMEOUT.  Synchronises `stream`. */
+int u1u1_ensemble_status(u1u1_ensemble* e, int* status, void* stream);
+
+/* Wait limit of the persistent kernel's per-item dependency wait, in
+ * nanoseconds (default 2e9). */
+int u1u1_ensemble_set_wait_limit(u1u1_ensemble* e, int64_t ns);
+
+/* Fault injection for tests of the bounded wait: when enabled, the first
+ * work item of step 1 of the first box in the next persistent run waits for
+ * a completion count that is never reached, so the run ends with
+ * U1U1_ERR_TIMEOUT after the wait limit instead of hanging. */
+int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enable);
+
+void u1u1_ensemble_destroy(u1u1_ensemble* e);
+
 /* ---- check entry points ---------------------------------------------------- */
 
 /* Evaluate, on n device values theta, the FP32 routine the kernels use for

@@ -13,10 +13,10 @@ import math
 from dataclasses import dataclass, fields
 
 from . import _abi
-from ._abi import (FP32, FP64, KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, NFIELDS, NMOM, NPOS,  # noqa: F401
-                   U1U1Error, check, lib)
+from ._abi import (ENS_PER_STEP, ENS_PERSISTENT, ENS_UNBATCHED, FP32, FP64, KERNEL_AUTO,  # noqa: F401
+                   KERNEL_SIMPLE, KERNEL_TILED, NFIELDS, NMOM, NPOS, U1U1Error, check, lib)
 
-__all__ = ["Params", "Lattice", "U1U1Error", "FP32", "FP64", "KERNEL_AUTO", "KERNEL_SIMPLE",
+__all__ = ["Params", "Lattice", "Ensemble", "U1U1Error", "FP32", "FP64", "KERNEL_AUTO", "KERNEL_SIMPLE",
            "KERNEL_TILED", "coefficients", "version", "lib"]
 
 
@@ -95,7 +95,7 @@ class Lattice:
     """
 
     def __init__(self, params: Params, device="cuda", init: bool = True, stream=None,
-                 kernel: int = KERNEL_AUTO):
+                 kernel: int = KERNEL_AUTO, _borrow=None):
         import torch
         check_params(params)
         if not torch.cuda.is_available():
@@ -103,16 +103,13 @@ class Lattice:
         self.params = params
         self.device = torch.device(device)
         self.dtype = torch.float64 if params.precision == FP64 else torch.float32
-        V = params.nsites
-        self.pos = [[torch.empty(V, dtype=self.dtype, device=self.device) for _ in range(NPOS)]
-                    for _ in range(2)]
-        self.mom = [torch.empty(V, dtype=self.dtype, device=self.device) for _ in range(NMOM)]
-        self._bufs = _abi.CBuffers()
-        for k in range(2):
-            for f in range(NPOS):
-                self._bufs.pos[k][f] = self.pos[k][f].data_ptr()
-        for f in range(NMOM):
-            self._bufs.mom[f] = self.mom[f].data_ptr()
+        self._owner = None
+        if _borrow is not None:  # a box of an Ensemble: tensors and handle belong to it
+            self.pos, self.mom, handle, self._owner = _borrow
+            self._bufs = None
+            self._h = handle
+            return
+        self.pos, self.mom, self._bufs = _alloc_fields(params, self.dtype, self.device)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             if init:
@@ -126,6 +123,9 @@ class Lattice:
 
     # -- lifecycle --
     def close(self):
+        if self._owner is not None:  # borrowed from an Ensemble
+            self._h = ctypes.c_void_p()
+            return
         if self._h:
             lib().u1u1_destroy(self._h)
             self._h = ctypes.c_void_p()
@@ -166,6 +166,8 @@ class Lattice:
     def set_state(self, st, n: int = 0):
         """Write a (20, nz, ny, nx) array (torch or numpy) into buffer 0 and reset
         the step index to n (the handle is re-attached)."""
+        if self._owner is not None:
+            raise U1U1Error(-8, "set_state re-attaches the handle; not available for ensemble boxes")
         import torch
         t = torch.as_tensor(st).to(device=self.device, dtype=self.dtype).reshape(NFIELDS, -1)
         for f in range(NPOS):
@@ -244,6 +246,82 @@ class Lattice:
 
     def load(self, path: str, stream=None):
         check(lib().u1u1_load(self._h, str(path).encode(), _stream_ptr(stream)))
+
+
+def _alloc_fields(params: Params, dtype, device):
+    import torch
+    V = params.nsites
+    pos = [[torch.empty(V, dtype=dtype, device=device) for _ in range(NPOS)] for _ in range(2)]
+    mom = [torch.empty(V, dtype=dtype, device=device) for _ in range(NMOM)]
+    bufs = _abi.CBuffers()
+    for k in range(2):
+        for f in range(NPOS):
+            bufs.pos[k][f] = pos[k][f].data_ptr()
+    for f in range(NMOM):
+        bufs.mom[f] = mom[f].data_ptr()
+    return pos, mom, bufs
+
+
+class Ensemble:
+    """Independent lattices of uneven size advanced together (u1u1_ensemble_*).
+
+    ``boxes[b]`` is a Lattice view of box b (detection, diagnostics, state);
+    its tensors and handle belong to the ensemble."""
+
+    def __init__(self, params_list, device="cuda", horizon: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise U1U1Error(-4, "no CUDA device: libu1u1 has no CPU path")
+        self.params = list(params_list)
+        self.device = torch.device(device)
+        nb = len(self.params)
+        cps = (_abi.CParams * nb)(*[p.c() for p in self.params])
+        bufs = (_abi.CBuffers * nb)()
+        fields = []
+        for b, p in enumerate(self.params):
+            check_params(p)
+            dtype = torch.float64 if p.precision == FP64 else torch.float32
+            pos, mom, cb = _alloc_fields(p, dtype, self.device)
+            bufs[b] = cb
+            fields.append((pos, mom))
+        self._fields = fields
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().u1u1_ensemble_create(cps, nb, bufs, int(horizon), _stream_ptr(stream), ctypes.byref(self._h)))
+        self.boxes = []
+        for b, p in enumerate(self.params):
+            hb = ctypes.c_void_p()
+            check(lib().u1u1_ensemble_lattice(self._h, b, ctypes.byref(hb)))
+            pos, mom = fields[b]
+            self.boxes.append(Lattice(p, device=device, _borrow=(pos, mom, hb, self)))
+
+    def run(self, steps, mode: int = ENS_PERSISTENT, use_graph: bool = False, stream=None):
+        arr = (ctypes.c_int * len(self.params))(*[int(s) for s in steps])
+        check(lib().u1u1_ensemble_run(self._h, arr, int(mode), int(bool(use_graph)), _stream_ptr(stream)))
+
+    def status(self, stream=None) -> int:
+        v = ctypes.c_int()
+        check(lib().u1u1_ensemble_status(self._h, ctypes.byref(v), _stream_ptr(stream)))
+        return v.value
+
+    def set_wait_limit(self, ns: int):
+        check(lib().u1u1_ensemble_set_wait_limit(self._h, int(ns)))
+
+    def inject_unreachable_wait(self, enable: bool = True):
+        check(lib().u1u1_ensemble_inject_unreachable_wait(self._h, int(bool(enable))))
+
+    def close(self):
+        if self._h:
+            for b in self.boxes:
+                b._h = ctypes.c_void_p()
+            lib().u1u1_ensemble_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 def nan_to_none(d: dict) -> dict:

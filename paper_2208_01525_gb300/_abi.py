@@ -21,6 +21,7 @@ FP32, FP64 = 0, 1
 NPOS, NMOM = 10, 10
 NFIELDS = NPOS + NMOM
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED = 0, 1, 2
+ENS_PERSISTENT, ENS_PER_STEP, ENS_UNBATCHED = 0, 1, 2
 
 
 class U1U1Error(RuntimeError):
@@ -108,6 +109,13 @@ PROTOTYPES = {
     "u1u1_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
     "u1u1_get_kernel": (ctypes.c_int, [_vp, _P(ctypes.c_int)]),
     "u1u1_eval_link_phase": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
+    "u1u1_ensemble_create": (ctypes.c_int, [_P(CParams), ctypes.c_int, _P(CBuffers), ctypes.c_int, _vp, _P(_vp)]),
+    "u1u1_ensemble_run": (ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_int, ctypes.c_int, _vp]),
+    "u1u1_ensemble_lattice": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp)]),
+    "u1u1_ensemble_status": (ctypes.c_int, [_vp, _P(ctypes.c_int), _vp]),
+    "u1u1_ensemble_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "u1u1_ensemble_inject_unreachable_wait": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "u1u1_ensemble_destroy": (None, [_vp]),
 }
 
 _lib = None

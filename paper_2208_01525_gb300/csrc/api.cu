@@ -11,11 +11,12 @@
 #include <string>
 
 #include "../../include/u1u1.h"
+#include "host_internal.h"
 #include "u1u1_internal.cuh"
 
 using namespace u1u1;
 
-namespace {
+namespace u1u1 {
 
 thread_local std::string g_last_error;
 
@@ -33,40 +34,13 @@ int cuda_fail(cudaError_t e, const char* where) {
   return fail(U1U1_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-#define U1U1_CUDA_TRY(expr, where)          \
-  do {                                      \
-    cudaError_t e_ = (expr);                \
-    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-  } while (0)
+}  // namespace u1u1
 
-constexpr int RING_CAP = 1024;
+namespace {
 constexpr double TWO_PI = 6.283185307179586476925286766559;
-
 }  // namespace
 
-struct u1u1_lattice {
-  u1u1_params p;
-  size_t V;
-  size_t esize;
-  void* pos[2][U1U1_NPOS];
-  void* mom[U1U1_NMOM];
-  int cur;
-  int64_t n;
-  int kernel;       // U1U1_KERNEL_*
-  int overlap_tol;
-  // scratch (owned)
-  uint8_t* faces;
-  uint32_t* masks;  // packed pierced-cell bits, two sectors
-  BlockPartial* partials;
-  int npartials;
-  CellPartial* cpartials;
-  int ncpartials;
-  RawRecord* ring;
-  RawRecord* scratch_rec;
-  RawRecord* host_rec;  // pinned, RING_CAP entries
-  int64_t rec_written;
-  int64_t rec_read;
-};
+
 
 // ---------------------------------------------------------------------------
 // parameters and coefficients
@@ -118,7 +92,7 @@ extern "C" int u1u1_check_params(const u1u1_params* p) {
   return U1U1_OK;
 }
 
-static void coeffs(const u1u1_params* p, int64_t n, double out[6]) {
+void u1u1::coeffs(const u1u1_params* p, int64_t n, double out[6]) {
   double eta = p->eta0 + (double)n * p->deta;
   double pm = (p->m == 0.0) ? 0.0 : p->m / (1.0 - p->m);
   double a = (pm == 0.0) ? 1.0 : pow(eta / p->eta_ref, pm);
@@ -158,7 +132,7 @@ extern "C" void u1u1_abi_sizes(size_t out[4]) {
 }
 
 template <typename T>
-static Coef<T> make_coef(const u1u1_params* p, int64_t n) {
+Coef<T> u1u1::make_coef(const u1u1_params* p, int64_t n) {
   double cf[6];
   coeffs(p, n, cf);
   const double c = cf[2], delta = cf[3], omega = cf[4];
@@ -218,7 +192,7 @@ static int check_buffers(const u1u1_params* p, const u1u1_buffers* b) {
   return U1U1_OK;
 }
 
-static void free_scratch(u1u1_lattice* h) {
+void u1u1::lattice_free_scratch(u1u1_lattice* h) {
   if (!h) return;
   cudaFree(h->faces);
   cudaFree(h->masks);
@@ -229,7 +203,7 @@ static void free_scratch(u1u1_lattice* h) {
   cudaFreeHost(h->host_rec);
 }
 
-static int create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out) {
+int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out) {
   int rc = u1u1_check_params(p);
   if (rc) return rc;
   if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
@@ -258,7 +232,7 @@ static int create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** ou
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->scratch_rec, sizeof(RawRecord));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_rec, sizeof(RawRecord) * RING_CAP);
   if (e != cudaSuccess) {
-    free_scratch(h);
+    lattice_free_scratch(h);
     free(h);
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? U1U1_ERR_OUT_OF_MEMORY : U1U1_ERR_CUDA,
@@ -283,24 +257,28 @@ static LatticeView<T> view(const u1u1_lattice* h) {
 }
 
 template <typename T>
-static cudaError_t init_fields(u1u1_lattice* h, cudaStream_t st) {
+static cudaError_t init_fields_t(u1u1_lattice* h, cudaStream_t st) {
   LatticeView<T> v = view<T>(h);
   T* pos1[U1U1_NPOS];
   for (int f = 0; f < U1U1_NPOS; ++f) pos1[f] = (T*)h->pos[1][f];
   return launch_init<T>(v, pos1, h->p.seed, h->p.sigma_p, h->p.sigma_q, st);
 }
 
+cudaError_t u1u1::lattice_init_fields(u1u1_lattice* h, cudaStream_t st) {
+  return h->esize == 8 ? init_fields_t<double>(h, st) : init_fields_t<float>(h, st);
+}
+
 extern "C" int u1u1_init_lattice(const u1u1_params* p, const u1u1_buffers* b, void* stream,
                                  u1u1_lattice** out) {
   u1u1_lattice* h = nullptr;
-  int rc = create(p, b, &h);
+  int rc = lattice_create(p, b, &h);
   if (rc) return rc;
   h->cur = 0;
   h->n = 0;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = h->esize == 8 ? init_fields<double>(h, st) : init_fields<float>(h, st);
+  cudaError_t e = lattice_init_fields(h, st);
   if (e != cudaSuccess) {
-    free_scratch(h);
+    lattice_free_scratch(h);
     free(h);
     return cuda_fail(e, "initial conditions");
   }
@@ -312,7 +290,7 @@ extern "C" int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, 
                                    u1u1_lattice** out) {
   if (current != 0 && current != 1) return fail(U1U1_ERR_INVALID_ARG, "current must be 0 or 1");
   u1u1_lattice* h = nullptr;
-  int rc = create(p, b, &h);
+  int rc = lattice_create(p, b, &h);
   if (rc) return rc;
   h->cur = current;
   h->n = n;
@@ -322,7 +300,7 @@ extern "C" int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, 
 
 extern "C" void u1u1_destroy(u1u1_lattice* h) {
   if (!h) return;
-  free_scratch(h);
+  lattice_free_scratch(h);
   free(h);
 }
 
@@ -700,3 +678,6 @@ extern "C" int u1u1_eval_link_phase(const float* theta, float* sin_out, float* c
   if (e != cudaSuccess) return cuda_fail(e, "link phase kernel");
   return U1U1_OK;
 }
+
+template Coef<float> u1u1::make_coef<float>(const u1u1_params*, int64_t);
+template Coef<double> u1u1::make_coef<double>(const u1u1_params*, int64_t);

@@ -1,0 +1,68 @@
+// Host-side internals shared by the C-ABI translation units (api.cu,
+// ensemble.cu): the lattice handle, error reporting and coefficients.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/u1u1.h"
+#include "u1u1_internal.cuh"
+
+namespace u1u1 {
+
+constexpr int RING_CAP = 1024;  // detection records kept on the device
+
+extern thread_local std::string g_last_error;
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* where);
+
+#define U1U1_CUDA_TRY(expr, where)                      \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return ::u1u1::cuda_fail(e_, where); \
+  } while (0)
+
+// step coefficients of step n (Eqs. 12, 19, 22), FP64
+void coeffs(const u1u1_params* p, int64_t n, double out[6]);
+// the kernels' coefficient block for step n
+template <typename T>
+Coef<T> make_coef(const u1u1_params* p, int64_t n);
+
+}  // namespace u1u1
+
+struct u1u1_lattice {
+  using BlockPartial = u1u1::BlockPartial;
+  using CellPartial = u1u1::CellPartial;
+  using RawRecord = u1u1::RawRecord;
+  u1u1_params p;
+  size_t V;
+  size_t esize;
+  void* pos[2][U1U1_NPOS];
+  void* mom[U1U1_NMOM];
+  int cur;
+  int64_t n;
+  int kernel;       // U1U1_KERNEL_*
+  int overlap_tol;
+  // scratch (owned)
+  uint8_t* faces;
+  uint32_t* masks;  // packed pierced-cell bits, two sectors
+  BlockPartial* partials;
+  int npartials;
+  CellPartial* cpartials;
+  int ncpartials;
+  RawRecord* ring;
+  RawRecord* scratch_rec;
+  RawRecord* host_rec;  // pinned, RING_CAP entries
+  int64_t rec_written;
+  int64_t rec_read;
+};
+
+namespace u1u1 {
+// validate, allocate the handle and its scratch (no kernel launched)
+int lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out);
+void lattice_free_scratch(u1u1_lattice* h);
+// enqueue the random-phase initial conditions into buffer 0 (and zero the rest)
+cudaError_t lattice_init_fields(u1u1_lattice* h, cudaStream_t st);
+}  // namespace u1u1

@@ -164,32 +164,39 @@ __device__ __forceinline__ void emit_windings(const int W01[2], const T S02[2], 
 }
 
 // Halo point handled by thread tid, or -1: the TX + TY halo points of a
-// plane are spread evenly over the CTA's warps so that no warp carries all
-// of the extra work between two barriers.
+// plane go to the first threads, so they cost one or two warp passes
+// (spreading them over all warps costs one pass per warp, measured slower).
 template <int NT, int NH>
 __device__ __forceinline__ int halo_point(int tid) {
   static_assert(NH <= NT, "more halo points than threads");
-  const int h = (tid * NH + NT - 1) / NT;
-  return (h < NH && (h * NT) / NH == tid) ? h : -1;
+  return tid < NH ? tid : -1;
 }
 
-template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX* TY, sizeof(T) == 8 ? 1 : (MODE == MODE_WRITE ? 3 : 2))
-k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
+// Momentum loads.  Within one kernel launch a tile's momenta may have been
+// written by another CTA (persistent ensemble kernel), so that variant
+// bypasses L1 (ld.global.cg); the per-step kernels use plain loads.
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld_mom(const T* p) {
+  if (COHERENT) return __ldcg(p);
+  return *p;
+}
+
+// One tile column (tile (bx, by), planes [z0, z1)) of a step or measuring
+// pass; `bid` indexes the block partial of a measuring pass.
+template <typename T, int TX, int TY, int MODE, bool COHERENT>
+__device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeView<T>& v, const Coef<T>& c,
+                                         const MeasureOut& mo, int bx, int by, int z0, int z1, int bid) {
   using TL = Tile<T, TX, TY>;
   constexpr bool WRITE = (MODE & MODE_WRITE) != 0;
   constexpr bool MEAS = (MODE & MODE_MEASURE) != 0;
   constexpr bool GAUSS = (MODE & MODE_GAUSS) != 0;
   static_assert(!(WRITE && GAUSS), "Gauss needs unmodified neighbour momenta");
   using SM = Smem<T, TX, TY, MEAS, GAUSS>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   SM& sm = *reinterpret_cast<SM*>(smem_raw);
 
   const int tid = threadIdx.x;
   const int lx = tid % TX, ly = tid / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * lz;
-  const int z1 = min(z0 + lz, v.nz);
+  const int x0 = bx * TX, y0 = by * TY;
   const int gx = x0 + lx, gy = y0 + ly;
   const bool active = gx < v.nx && gy < v.ny;
   const long long plane = (long long)v.nx * v.ny;
@@ -242,7 +249,8 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
       cF02[s] = curl_ft<T>(A2[TL::at(ly, lx + 1)], A2[a], sm.pos[1][4 + 3 * s][a], A0[a]);
       cF12[s] = curl_ft<T>(A2[TL::at(ly + 1, lx)], A2[a], sm.pos[1][5 + 3 * s][a], A1[a]);
       cE2[s] = T(0);
-      if (GAUSS && active) cE2[s] = v.mom[6 + 3 * s][(long long)wrapm(z0 - 1, v.nz) * plane + (long long)gy * v.nx + gx];
+      if (GAUSS && active)
+        cE2[s] = ld_mom<COHERENT>(&v.mom[6 + 3 * s][(long long)wrapm(z0 - 1, v.nz) * plane + (long long)gy * v.nx + gx]);
     }
   }
 
@@ -265,10 +273,10 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
     if (active) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        pr[s] = v.mom[2 * s][gsite];
-        pim[s] = v.mom[2 * s + 1][gsite];
+        pr[s] = ld_mom<COHERENT>(&v.mom[2 * s][gsite]);
+        pim[s] = ld_mom<COHERENT>(&v.mom[2 * s + 1][gsite]);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) E[s][i] = v.mom[4 + 3 * s + i][gsite];
+        for (int i = 0; i < 3; ++i) E[s][i] = ld_mom<COHERENT>(&v.mom[4 + 3 * s + i][gsite]);
       }
     } else {
 #pragma unroll
@@ -335,7 +343,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
           sm.Ft[s][2][ha] = curl_ft<T>(A2[TL::at(hy + 1, hx)], A2[ha], sm.pos[bn][5 + 3 * s][ha], A1[ha]);
         if (GAUSS) {
           const long long hs = (long long)z * plane + (long long)wrapm(y0 + hy, v.ny) * v.nx + wrapm(x0 + hx, v.nx);
-          sm.Eg[s][d][ha] = v.mom[4 + 3 * s + d][hs];
+          sm.Eg[s][d][ha] = ld_mom<COHERENT>(&v.mom[4 + 3 * s + d][hs]);
         }
       }
     }
@@ -564,9 +572,18 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
     for (int k = 0; k < NCNT; ++k) ta.cnt[k] = cnt[k];
     __syncthreads();
     ReduceSmem<TL::NT / 32>& rs = *reinterpret_cast<ReduceSmem<TL::NT / 32>*>(smem_raw);
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     block_reduce<TL::NT / 32>(ta, rs, mo.partial + bid);
   }
+}
+
+template <typename T, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(TX* TY, sizeof(T) == 8 ? 1 : (MODE == MODE_WRITE ? 3 : 2))
+k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z0 = blockIdx.z * lz;
+  const int z1 = min(z0 + lz, v.nz);
+  const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  tile_run<T, TX, TY, MODE, false>(smem_raw, v, c, mo, blockIdx.x, blockIdx.y, z0, z1, bid);
 }
 
 template <typename T>
@@ -624,6 +641,214 @@ int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t) {
   Grid g = sizeof_t == 8 ? tiled_grid<double>(nx, ny, nz) : tiled_grid<float>(nx, ny, nz);
   return g.gx * g.gy * g.gz;
 }
+
+// ---------------------------------------------------------------------------
+// Ensemble kernels: many independent boxes in one launch.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+__device__ __forceinline__ long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
+// largest i in [0, n) with a[i] <= r (a ascending, a[0] = 0 <= r)
+__device__ __forceinline__ int upper_index(const long long* a, int n, long long r) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a[mid] <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, bool COHERENT>
+__device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T>& B, int cur, const Coef<T>& c,
+                                             long long t) {
+  constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
+  const int bx = (int)(t % B.gx);
+  const int by = (int)((t / B.gx) % B.gy);
+  const int bz = (int)(t / ((long long)B.gx * B.gy));
+  const int z0 = bz * B.lz;
+  const int z1 = min(z0 + B.lz, B.nz);
+  LatticeView<T> v;
+#pragma unroll
+  for (int f = 0; f < U1U1_NPOS; ++f) {
+    v.pin[f] = B.pos[cur][f];
+    v.pout[f] = B.pos[cur ^ 1][f];
+  }
+#pragma unroll
+  for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = B.mom[f];
+  v.nx = B.nx;
+  v.ny = B.ny;
+  v.nz = B.nz;
+  MeasureOut mo{nullptr, nullptr, nullptr};
+  tile_run<T, TX, TY, MODE_WRITE, COHERENT>(smem, v, c, mo, bx, by, z0, z1, 0);
+}
+
+// Persistent ensemble kernel: CTAs take work items (step k, box, tile) in
+// ticket order, step-major, boxes with more steps first.  An item of step k
+// waits until all items of step k-1 of its box are done.  Every wait is
+// bounded: past limit_ns the kernel records U1U1_ERR_TIMEOUT and all CTAs
+// return.  Deadlock freedom: tickets are taken only by running CTAs and an
+// item depends only on items with smaller tickets.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
+k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
+                 EnsSched sc, unsigned long long* ticket, unsigned* done, int* err, long long limit_ns, int inject) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Coef<T> cs;
+  __shared__ long long s_t;
+  __shared__ int s_box, s_k, s_go;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long tk = (long long)atomicAdd(ticket, 1ull);
+      int go = (tk < sc.total) && (*(volatile int*)err == 0);
+      int box = 0, k = 0;
+      long long t = 0;
+      if (go) {
+        k = upper_index(sc.step_off, sc.smax + 1, tk);
+        const long long r = tk - sc.step_off[k];
+        const int si = upper_index(sc.box_prefix, sc.nboxes + 1, r);
+        box = sc.order[si];
+        t = r - sc.box_prefix[si];
+        unsigned need = (unsigned)k * (unsigned)boxes[box].ntiles;
+        if (inject && si == 0 && k == 1 && t == 0) need += 1u;  // a count nothing reaches
+        if (need > 0) {
+          const long long t0 = globaltimer_ns();
+          while (*(volatile unsigned*)&done[box] < need) {
+            if (*(volatile int*)err != 0) {
+              go = 0;
+              break;
+            }
+            if (globaltimer_ns() - t0 > limit_ns) {
+              atomicExch(err, U1U1_ERR_TIMEOUT);
+              go = 0;
+              break;
+            }
+            __nanosleep(256);
+          }
+          __threadfence();
+        }
+        if (go) cs = coef[boxes[box].coef0 + dyn[box].n + k];
+      }
+      s_go = go;
+      s_box = box;
+      s_k = k;
+      s_t = t;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const EnsBox<T>& B = boxes[s_box];
+    ens_run_item<T, true>(smem_raw, B, (dyn[s_box].cur + s_k) & 1, cs, s_t);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[s_box], 1u);
+    }
+  }
+}
+
+// One step k of every box that still has steps: one CTA per work item.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
+k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
+           EnsSched sc, int k) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Coef<T> cs;
+  const long long r = blockIdx.x;
+  const int si = upper_index(sc.box_prefix, sc.nboxes + 1, r);
+  const int box = sc.order[si];
+  if (threadIdx.x == 0) cs = coef[boxes[box].coef0 + dyn[box].n + k];
+  __syncthreads();
+  ens_run_item<T, false>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si]);
+}
+
+__global__ void k_ens_advance(EnsDyn* dyn, const int* steps, int nboxes) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nboxes) {
+    dyn[b].n += steps[b];
+    dyn[b].cur ^= (steps[b] & 1);
+  }
+}
+
+template <typename T>
+size_t ens_smem_bytes() {
+  return sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, false, false>);
+}
+
+template <typename KernelT>
+cudaError_t set_smem_attr(KernelT kernel, size_t bytes) {
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz) {
+  *gx = (nx + 31) / 32;
+  *gy = (ny + 7) / 8;
+  *lz = nz < ENS_LZ ? nz : ENS_LZ;
+  *gz = (nz + *lz - 1) / *lz;
+  return *gx * *gy * *gz;
+}
+
+template <typename T>
+cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
+                                  unsigned long long* ticket, unsigned* done, int* err, long long limit_ns,
+                                  int inject, cudaStream_t st) {
+  const size_t bytes = ens_smem_bytes<T>();
+  cudaError_t e = set_smem_attr(k_ens_persistent<T>, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<T>, 256, bytes)) != cudaSuccess)
+    return e;
+  long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > sc.total) grid = sc.total;
+  if (grid < 1) return cudaSuccess;
+  k_ens_persistent<T><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, ticket, done, err, limit_ns, inject);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
+                            int k, long long items, cudaStream_t st) {
+  const size_t bytes = ens_smem_bytes<T>();
+  cudaError_t e = set_smem_attr(k_ens_step<T>, bytes);
+  if (e != cudaSuccess) return e;
+  if (items <= 0) return cudaSuccess;
+  k_ens_step<T><<<(unsigned)items, 256, bytes, st>>>(boxes, dyn, coef, sc, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, cudaStream_t st) {
+  k_ens_advance<<<(nboxes + 127) / 128, 128, 0, st>>>(dyn, steps, nboxes);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_ens_persistent<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*,
+                                                  const EnsSched&, unsigned long long*, unsigned*, int*, long long,
+                                                  int, cudaStream_t);
+template cudaError_t launch_ens_persistent<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,
+                                                   const EnsSched&, unsigned long long*, unsigned*, int*, long long,
+                                                   int, cudaStream_t);
+template cudaError_t launch_ens_step<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*, const EnsSched&,
+                                            int, long long, cudaStream_t);
+template cudaError_t launch_ens_step<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,
+                                             const EnsSched&, int, long long, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,

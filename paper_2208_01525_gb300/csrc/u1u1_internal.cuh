@@ -113,6 +113,42 @@ template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
                          cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Ensembles: per-box tables for the batched kernels.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EnsBox {
+  T* pos[2][U1U1_NPOS];
+  T* mom[U1U1_NMOM];
+  int nx, ny, nz;
+  int gx, gy, lz, gz, ntiles;  // tile grid of this box
+  long long coef0;             // first row of this box in the coefficient table
+};
+struct EnsDyn {                // device-side step index and current buffer
+  long long n;
+  int cur;
+  int pad;
+};
+struct EnsSched {              // one run's work-item order
+  const int* order;            // sorted position -> box (steps descending)
+  const int* steps;            // steps of each box (box index)
+  const long long* box_prefix; // nboxes + 1 cumulative tiles in sorted order
+  const long long* step_off;   // smax + 1 cumulative items before each step
+  int nboxes, smax;
+  long long total;
+};
+constexpr int ENS_LZ = 32;     // z-chunk of an ensemble work item
+
+int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz);
+template <typename T>
+cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
+                                  unsigned long long* ticket, unsigned* done, int* err, long long limit_ns,
+                                  int inject, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
+                            int k, long long items, cudaStream_t st);
+cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, cudaStream_t st);
+
 // Cells and overlap from face bytes; masks holds 2 * cell_mask_words words.
 int cells_grid_blocks();
 size_t cell_mask_words(int nx, int ny, int nz);

@@ -1,0 +1,112 @@
+"""Batched ensembles of independent boxes of uneven size: every box advanced
+in an ensemble run equals the same box advanced alone by the single-lattice
+tiled kernel, bit for bit, in all three scheduling modes and through CUDA
+graph replays; the persistent kernel's bounded dependency wait turns an
+unreachable wait into a reported timeout."""
+import numpy as np
+import pytest
+
+import paper_2208_01525_gb300 as U
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def box_params(prec=U.FP32):
+    """Uneven boxes, eras, beta and seeds (ragged tiles in x, y and z)."""
+    shapes = [(16, 16, 16), (24, 20, 12), (32, 8, 40), (8, 12, 4), (40, 24, 33), (12, 12, 12)]
+    out = []
+    for b, (nx, ny, nz) in enumerate(shapes):
+        m = (0.5, 2.0 / 3.0)[b % 2]
+        beta = (1.0, 0.0, -1.0)[b % 3]
+        out.append(U.Params(nx=nx, ny=ny, nz=nz, m=m, beta=beta, eta0=1.0,
+                            eta_ref=3.0 if beta > 0 else 1.0, seed=1000 + b, precision=prec))
+    return out
+
+
+def alone(p, nsteps):
+    lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+    lat.step(nsteps)
+    return lat.state()
+
+
+@pytest.mark.parametrize("mode", [U.ENS_PERSISTENT, U.ENS_PER_STEP, U.ENS_UNBATCHED])
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_ensemble_matches_single_boxes(mode, prec):
+    ps = box_params(prec)
+    steps = [10, 7, 13, 0, 5, 9]
+    ens = U.Ensemble(ps)
+    ens.run(steps, mode=mode)
+    assert ens.status() == 0
+    for b, p in enumerate(ps):
+        assert ens.boxes[b].n == steps[b]
+        assert torch.equal(ens.boxes[b].state(), alone(p, steps[b])), b
+    ens.close()
+
+
+@pytest.mark.parametrize("mode", [U.ENS_PERSISTENT, U.ENS_PER_STEP])
+def test_ensemble_graph_replays(mode):
+    ps = box_params()
+    steps = [3, 4, 1, 2, 5, 3]
+    ens = U.Ensemble(ps)
+    for _ in range(3):  # capture once, replay twice; odd counts flip buffers
+        ens.run(steps, mode=mode, use_graph=True)
+    torch.cuda.synchronize()
+    assert ens.status() == 0
+    for b, p in enumerate(ps):
+        assert ens.boxes[b].n == 3 * steps[b]
+        assert torch.equal(ens.boxes[b].state(), alone(p, 3 * steps[b])), b
+
+
+def test_ensemble_mixed_with_box_handles():
+    """Steps taken through a box's own handle between ensemble runs are
+    picked up by the next run; detection on a box equals detection alone."""
+    ps = box_params()
+    ens = U.Ensemble(ps)
+    ens.run([4] * 6, mode=U.ENS_PERSISTENT)
+    ens.boxes[2].step(3)
+    ens.run([2] * 6, mode=U.ENS_PERSISTENT)
+    want = [6, 6, 9, 6, 6, 6]
+    for b, p in enumerate(ps):
+        assert ens.boxes[b].n == want[b]
+        ref = U.Lattice(p, kernel=U.KERNEL_TILED)
+        ref.step(want[b])
+        assert torch.equal(ens.boxes[b].state(), ref.state()), b
+        if b == 4:
+            s1 = ens.boxes[b].detect_strings()
+            s2 = ref.detect_strings()
+            assert s1["n_p"] == s2["n_p"] and s1["n_pq_cell"] == s2["n_pq_cell"]
+
+
+def test_ensemble_bounded_wait_reports_timeout():
+    """A work item waiting for a count nothing reaches: the run ends with
+    U1U1_ERR_TIMEOUT after the wait limit, no hang; the ensemble then
+    refuses further runs."""
+    ps = box_params()
+    ens = U.Ensemble(ps)
+    ens.set_wait_limit(50_000_000)  # 50 ms
+    ens.inject_unreachable_wait(True)
+    ens.run([3] * 6, mode=U.ENS_PERSISTENT)
+    assert ens.status() == -5
+    with pytest.raises(U.U1U1Error):
+        ens.run([1] * 6)
+    ens.close()
+    # a fresh ensemble on the same device works normally afterwards
+    ens2 = U.Ensemble(ps)
+    ens2.run([2] * 6)
+    assert ens2.status() == 0
+
+
+def test_ensemble_errors():
+    ps = box_params()
+    ens = U.Ensemble(ps, horizon=16)
+    with pytest.raises(U.U1U1Error):
+        ens.run([-1, 0, 0, 0, 0, 0])
+    with pytest.raises(U.U1U1Error):
+        ens.run([17, 0, 0, 0, 0, 0])
+    with pytest.raises(U.U1U1Error):
+        ens.run([1] * 6, mode=U.ENS_UNBATCHED, use_graph=True)
+    ens.run([0] * 6)
+    assert all(b.n == 0 for b in ens.boxes)
+    with pytest.raises(U.U1U1Error):
+        U.Ensemble([ps[0], U.Params(nx=8, ny=8, nz=8, precision=U.FP64)])
