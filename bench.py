@@ -193,6 +193,24 @@ def ensemble_bench(U, torch, dev):
         out[name] = {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": status}
     out["speedup_vs_unbatched"] = out["persistent_graph"]["site_updates_per_s"] / \
         out["unbatched"]["site_updates_per_s"]
+    # the small-box class alone (16 x 64^3), where per-box launches cannot fill the GPU
+    small = [p for p, n in zip(ps, sizes) if n == 64]
+    ssteps = [s_ for s_, n in zip(steps, sizes) if n == 64]
+    swork = sum(s_ * 64 ** 3 for s_ in ssteps)
+    res = {}
+    for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True), ("unbatched", U.ENS_UNBATCHED, False)):
+        ens = U.Ensemble(small, device=dev, horizon=2048)
+        ens.run(ssteps, mode=mode, use_graph=graph)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.run(ssteps, mode=mode, use_graph=graph)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = swork / (a.elapsed_time(b) * 1e-3)
+        ens.close()
+    out["small_boxes_64"] = {"site_updates_per_s": res,
+                             "speedup_vs_unbatched": res["persistent_graph"] / res["unbatched"]}
     return out
 
 

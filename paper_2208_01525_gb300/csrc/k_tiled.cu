@@ -716,7 +716,7 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
         box = sc.order[si];
         t = r - sc.box_prefix[si];
         unsigned need = (unsigned)k * (unsigned)boxes[box].ntiles;
-        if (inject && si == 0 && k == 1 && t == 0) need += 1u;  // a count nothing reaches
+        if (inject && si == 0 && k == 1 && t == 0) need = 0xFFFFFFFFu;  // a count no run reaches
         if (need > 0) {
           const long long t0 = globaltimer_ns();
           while (*(volatile unsigned*)&done[box] < need) {
