@@ -316,6 +316,37 @@ int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enable);
 
 void u1u1_ensemble_destroy(u1u1_ensemble* e);
 
+/* ---- detection without device allocation ------------------------------------ */
+
+/* Largest lattice, in sites, accepted by u1u1_detect_strings_noalloc. */
+#define U1U1_NOALLOC_MAX_SITES 16777216 /* 256^3 */
+
+/* Fast string detection (same windings, cells, overlap and counts as
+ * u1u1_detect_strings) for callers that cannot allocate device memory:
+ * code that runs while a framework owns the whole device pool, inside an
+ * allocator or memory-pressure callback, or under a policy that forbids
+ * allocation after start-up.  It needs no lattice handle and calls no
+ * cudaMalloc, cudaFree or other allocating routine; its scratch (winding
+ * bytes, cell masks, block partials, one record) is a fixed static device
+ * array inside the library, 48 MiB on every GPU that loads the library,
+ * held until the process exits.  This entry point is an engineering
+ * addition: the paper has no counterpart.
+ * Arguments: p, the lattice parameters; fields, the 20 device field arrays
+ * of the state (U1U1_POS_* then U1U1_MOM_* order, layout as for a lattice,
+ * 256-byte aligned), read only; n, the step index the record reports;
+ * overlap_tol, 0 or 1; *out, filled on the host.  Synchronises `stream`.
+ * Limits: at most U1U1_NOALLOC_MAX_SITES sites, and the scratch the shape
+ * needs must fit the array (every cubic box up to 256^3 does); larger
+ * requests return U1U1_ERR_INVALID_ARG with the byte count in the message.
+ * Set-up: the first call on a device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents: calls that overlap on the GPU (several streams
+ * or threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG, NOT_SUPPORTED (device index >= 64), CUDA. */
+int u1u1_detect_strings_noalloc(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int64_t n,
+                                int overlap_tol, u1u1_strings* out, void* stream);
+
 /* ---- check entry points ---------------------------------------------------- */
 
 /* Evaluate, on n device values theta, the FP32 routine the kernels use for

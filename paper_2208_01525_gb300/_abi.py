@@ -18,6 +18,7 @@ ERRORS = {
     -6: "NAN", -7: "NOT_SUPPORTED", -8: "STATE", -9: "IO",
 }
 FP32, FP64 = 0, 1
+NOALLOC_MAX_SITES = 16777216
 NPOS, NMOM = 10, 10
 NFIELDS = NPOS + NMOM
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED = 0, 1, 2
@@ -116,6 +117,8 @@ PROTOTYPES = {
     "u1u1_ensemble_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "u1u1_ensemble_inject_unreachable_wait": (ctypes.c_int, [_vp, ctypes.c_int]),
     "u1u1_ensemble_destroy": (None, [_vp]),
+    "u1u1_detect_strings_noalloc": (ctypes.c_int, [_P(CParams), _P(_vp), ctypes.c_int64, ctypes.c_int,
+                                                   _P(CStrings), _vp]),
 }
 
 _lib = None

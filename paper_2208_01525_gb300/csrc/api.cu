@@ -400,7 +400,7 @@ static double sqrt_ratio(double num, double den) {
   return r >= 0.0 ? sqrt(r) : NAN;
 }
 
-static void to_strings(const u1u1_params* p, const RawRecord& r, u1u1_strings* s) {
+void u1u1::to_strings(const u1u1_params* p, const RawRecord& r, u1u1_strings* s) {
   memset(s, 0, sizeof(*s));
   double cf[6];
   coeffs(p, r.n, cf);

@@ -29,6 +29,8 @@ void coeffs(const u1u1_params* p, int64_t n, double out[6]);
 // the kernels' coefficient block for step n
 template <typename T>
 Coef<T> make_coef(const u1u1_params* p, int64_t n);
+// host epilogue of a detection record (Sec. III.A, Eqs. 31-35)
+void to_strings(const u1u1_params* p, const RawRecord& r, u1u1_strings* s);
 
 }  // namespace u1u1
 

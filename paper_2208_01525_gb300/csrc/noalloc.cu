@@ -1,0 +1,121 @@
+// String detection for callers that cannot allocate device memory.
+//
+// u1u1_detect_strings_noalloc runs the same measuring kernel, cell pass and
+// finalize as u1u1_detect_strings, but without a lattice handle: its scratch
+// (per-site winding bytes, packed cell masks, block partials and the result
+// record) is carved out of one file-scope static device array, so the call
+// itself never calls cudaMalloc, cudaFree or any allocating routine.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/u1u1.h"
+#include "host_internal.h"
+#include "u1u1_internal.cuh"
+
+using namespace u1u1;
+
+namespace {
+
+constexpr size_t NOALLOC_BYTES = 48ull << 20;  // 48 MiB on every GPU that loads the library
+
+// The scratch array.  In host code this name is only a host-side stand-in:
+// its device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+void* g_scratch_addr[MAX_DEVICES] = {};
+std::mutex g_scratch_mu;
+
+size_t round_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// device address of the scratch array on the current device (set up on the
+// first call per device)
+int scratch_address(void** out) {
+  int dev = 0;
+  U1U1_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= MAX_DEVICES) return fail(U1U1_ERR_NOT_SUPPORTED, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return U1U1_OK;
+}
+
+template <typename T>
+int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int64_t n, int tol, unsigned char* base,
+               u1u1_strings* out, cudaStream_t st) {
+  const size_t V = (size_t)p->nx * p->ny * p->nz;
+  const int nblocks = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)sizeof(T));
+  const int ncblocks = cells_grid_blocks();
+  // carve the scratch: face bytes, cell masks, block partials, cell partials, record
+  const size_t off_faces = 0;
+  const size_t off_masks = off_faces + round_up(2 * V);
+  const size_t off_part = off_masks + round_up(2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
+  const size_t off_cpart = off_part + round_up(sizeof(BlockPartial) * (size_t)nblocks);
+  const size_t off_rec = off_cpart + round_up(sizeof(CellPartial) * (size_t)ncblocks);
+  const size_t need = off_rec + round_up(sizeof(RawRecord));
+  if (need > NOALLOC_BYTES)
+    return fail(U1U1_ERR_INVALID_ARG, "lattice %dx%dx%d needs %zu bytes of scratch; the static array holds %zu", p->nx,
+                p->ny, p->nz, need, NOALLOC_BYTES);
+  uint8_t* faces = base + off_faces;
+  uint32_t* masks = (uint32_t*)(base + off_masks);
+  BlockPartial* part = (BlockPartial*)(base + off_part);
+  CellPartial* cpart = (CellPartial*)(base + off_cpart);
+  RawRecord* rec = (RawRecord*)(base + off_rec);
+  // every scratch word read below is first written by the same call (face
+  // bytes and masks for every site, one partial per block, the record), so
+  // nothing needs clearing
+
+  LatticeView<T> v;
+  for (int f = 0; f < U1U1_NPOS; ++f) {
+    v.pin[f] = (const T*)fields[f];
+    v.pout[f] = (T*)fields[f];  // a measuring pass writes no field
+  }
+  for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = (T*)fields[U1U1_NPOS + f];
+  v.nx = p->nx;
+  v.ny = p->ny;
+  v.nz = p->nz;
+  const Coef<T> c = make_coef<T>(p, n);
+  MeasureOut mo{part, faces, nullptr};
+  cudaError_t e = launch_tiled<T>(MODE_MEASURE, v, c, mo, st);
+  if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
+  e = launch_cells(faces, p->nx, p->ny, p->nz, tol, nullptr, nullptr, masks, cpart, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
+  e = launch_finalize(part, nblocks, cpart, ncblocks, rec, (long long)n, 1, 0, 1, tol, st);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+  RawRecord r;
+  U1U1_CUDA_TRY(cudaMemcpyAsync(&r, rec, sizeof(RawRecord), cudaMemcpyDeviceToHost, st), "record copy");
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  to_strings(p, r, out);
+  return U1U1_OK;
+}
+
+}  // namespace
+
+extern "C" int u1u1_detect_strings_noalloc(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int64_t n,
+                                           int overlap_tol, u1u1_strings* out, void* stream) {
+  int rc = u1u1_check_params(p);
+  if (rc) return rc;
+  if (!fields || !out) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  for (int f = 0; f < U1U1_NFIELDS; ++f) {
+    if (!fields[f]) return fail(U1U1_ERR_INVALID_ARG, "fields[%d] is NULL", f);
+    if ((uintptr_t)fields[f] % 256 != 0) return fail(U1U1_ERR_INVALID_ARG, "fields[%d] is not 256-byte aligned", f);
+  }
+  if (overlap_tol < 0 || overlap_tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
+  const double sites = (double)p->nx * p->ny * p->nz;
+  if (sites > (double)U1U1_NOALLOC_MAX_SITES)
+    return fail(U1U1_ERR_INVALID_ARG, "lattice of %.0f sites exceeds the %d-site limit of the allocation-free entry point",
+                sites, U1U1_NOALLOC_MAX_SITES);
+  void* base = nullptr;
+  rc = scratch_address(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return p->precision == U1U1_FP64 ? run_detect<double>(p, fields, n, overlap_tol, (unsigned char*)base, out, st)
+                                   : run_detect<float>(p, fields, n, overlap_tol, (unsigned char*)base, out, st);
+}
