@@ -147,6 +147,20 @@ typedef struct {
   int64_t nan_count;    /* NaN entries among the 20 fields */
 } u1u1_diag;
 
+/* Bound-state segments of the robust method (Sec. III.B, Eq. 38). */
+typedef struct {
+  int64_t n;            /* step index of the state */
+  int32_t overlap_tol;  /* cell overlap tolerance used for the pq cells */
+  int32_t min_cells;    /* a component counts as a segment when it has more cells */
+  int64_t n_cells;      /* pq cells (p-anchored fast-method overlap) */
+  int64_t n_components; /* connected components of the pq cells */
+  int64_t n_segments;   /* N_pq: components with more than min_cells cells */
+  int64_t largest;      /* cells in the largest component */
+  double L_pq;          /* dx * sum over segments of (N_cells - 1) */
+  double l_pq;          /* L_pq / N_pq (Eq. 38); NaN when there is no segment */
+  double xi_pq;         /* sqrt(V / L_pq); +inf when L_pq = 0 */
+} u1u1_segments;
+
 typedef struct u1u1_lattice u1u1_lattice;
 typedef struct u1u1_ensemble u1u1_ensemble;
 
@@ -215,6 +229,23 @@ int u1u1_current(const u1u1_lattice* h, int64_t* n, int* current);
  * in a CUDA graph.  Errors: INVALID_ARG, CUDA. */
 int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* stream);
 
+/* Diffusive cooling (Sec. III, Eqs. 27-30): nsteps >= 0 forward-Euler steps
+ * of size dt > 0 of the first-order flow, per sector,
+ *   d phi / dt = D^- D^+ phi - lambda/2 (|phi|^2 - sigma^2) phi,
+ *   d A_i / dt = -sum_j (F_ij(x) - F_ij(x-j)) / dx + 2 e^2 Im[phi^* D_i^+ phi],
+ * with lambda_0, e_0 and no kappa term, as printed; afterwards every
+ * momentum and electric field is zero.  The step index is unchanged.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+int u1u1_cool(u1u1_lattice* h, double dt, int nsteps, void* stream);
+
+/* Replace the time-dependent parameters of a handle (m, eta0, eta_ref,
+ * deta, beta, alpha, couplings and vacuum values) by those of *p and set its
+ * step index to n, keeping the lattice, precision, seed, buffers and the
+ * current state: this chains the phases of a run schedule (damping with
+ * m_damp, core growth with beta < 0, physical evolution; Sec. V, Table 3).
+ * Errors: INVALID_ARG (invalid parameters or a different lattice/precision). */
+int u1u1_set_params(u1u1_lattice* h, const u1u1_params* p, int64_t n);
+
 /* Overlap tolerance (0: same cell, 1: one cell in any of the 26 directions)
  * used by fused detection steps. */
 int u1u1_set_overlap_tol(u1u1_lattice* h, int tol);
@@ -227,6 +258,21 @@ int u1u1_set_overlap_tol(u1u1_lattice* h, int tol);
  * (synchronises `stream`).  Errors: INVALID_ARG, CUDA. */
 int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
                         int8_t* windings, u1u1_strings* out, void* stream);
+
+/* Robust-method bound-state segments on the current state (Sec. III.B,
+ * Eq. 38): the fast method's p-anchored pq cells (tolerance overlap_tol, 0
+ * or 1) are split into connected components on the periodic lattice, cells
+ * joined when they share a face, an edge or a corner (the connectivity
+ * filter's rule); a component of N cells is a segment of length (N - 1) dx
+ * (the off-by-one correction) and counts when N > min_cells (the paper uses
+ * 41 at 4096^3).  labels_out (optional device int32 array of nx*ny*nz)
+ * receives each pq cell's component label -- the smallest site index of its
+ * component -- and -1 elsewhere.  Scratch (8 bytes per site) is allocated on
+ * the handle's first call.  *out is filled on the host (synchronises
+ * `stream`).  Errors: INVALID_ARG, NOT_SUPPORTED (more than 2^31 - 1
+ * sites), OUT_OF_MEMORY, CUDA. */
+int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells, int32_t* labels_out, u1u1_segments* out,
+                     void* stream);
 
 /* All diagnostics of Sec. III.A on the current state, including the Gauss
  * law residual per sector at n-1/2 (Eqs. 9-10), without stepping.  Fills

@@ -129,6 +129,8 @@ def _load(path: str):
     L.orc_overlap.argtypes = [P, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     L.orc_overlap.restype = ctypes.c_long
     L.orc_diagnostics.argtypes = [P, dp, ctypes.c_long, dp, dp]
+    L.orc_pq_mask.argtypes = [P, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    L.orc_components.argtypes = [P, ctypes.c_void_p, ctypes.c_void_p]
     L.orc_diag_count.restype = ctypes.c_int
     L.orc_set_threads.argtypes = [ctypes.c_int]
     L.orc_max_threads.restype = ctypes.c_int
@@ -249,6 +251,43 @@ def overlap(p: Params, anchor: np.ndarray, other: np.ndarray, tol: int) -> int:
     a = np.ascontiguousarray(anchor, dtype=np.uint8)
     o = np.ascontiguousarray(other, dtype=np.uint8)
     return int(lib().orc_overlap(ctypes.byref(p.c()), a.ctypes.data, o.ctypes.data, int(tol)))
+
+
+def pq_mask(p: Params, anchor: np.ndarray, other: np.ndarray, tol: int) -> np.ndarray:
+    """Cells of the fast method's bound-state overlap (uint8 0/1)."""
+    a = np.ascontiguousarray(anchor, dtype=np.uint8)
+    o = np.ascontiguousarray(other, dtype=np.uint8)
+    m = np.zeros(p.shape, dtype=np.uint8)
+    lib().orc_pq_mask(ctypes.byref(p.c()), a.ctypes.data, o.ctypes.data, int(tol), m.ctypes.data)
+    return m
+
+
+def components(p: Params, mask: np.ndarray) -> np.ndarray:
+    """Periodic 26-connected components: smallest site index per component, -1 outside."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    lab = np.zeros(p.shape, dtype=np.int64)
+    lib().orc_components(ctypes.byref(p.c()), m.ctypes.data, lab.ctypes.data)
+    return lab
+
+
+def segments(p: Params, st: np.ndarray, tol: int = 1, min_cells: int = 41) -> dict:
+    """Robust-method bound-state segments (Sec. III.B, Eq. 38): connected
+    components of the pq cells; a segment of N cells has length (N - 1) dx
+    and counts when N > min_cells; N_pq segments, L_pq their total length,
+    l_pq = L_pq / N_pq, xi_pq = sqrt(V / L_pq)."""
+    W, _ = windings(p, st)
+    C = cells(p, W)
+    mask = pq_mask(p, C[0], C[1], tol)
+    lab = components(p, mask)
+    roots, sizes = np.unique(lab[lab >= 0], return_counts=True)
+    keep = sizes > min_cells
+    L = p.dx * float((sizes[keep] - 1).sum())
+    n_seg = int(keep.sum())
+    vol = p.nsites * p.dx ** 3
+    return dict(n_cells=int(mask.sum()), n_components=int(len(roots)), n_segments=n_seg,
+                largest=int(sizes.max()) if len(sizes) else 0, L_pq=L,
+                l_pq=(L / n_seg) if n_seg else math.nan, xi_pq=_sqrt_ratio(vol, L),
+                labels=lab, mask=mask)
 
 
 def diagnostic_sums(p: Params, st: np.ndarray, n: int) -> dict:

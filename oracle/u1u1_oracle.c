@@ -387,6 +387,56 @@ long orc_overlap(const orc_params* p, const unsigned char* anchor, const unsigne
   return count;
 }
 
+/* The fast method's bound-state cells (Sec. III.B): mask[x] = 1 when
+ * anchor[x] > 0 and other[y] > 0 for some y in x + {-tol..tol}^3. */
+void orc_pq_mask(const orc_params* p, const unsigned char* anchor, const unsigned char* other, int tol,
+                 unsigned char* mask) {
+  for (long z = 0; z < p->nz; ++z)
+    for (long y = 0; y < p->ny; ++y)
+      for (long x = 0; x < p->nx; ++x) {
+        long site = sidx(p, x, y, z);
+        int hit = 0;
+        if (anchor[site] > 0)
+          for (int dz = -tol; dz <= tol && !hit; ++dz)
+            for (int dy = -tol; dy <= tol && !hit; ++dy)
+              for (int dx = -tol; dx <= tol && !hit; ++dx)
+                if (other[sidx(p, x + dx, y + dy, z + dz)] > 0) hit = 1;
+        mask[site] = (unsigned char)hit;
+      }
+}
+
+/* Connected components of a cell mask on the periodic lattice, cells joined
+ * when they share a face, an edge or a corner (26 neighbours): the
+ * connectivity filter of the robust method (Sec. III.B).  label[x] is the
+ * smallest site index of x's component, -1 outside the mask.  Breadth-first
+ * search from every unlabelled mask cell in increasing index order, so the
+ * start of each search is the smallest index of its component. */
+void orc_components(const orc_params* p, const unsigned char* mask, long* label) {
+  long V = nsites(p);
+  long* queue = (long*)malloc(sizeof(long) * (size_t)V);
+  for (long i = 0; i < V; ++i) label[i] = -1;
+  for (long start = 0; start < V; ++start) {
+    if (!mask[start] || label[start] >= 0) continue;
+    long head = 0, tail = 0;
+    queue[tail++] = start;
+    label[start] = start;
+    while (head < tail) {
+      long c = queue[head++];
+      long cx = c % p->nx, cy = (c / p->nx) % p->ny, cz = c / ((long)p->nx * p->ny);
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            long nb = sidx(p, cx + dx, cy + dy, cz + dz);
+            if (mask[nb] && label[nb] < 0) {
+              label[nb] = start;
+              queue[tail++] = nb;
+            }
+          }
+    }
+  }
+  free(queue);
+}
+
 /* ---- network diagnostics (Sec. III.A, Eqs. 33, 36-37; Sec. IV) ---------- */
 
 /* Neumaier compensated sum */

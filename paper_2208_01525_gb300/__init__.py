@@ -193,6 +193,15 @@ class Lattice:
     def step(self, nsteps: int = 1, detect_every: int = 0, stream=None):
         check(lib().u1u1_step(self._h, int(nsteps), int(detect_every), _stream_ptr(stream)))
 
+    def cool(self, dt: float, nsteps: int, stream=None):
+        """Diffusive cooling flow of Eqs. 27-30; momenta are zero afterwards."""
+        check(lib().u1u1_cool(self._h, float(dt), int(nsteps), _stream_ptr(stream)))
+
+    def set_params(self, params: Params, n: int, stream=None):
+        """Switch to another phase's time-dependent parameters at step index n."""
+        check(lib().u1u1_set_params(self._h, ctypes.byref(params.c()), int(n)))
+        self.params = params
+
     def set_overlap_tol(self, tol: int):
         check(lib().u1u1_set_overlap_tol(self._h, int(tol)))
 
@@ -214,6 +223,19 @@ class Lattice:
             res["cells"] = torch.stack([cp, cq]).view(2, *self.params.shape)
         if windings:
             res["windings"] = w.view(2, 3, *self.params.shape)
+        return res
+
+    def pq_segments(self, tol: int = 1, min_cells: int = 41, labels: bool = False, stream=None) -> dict:
+        """Robust-method bound-state segments (connected pq-cell components)."""
+        import torch
+        lab = torch.empty(self.params.nsites, dtype=torch.int32, device=self.device) if labels else None
+        out = _abi.CSegments()
+        check(lib().u1u1_pq_segments(self._h, int(tol), int(min_cells),
+                                     ctypes.c_void_p(lab.data_ptr()) if lab is not None else None,
+                                     ctypes.byref(out), _stream_ptr(stream)))
+        res = _abi.struct_to_dict(out)
+        if labels:
+            res["labels"] = lab.view(*self.params.shape)
         return res
 
     def diagnostics(self, stream=None) -> dict:

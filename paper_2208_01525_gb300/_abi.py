@@ -64,6 +64,15 @@ class CStrings(ctypes.Structure):
     ]
 
 
+class CSegments(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("overlap_tol", ctypes.c_int32), ("min_cells", ctypes.c_int32),
+        ("n_cells", ctypes.c_int64), ("n_components", ctypes.c_int64), ("n_segments", ctypes.c_int64),
+        ("largest", ctypes.c_int64), ("L_pq", ctypes.c_double), ("l_pq", ctypes.c_double),
+        ("xi_pq", ctypes.c_double),
+    ]
+
+
 _DIAG_DOUBLES_1 = ["eta", "a", "kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q",
                    "pot", "vint", "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den",
                    "lag_total", "energy_total", "xi_l", "R_l", "v2_l", "R_pq", "v2_pq"]
@@ -99,8 +108,11 @@ PROTOTYPES = {
     "u1u1_current": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int)]),
     "u1u1_step": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
     "u1u1_set_overlap_tol": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "u1u1_cool": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp]),
+    "u1u1_set_params": (ctypes.c_int, [_vp, _P(CParams), ctypes.c_int64]),
     "u1u1_detect_strings": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _P(CStrings), _vp]),
     "u1u1_diagnostics": (ctypes.c_int, [_vp, _P(CDiag), _vp]),
+    "u1u1_pq_segments": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _P(CSegments), _vp]),
     "u1u1_read_records": (ctypes.c_int, [_vp, _P(CStrings), _P(CDiag), ctypes.c_int, _P(ctypes.c_int),
                                          _P(ctypes.c_int64), _vp]),
     "u1u1_upload_state": (ctypes.c_int, [_vp, _P(_vp), _vp]),

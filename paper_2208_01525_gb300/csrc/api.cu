@@ -196,6 +196,10 @@ void u1u1::lattice_free_scratch(u1u1_lattice* h) {
   if (!h) return;
   cudaFree(h->faces);
   cudaFree(h->masks);
+  cudaFree(h->mpq);
+  cudaFree(h->seg_label);
+  cudaFree(h->seg_size);
+  cudaFree(h->seg_counts);
   cudaFree(h->partials);
   cudaFree(h->cpartials);
   cudaFree(h->ring);
@@ -393,6 +397,71 @@ extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* st
   return U1U1_OK;
 }
 
+// Cooling (Eqs. 27-30) reuses the step kernel: with the old momenta weighted
+// by zero, a kick of size dt equal to the flow's right-hand side, and a drift
+// of weight one, a leapfrog step is exactly one forward-Euler cooling step.
+template <typename T>
+static Coef<T> make_cool_coef(const u1u1_params* p, double dt) {
+  Coef<T> k;
+  memset(&k, 0, sizeof(k));
+  const double dx = p->dx;
+  const double lam[2] = {p->lambda_p, p->lambda_q};
+  const double e[2] = {p->e_p, p->e_q};
+  const double sig[2] = {p->sigma_p, p->sigma_q};
+  k.kPa = (T)0;
+  k.kP1 = (T)(dt / (dx * dx));
+  for (int s = 0; s < 2; ++s) k.kgl[s] = (T)(dt * 0.5 * lam[s]);
+  k.kgk = (T)0;  // no kappa term in the cooling flow
+  k.kEa = (T)0;
+  k.kE1 = (T)(dt / (dx * dx));
+  for (int s = 0; s < 2; ++s) k.kE2[s] = (T)(dt * 2.0 * e[s] * e[s] / dx);
+  k.deta = (T)1;
+  k.dx = (T)dx;
+  for (int s = 0; s < 2; ++s) k.sig2[s] = (T)(sig[s] * sig[s]);
+  return k;
+}
+
+template <typename T>
+static cudaError_t cool_t(u1u1_lattice* h, double dt, int nsteps, cudaStream_t st) {
+  const Coef<T> c = make_cool_coef<T>(&h->p, dt);
+  const MeasureOut mo{nullptr, nullptr, nullptr};
+  for (int k = 0; k < nsteps; ++k) {
+    LatticeView<T> v = view<T>(h);
+    cudaError_t e = use_tiled(h) ? launch_tiled<T>(MODE_WRITE, v, c, mo, st) : launch_simple<T>(MODE_WRITE, v, c, mo, st);
+    if (e != cudaSuccess) return e;
+    h->cur ^= 1;
+  }
+  const size_t bytes = h->V * h->esize;
+  for (int f = 0; f < U1U1_NMOM; ++f) {
+    cudaError_t e = cudaMemsetAsync(h->mom[f], 0, bytes, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+extern "C" int u1u1_cool(u1u1_lattice* h, double dt, int nsteps, void* stream) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(U1U1_ERR_INVALID_ARG, "dt must be > 0");
+  if (nsteps < 0) return fail(U1U1_ERR_INVALID_ARG, "nsteps must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = h->esize == 8 ? cool_t<double>(h, dt, nsteps, st) : cool_t<float>(h, dt, nsteps, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cooling");
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_set_params(u1u1_lattice* h, const u1u1_params* p, int64_t n) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  int rc = u1u1_check_params(p);
+  if (rc) return rc;
+  if (p->nx != h->p.nx || p->ny != h->p.ny || p->nz != h->p.nz || p->precision != h->p.precision)
+    return fail(U1U1_ERR_INVALID_ARG, "lattice sides and precision must stay the same");
+  u1u1_params q = *p;
+  q.seed = h->p.seed;
+  h->p = q;
+  h->n = n;
+  return U1U1_OK;
+}
+
 // host epilogue (Sec. III.A): raw sums and counts -> estimators
 static double sqrt_ratio(double num, double den) {
   if (den == 0.0) return INFINITY;
@@ -512,6 +581,60 @@ extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* ce
   int rc = read_scratch(h, &r, st);
   if (rc) return rc;
   to_strings(&h->p, r, out);
+  return U1U1_OK;
+}
+
+extern "C" int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells, int32_t* labels_out,
+                                u1u1_segments* out, void* stream) {
+  if (!h || !out) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  if (overlap_tol < 0 || overlap_tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
+  if (min_cells < 0) return fail(U1U1_ERR_INVALID_ARG, "min_cells must be >= 0");
+  if (h->V > 2147483647ull) return fail(U1U1_ERR_NOT_SUPPORTED, "component labels need fewer than 2^31 sites");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!h->seg_size) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->mpq, sizeof(uint32_t) * cell_mask_words(h->p.nx, h->p.ny, h->p.nz));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->seg_label, sizeof(int) * h->V);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->seg_size, sizeof(int) * h->V);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->seg_counts, sizeof(SegCounts));
+    if (e != cudaSuccess) {
+      cudaFree(h->mpq);
+      cudaFree(h->seg_label);
+      cudaFree(h->seg_size);
+      cudaFree(h->seg_counts);
+      h->mpq = nullptr;
+      h->seg_label = h->seg_size = nullptr;
+      h->seg_counts = nullptr;
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? U1U1_ERR_OUT_OF_MEMORY : U1U1_ERR_CUDA, "segment scratch: %s",
+                  cudaGetErrorString(e));
+    }
+  }
+  MeasureOut mo{h->partials, h->faces, nullptr};
+  cudaError_t e = dispatch(h, MODE_MEASURE, mo, st);
+  if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
+  e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, nullptr, nullptr, h->masks, h->cpartials, st,
+                   h->mpq);
+  if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
+  int* label = labels_out ? (int*)labels_out : h->seg_label;
+  e = launch_segments(h->mpq, h->p.nx, h->p.ny, h->p.nz, min_cells, label, h->seg_size, h->seg_counts, st);
+  if (e != cudaSuccess) return cuda_fail(e, "segment kernels");
+  SegCounts c;
+  U1U1_CUDA_TRY(cudaMemcpyAsync(&c, h->seg_counts, sizeof(SegCounts), cudaMemcpyDeviceToHost, st), "segment counts");
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  if (c.err) return fail(U1U1_ERR_CUDA, "component labelling hit its iteration limit");
+  memset(out, 0, sizeof(*out));
+  out->n = h->n;
+  out->overlap_tol = overlap_tol;
+  out->min_cells = min_cells;
+  out->n_cells = (int64_t)c.n_cells;
+  out->n_components = (int64_t)c.n_components;
+  out->n_segments = (int64_t)c.n_segments;
+  out->largest = (int64_t)c.largest;
+  out->L_pq = h->p.dx * (double)c.sum_len;
+  out->l_pq = c.n_segments ? out->L_pq / (double)c.n_segments : NAN;
+  const double vol = (double)h->V * h->p.dx * h->p.dx * h->p.dx;
+  out->xi_pq = sqrt_ratio(vol, out->L_pq);
   return U1U1_OK;
 }
 

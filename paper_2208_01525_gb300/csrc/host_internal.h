@@ -54,6 +54,10 @@ struct u1u1_lattice {
   int npartials;
   CellPartial* cpartials;
   int ncpartials;
+  uint32_t* mpq;      // bound-state cell bits (segments), lazily allocated
+  int* seg_label;     // component labels (segments), lazily allocated
+  int* seg_size;
+  u1u1::SegCounts* seg_counts;
   RawRecord* ring;
   RawRecord* scratch_rec;
   RawRecord* host_rec;  // pinned, RING_CAP entries

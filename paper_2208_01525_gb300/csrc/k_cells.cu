@@ -75,7 +75,7 @@ __device__ __forceinline__ uint32_t xdilate(const uint32_t* m, long long rowbase
 
 __global__ void __launch_bounds__(OVL_THREADS)
 k_overlap(const uint32_t* __restrict__ mp, const uint32_t* __restrict__ mq, int nx, int ny, int nz, int words,
-          int tol, CellPartial* part) {
+          int tol, CellPartial* part, uint32_t* mpq) {
   const long long nw = (long long)ny * nz * words;
   long long cnt[2] = {0, 0};
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nw;
@@ -87,9 +87,13 @@ k_overlap(const uint32_t* __restrict__ mp, const uint32_t* __restrict__ mq, int 
     if (tol == 0) {
       cnt[0] += __popc(p & q);
       cnt[1] += __popc(p & q);
+      if (mpq) mpq[idx] = p & q;
       continue;
     }
-    if ((p | q) == 0) continue;
+    if ((p | q) == 0) {
+      if (mpq) mpq[idx] = 0u;
+      continue;
+    }
     uint32_t dq = 0, dp = 0;
     for (int dz = -1; dz <= 1; ++dz) {
       const int zz = z + dz < 0 ? nz - 1 : (z + dz >= nz ? 0 : z + dz);
@@ -102,6 +106,7 @@ k_overlap(const uint32_t* __restrict__ mp, const uint32_t* __restrict__ mq, int 
     }
     cnt[0] += __popc(p & dq);
     cnt[1] += __popc(q & dp);
+    if (mpq) mpq[idx] = p & dq;  // the p-anchored bound-state cells
   }
   __shared__ long long sm[OVL_THREADS / 32][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -200,7 +205,7 @@ int cells_grid_blocks() { return OVL_BLOCKS; }
 size_t cell_mask_words(int nx, int ny, int nz) { return (size_t)((nx + 31) / 32) * ny * nz; }
 
 cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p, uint8_t* cell_q,
-                         uint32_t* masks, CellPartial* part, cudaStream_t st) {
+                         uint32_t* masks, CellPartial* part, cudaStream_t st, uint32_t* mpq) {
   const int words = (nx + 31) / 32;
   const size_t nw = cell_mask_words(nx, ny, nz);
   uint32_t* mp = masks;
@@ -212,7 +217,7 @@ cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, 
   k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part);
+  k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part, mpq);
   return cudaGetLastError();
 }
 

@@ -152,8 +152,19 @@ cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, cudaSt
 // Cells and overlap from face bytes; masks holds 2 * cell_mask_words words.
 int cells_grid_blocks();
 size_t cell_mask_words(int nx, int ny, int nz);
+// mpq (optional, cell_mask_words words): the p-anchored bound-state cells.
 cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p,
-                         uint8_t* cell_q, uint32_t* masks, CellPartial* part, cudaStream_t st);
+                         uint8_t* cell_q, uint32_t* masks, CellPartial* part, cudaStream_t st,
+                         uint32_t* mpq = nullptr);
+
+// Connected components of the bound-state cells (robust method).
+struct SegCounts {
+  unsigned long long n_cells, n_components, n_segments, sum_len, largest;
+  int err;  // nonzero when a union-find loop hit its iteration limit
+  int pad;
+};
+cudaError_t launch_segments(const uint32_t* mpq, int nx, int ny, int nz, int min_cells, int* label, int* size,
+                            SegCounts* counts, cudaStream_t st);
 
 // The FP32 link-phase routine on n values (check entry point).
 cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n, cudaStream_t st);

@@ -581,9 +581,69 @@ def pin_bruteforce_overlap():
             assert O.overlap(p, b, a, tol) == bruteforce_overlap(b, a, tol)
 
 
+def bruteforce_components(mask):
+    """Periodic 26-connected labelling by repeated relaxation: every cell takes
+    the smallest label among itself and its 26 neighbours until nothing
+    changes (labels start as the site indices)."""
+    nz, ny, nx = mask.shape
+    big = np.iinfo(np.int64).max
+    lab = np.where(mask > 0, np.arange(mask.size).reshape(mask.shape), big)
+    while True:
+        best = lab.copy()
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    sh = np.roll(lab, (dz, dy, dx), axis=(0, 1, 2))
+                    best = np.minimum(best, np.where(mask > 0, sh, big))
+        best = np.where(mask > 0, best, big)
+        if np.array_equal(best, lab):
+            return np.where(mask > 0, lab, -1)
+        lab = best
+
+
+def pin_components():
+    """Connected components of cell masks (the robust method's connectivity
+    filter, Sec. III.B): agree with an independent relaxation labelling on
+    random periodic masks; cells touching only at a corner are joined
+    (26-connectivity); the pq mask agrees with the overlap count."""
+    p = O.Params(9, 8, 7)
+    for seed, dens in ((1, 0.08), (2, 0.2), (3, 0.35)):
+        rng = np.random.default_rng(seed)
+        m = (rng.random(p.shape) < dens).astype(np.uint8)
+        assert np.array_equal(O.components(p, m), bruteforce_components(m))
+    m = np.zeros(p.shape, dtype=np.uint8)
+    m[1, 1, 1] = m[2, 2, 2] = 1          # corner contact
+    m[5, 6, 8] = m[5, 6, 0] = 1          # face contact across the periodic x boundary
+    lab = O.components(p, m)
+    assert lab[2, 2, 2] == lab[1, 1, 1] and lab[5, 6, 0] == lab[5, 6, 8]
+    assert len(np.unique(lab[lab >= 0])) == 2
+    a = synth.sparse_cells(p.shape, 0.1, 5)
+    b = synth.sparse_cells(p.shape, 0.1, 6)
+    for tol in (0, 1):
+        assert int(O.pq_mask(p, a, b, tol).sum()) == O.overlap(p, a, b, tol)
+
+
+def pin_segments_planted():
+    """Four planted straight strings in both sectors (synth.vortex_map): the
+    pq cells form four periodic lines of nz cells, so there are four segments
+    of length (nz - 1) dx each (Eq. 38 with the off-by-one correction) when
+    nz exceeds the threshold, none otherwise."""
+    shape = (14, 12, 16)
+    nz, ny, nx = shape
+    p = O.Params(nx, ny, nz, m=0.0)
+    st = O.new_state(p)
+    vm = synth.vortex_map(shape)
+    st[0], st[1], st[2], st[3] = vm.real, vm.imag, vm.real, vm.imag
+    r = O.segments(p, st, tol=1, min_cells=10)
+    assert r["n_cells"] == 4 * nz and r["n_components"] == 4 and r["n_segments"] == 4
+    assert r["L_pq"] == 4 * (nz - 1) * p.dx and r["l_pq"] == (nz - 1) * p.dx
+    assert O.segments(p, st, tol=1, min_cells=nz)["n_segments"] == 0
+
+
 ALL_PINS = [
     pin_gauss_conserved, pin_gauss_step_identity, pin_energy_second_order,
     pin_linear_dispersion, pin_homogeneous_modes, pin_gauge_covariance, pin_sector_swap,
     pin_kappa_decoupling, pin_winding_topology, pin_planted_vortices, pin_bruteforce_windings, pin_bruteforce_overlap,
-    pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic,
+    pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic, pin_components,
+    pin_segments_planted,
 ]

@@ -36,7 +36,8 @@ MUTATIONS = [
      "+ edge_chi(p, st, s, i, xj, &cut) - edge_chi(p, st, s, j, site, &cut);"),
     ("winding_without_links", "tot += p->dx * (get_A(p, st, s, i, site)", "tot += 0.0 * (get_A(p, st, s, i, site)"),
     ("cell_wrong_face", "abs(w[0 * V + site]) + abs(w[0 * V + zp])", "abs(w[0 * V + site]) + abs(w[0 * V + site])"),
-    ("overlap_one_sided", "for (int dz = -tol; dz <= tol && !hit; ++dz)", "for (int dz = 0; dz <= tol && !hit; ++dz)"),
+    ("overlap_one_sided", "        int hit = 0;\n        for (int dz = -tol; dz <= tol && !hit; ++dz)",
+     "        int hit = 0;\n        for (int dz = 0; dz <= tol && !hit; ++dz)"),
     ("kinetic_not_averaged", "kin[s] = 0.5 * (pm2 + pp2);", "kin[s] = pp2;"),
     ("magnetic_factor", "mag[s] = g * f2;", "mag[s] = 0.5 * g * f2;"),
     ("lagrangian_potential_sign", "+ (kin[1] - grad[1] + el[1] - mag[1]) - pot;",
@@ -46,6 +47,9 @@ MUTATIONS = [
     ("gauss_charge_factor", "double ct_prev = have_prev ? cfm[5] : 0.0;", "double ct_prev = have_prev ? cfm[2] : 0.0;"),
     ("ic_phase_range", "double th = (2.0 * M_PI) * u;", "double th = M_PI * u;"),
     ("electric_energy_factor", "e2sum += 0.5 * (em * em + ep * ep);", "e2sum += (em * em + ep * ep);"),
+    ("components_one_sided", "          for (int dx = -1; dx <= 1; ++dx) {\n            long nb",
+     "          for (int dx = 0; dx <= 1; ++dx) {\n            long nb"),
+    ("pq_mask_anchor_ignored", "        if (anchor[site] > 0)\n", "        if (anchor[site] >= 0)\n"),
 ]
 
 
