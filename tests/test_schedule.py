@@ -69,7 +69,10 @@ def test_schedule_gpu_matches_oracle(era, physical):
     got = lat.state().cpu().numpy()
     p0 = O.Params(20, 16, 12, seed=21)
     ref = oracle_run(p0, phases, O.init(p0))
-    scale = np.abs(ref).reshape(20, -1).max(axis=1)
-    err = np.abs(got - ref).reshape(20, -1).max(axis=1) / np.where(scale > 0, scale, 1)
+    # relative to each field's maximum, but never to a scale below the unit
+    # vacuum value: after the heavily damped phase (m_damp gives delta ~ 2)
+    # the momenta are many orders of magnitude below the fields
+    scale = np.maximum(np.abs(ref).reshape(20, -1).max(axis=1), 1.0)
+    err = np.abs(got - ref).reshape(20, -1).max(axis=1) / scale
     assert err.max() < 1e-10, err
     assert torch.cuda.is_available()
