@@ -300,7 +300,7 @@ def run_ours(args):
         barrier()
         e2e_s = time.perf_counter() - t0
         state_bytes = 20 * V * lat.dtype.itemsize
-        rec_bytes = 312  # one detection record copied per period
+        rec_bytes = 360  # one detection record copied per period
         e2e = {"value": site_updates / e2e_s, "unit": "site-updates/s",
                "h2d_bytes_per_step": state_bytes / args.steps,
                "d2h_bytes_per_step": state_bytes / args.steps + rec_bytes,

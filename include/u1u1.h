@@ -122,6 +122,8 @@ typedef struct {
   int64_t n_flagged;    /* plaquette windings within 1e-4 of the +-pi branch cut */
   int32_t max_abs_w;    /* largest |W| seen */
   int32_t overlap_tol;  /* cell displacement allowed by the overlap (0 or 1) */
+  int64_t n_w2_p, n_w2_q;           /* plaquettes with |W| >= 2 per sector (higher-winding census) */
+  int64_t n_cells_ge4_p, n_cells_ge4_q; /* cells of value >= 4, e.g. a (2,0) string (Sec. III.B) */
   double L_p, L_q, L_pq;      /* dx * counts, L_s with L_pq subtracted */
   double xi_p, xi_q, xi_pq;   /* Eq. 31; +inf when the length is 0 */
   double xi_w;                /* Eq. 32 */
@@ -135,10 +137,14 @@ typedef struct {
   double eta, a;
   double kin_p, kin_q, grad_p, grad_q, el_p, el_q, mag_p, mag_q; /* lattice sums */
   double pot, vint;     /* sum c_n V and sum kappa(|phi|^2-sigma_p^2)(|psi|^2-sigma_q^2) */
+  double pot_p, pot_q;  /* sum c_n lambda_s/4 (|phi_s|^2 - sigma_s^2)^2 per sector */
   double lag, energy;   /* sum of the Lagrangian and of the energy density */
   double rl_num, rl_den, rpq_num, rpq_den; /* Eq. 37 sums, W = L and W = V_int */
   double lag_total, energy_total; /* the sums times dx^3 */
   double xi_l;          /* Eq. 33 with mu = 2 pi sigma_p^2 */
+  double lag_p, lag_q;  /* per-sector Lagrangian sums (own kinetic, gradient, gauge and
+                           self-potential terms, the interaction term left out), times dx^3 */
+  double xi_l_p, xi_l_q; /* Eq. 33 per sector with mu_s = 2 pi sigma_s^2, for unequal tensions */
   double R_l, v2_l, R_pq, v2_pq; /* Eqs. 36-37 */
   int32_t has_gauss;    /* 1 when the Gauss fields below were computed */
   double gauss_sum_p, gauss_sum_q, charge_sum_p, charge_sum_q;

@@ -41,7 +41,7 @@ MOM_FIELDS = tuple(range(10, 20))
 DIAG_NAMES = (
     "kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q", "pot", "vint",
     "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den",
-    "gauss_sum_p", "gauss_sum_q", "charge_sum_p", "charge_sum_q",
+    "gauss_sum_p", "gauss_sum_q", "charge_sum_p", "charge_sum_q", "pot_p", "pot_q",
     "gauss_max_p", "gauss_max_q", "phi_min_p", "phi_max_p", "phi_min_q", "phi_max_q",
     "nan_count",
 )
@@ -331,6 +331,8 @@ def strings(p: Params, st: np.ndarray, tol: int = 1) -> dict:
         n_pq_cell_q=n_pq_cell_q, n_flagged=int(F.sum()),
         max_abs_w=int(absW.max()) if absW.size else 0,
         nonzero_p=int((W[0] != 0).sum()), nonzero_q=int((W[1] != 0).sum()),
+        n_w2_p=int((absW[0] >= 2).sum()), n_w2_q=int((absW[1] >= 2).sum()),
+        n_cells_ge4_p=int((C[0] >= 4).sum()), n_cells_ge4_q=int((C[1] >= 4).sum()),
         L_p=L_p, L_q=L_q, L_pq=L_pq,
         xi_p=_sqrt_ratio(vol, L_p), xi_q=_sqrt_ratio(vol, L_q), xi_pq=_sqrt_ratio(vol, L_pq),
         xi_w=_sqrt_ratio(vol, tot),
@@ -352,6 +354,12 @@ def diagnostics(p: Params, st: np.ndarray, n: int) -> dict:
     out["energy_total"] = dx3 * s["energy"]
     out["lag_total"] = dx3 * s["lag"]
     out["xi_l"] = _sqrt_ratio(-mu * vol, dx3 * s["lag"])
+    # per-sector Lagrangians (self-potential only, the interaction term left
+    # out) and their separations with mu_s = 2 pi sigma_s^2 (unequal tensions)
+    for k, sec in enumerate("pq"):
+        lag_s = dx3 * ((s["kin_" + sec] - s["grad_" + sec] + s["el_" + sec] - s["mag_" + sec]) - s["pot_" + sec])
+        out["lag_" + sec] = lag_s
+        out["xi_l_" + sec] = _sqrt_ratio(-2.0 * math.pi * p.sigma[k] ** 2 * vol, lag_s)
     for tag, num, den in (("l", "rl_num", "rl_den"), ("pq", "rpq_num", "rpq_den")):
         R = s[num] / s[den] if s[den] != 0.0 else math.nan
         out["R_" + tag] = R

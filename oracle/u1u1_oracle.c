@@ -452,6 +452,7 @@ enum {
   D_KIN_P, D_KIN_Q, D_GRAD_P, D_GRAD_Q, D_EL_P, D_EL_Q, D_MAG_P, D_MAG_Q, D_POT, D_VINT,
   D_LAG, D_ENERGY, D_RL_NUM, D_RL_DEN, D_RPQ_NUM, D_RPQ_DEN,
   D_GAUSS_SUM_P, D_GAUSS_SUM_Q, D_CHARGE_SUM_P, D_CHARGE_SUM_Q,
+  D_POT_P, D_POT_Q,
   D_NSUMS, /* compensated sums above, extrema below */
   D_GAUSS_MAX_P = D_NSUMS, D_GAUSS_MAX_Q, D_PHI_MIN_P, D_PHI_MAX_P, D_PHI_MIN_Q, D_PHI_MAX_Q,
   D_NAN, D_NOUT
@@ -468,6 +469,7 @@ int orc_diag_count(void) { return D_NOUT; }
  *   el_s   = sum_i (E_i^-^2 + E_i^+^2) / 2 / (2 e_s^2 c_n)
  *   mag_s  = sum_{i<j} F_ij^2 / (2 e_s^2 c_n)
  *   pot    = c_n V(phi, psi), V of Eq. 4 with lambda_0, kappa_0
+ *   pot_s  = c_n lambda_s/4 (|phi_s|^2 - sigma_s^2)^2, the self-potential of sector s
  *   vint   = kappa_0 (|phi|^2 - sigma_p^2)(|psi|^2 - sigma_q^2)
  *   L_x    = sum_s (kin - grad + el - mag) - pot           (Lagrangian)
  *   H_x    = sum_s (kin + grad + el + mag) + pot           (energy)
@@ -545,6 +547,8 @@ void orc_diagnostics(const orc_params* p, const double* st, long n, double* out,
     nadd(&acc[D_MAG_P], mag[0]);
     nadd(&acc[D_MAG_Q], mag[1]);
     nadd(&acc[D_POT], pot);
+    nadd(&acc[D_POT_P], c * 0.25 * p->lambda[0] * rp * rp);
+    nadd(&acc[D_POT_Q], c * 0.25 * p->lambda[1] * rq * rq);
     nadd(&acc[D_VINT], vint);
     nadd(&acc[D_LAG], L);
     nadd(&acc[D_ENERGY], H);

@@ -58,6 +58,8 @@ class CStrings(ctypes.Structure):
         ("n_pq_plaq", ctypes.c_int64), ("n_pq_cell", ctypes.c_int64), ("n_pq_cell_q", ctypes.c_int64),
         ("n_flagged", ctypes.c_int64),
         ("max_abs_w", ctypes.c_int32), ("overlap_tol", ctypes.c_int32),
+        ("n_w2_p", ctypes.c_int64), ("n_w2_q", ctypes.c_int64),
+        ("n_cells_ge4_p", ctypes.c_int64), ("n_cells_ge4_q", ctypes.c_int64),
         ("L_p", ctypes.c_double), ("L_q", ctypes.c_double), ("L_pq", ctypes.c_double),
         ("xi_p", ctypes.c_double), ("xi_q", ctypes.c_double), ("xi_pq", ctypes.c_double),
         ("xi_w", ctypes.c_double), ("f_total", ctypes.c_double), ("f_p", ctypes.c_double),
@@ -74,8 +76,9 @@ class CSegments(ctypes.Structure):
 
 
 _DIAG_DOUBLES_1 = ["eta", "a", "kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q",
-                   "pot", "vint", "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den",
-                   "lag_total", "energy_total", "xi_l", "R_l", "v2_l", "R_pq", "v2_pq"]
+                   "pot", "vint", "pot_p", "pot_q", "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den",
+                   "lag_total", "energy_total", "xi_l", "lag_p", "lag_q", "xi_l_p", "xi_l_q",
+                   "R_l", "v2_l", "R_pq", "v2_pq"]
 _DIAG_DOUBLES_2 = ["gauss_sum_p", "gauss_sum_q", "charge_sum_p", "charge_sum_q", "gauss_max_p",
                    "gauss_max_q", "gauss_rel_p", "gauss_rel_q", "phi_min_p", "phi_max_p",
                    "phi_min_q", "phi_max_q"]

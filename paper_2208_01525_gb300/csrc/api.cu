@@ -195,6 +195,7 @@ static int check_buffers(const u1u1_params* p, const u1u1_buffers* b) {
 void u1u1::lattice_free_scratch(u1u1_lattice* h) {
   if (!h) return;
   cudaFree(h->faces);
+  cudaFree(h->ge4);
   cudaFree(h->masks);
   cudaFree(h->mpq);
   cudaFree(h->seg_label);
@@ -228,6 +229,7 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   h->ncpartials = cells_grid_blocks();
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->faces, 2 * h->V);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->ge4, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&h->masks, 2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(BlockPartial) * (size_t)h->npartials);
@@ -383,11 +385,11 @@ extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* st
     if (e != cudaSuccess) return cuda_fail(e, "step kernel");
     if (det) {
       e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, h->overlap_tol, nullptr, nullptr, h->masks,
-                       h->cpartials, st);
+                       h->cpartials, st, nullptr, h->ge4);
       if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
       RawRecord* slot = h->ring + (h->rec_written % RING_CAP);
       e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, slot, (long long)h->n,
-                          1, 0, 1, h->overlap_tol, st);
+                          1, 0, 1, h->overlap_tol, st, h->ge4);
       if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
       h->rec_written++;
     }
@@ -485,6 +487,10 @@ void u1u1::to_strings(const u1u1_params* p, const RawRecord& r, u1u1_strings* s)
   s->n_flagged = r.cnt[C_FLAGGED];
   s->max_abs_w = (int32_t)r.cnt[C_MAXW];
   s->overlap_tol = r.tol;
+  s->n_w2_p = r.cnt[C_W2P];
+  s->n_w2_q = r.cnt[C_W2Q];
+  s->n_cells_ge4_p = r.cells[2];
+  s->n_cells_ge4_q = r.cells[3];
   const double dx = p->dx;
   const double vol = (double)p->nx * p->ny * p->nz * dx * dx * dx;
   s->L_pq = dx * (double)s->n_pq_cell;
@@ -516,6 +522,8 @@ static void to_diag(const u1u1_params* p, const RawRecord& r, u1u1_diag* d) {
   d->mag_q = r.sum[S_MAG_Q];
   d->pot = r.sum[S_POT];
   d->vint = r.sum[S_VINT];
+  d->pot_p = r.sum[S_POT_P];
+  d->pot_q = r.sum[S_POT_Q];
   // the Lagrangian and energy densities are linear in the component
   // densities, so their lattice sums are formed from the component sums
   d->lag = (d->kin_p - d->grad_p + d->el_p - d->mag_p) + (d->kin_q - d->grad_q + d->el_q - d->mag_q) - d->pot;
@@ -530,6 +538,10 @@ static void to_diag(const u1u1_params* p, const RawRecord& r, u1u1_diag* d) {
   d->lag_total = dx3 * d->lag;
   d->energy_total = dx3 * d->energy;
   d->xi_l = sqrt_ratio(-mu * vol, d->lag_total);
+  d->lag_p = dx3 * ((d->kin_p - d->grad_p + d->el_p - d->mag_p) - d->pot_p);
+  d->lag_q = dx3 * ((d->kin_q - d->grad_q + d->el_q - d->mag_q) - d->pot_q);
+  d->xi_l_p = sqrt_ratio(-TWO_PI * p->sigma_p * p->sigma_p * vol, d->lag_p);
+  d->xi_l_q = sqrt_ratio(-TWO_PI * p->sigma_q * p->sigma_q * vol, d->lag_q);
   d->R_l = d->rl_den != 0.0 ? d->rl_num / d->rl_den : NAN;
   d->v2_l = 2.0 * d->R_l / (1.0 + d->R_l);
   d->R_pq = d->rpq_den != 0.0 ? d->rpq_num / d->rpq_den : NAN;
@@ -572,10 +584,11 @@ extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* ce
   MeasureOut mo{h->partials, h->faces, windings};
   cudaError_t e = dispatch(h, MODE_MEASURE, mo, st);
   if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
-  e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->masks, h->cpartials, st);
+  e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->masks, h->cpartials, st,
+                   nullptr, h->ge4);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
   e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, h->scratch_rec,
-                      (long long)h->n, 1, 0, 1, overlap_tol, st);
+                      (long long)h->n, 1, 0, 1, overlap_tol, st, h->ge4);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   RawRecord r;
   int rc = read_scratch(h, &r, st);

@@ -54,6 +54,7 @@ struct u1u1_lattice {
   int npartials;
   CellPartial* cpartials;
   int ncpartials;
+  unsigned long long* ge4;  // census counters of cells with value >= 4
   uint32_t* mpq;      // bound-state cell bits (segments), lazily allocated
   int* seg_label;     // component labels (segments), lazily allocated
   int* seg_size;

@@ -27,7 +27,7 @@ __device__ __forceinline__ int face_w(const uint8_t* f, long long i, int k) { re
 
 __global__ void __launch_bounds__(32 * ROWS_PER_BLOCK)
 k_cellbits(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words, uint8_t* cell_p, uint8_t* cell_q,
-           uint32_t* mp, uint32_t* mq) {
+           uint32_t* mp, uint32_t* mq, unsigned long long* ge4) {
   const long long V = (long long)nx * ny * nz;
   const long long nrows = (long long)ny * nz;
   const int lane = threadIdx.x;
@@ -56,6 +56,15 @@ k_cellbits(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words,
     if (lane == 0) {
       mp[row * words + w] = bp;
       mq[row * words + w] = bq;
+    }
+    if (ge4) {
+      // census of cells pierced by winding two or more (value >= 4)
+      const uint32_t b4p = __ballot_sync(0xffffffffu, c[0] >= 4);
+      const uint32_t b4q = __ballot_sync(0xffffffffu, c[1] >= 4);
+      if (lane == 0 && (b4p | b4q)) {
+        atomicAdd(&ge4[0], (unsigned long long)__popc(b4p));
+        atomicAdd(&ge4[1], (unsigned long long)__popc(b4q));
+      }
     }
   }
 }
@@ -133,7 +142,8 @@ __device__ __forceinline__ void merge_pair(double& s, double& c, double s2, doub
 
 __global__ void __launch_bounds__(FIN_THREADS)
 k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __restrict__ cpart, int ncb,
-           RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol) {
+           RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol,
+           const unsigned long long* __restrict__ ge4) {
   __shared__ double ss[FIN_THREADS], sc[FIN_THREADS];
   __shared__ long long sl[FIN_THREADS];
   const int t = threadIdx.x;
@@ -190,6 +200,8 @@ k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __r
     __syncthreads();
   }
   if (t == 0) {
+    rec->cells[2] = ge4 ? (long long)ge4[0] : 0;
+    rec->cells[3] = ge4 ? (long long)ge4[1] : 0;
     rec->n = n;
     rec->has_diag = has_diag;
     rec->has_gauss = has_gauss;
@@ -205,7 +217,8 @@ int cells_grid_blocks() { return OVL_BLOCKS; }
 size_t cell_mask_words(int nx, int ny, int nz) { return (size_t)((nx + 31) / 32) * ny * nz; }
 
 cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p, uint8_t* cell_q,
-                         uint32_t* masks, CellPartial* part, cudaStream_t st, uint32_t* mpq) {
+                         uint32_t* masks, CellPartial* part, cudaStream_t st, uint32_t* mpq,
+                         unsigned long long* ge4) {
   const int words = (nx + 31) / 32;
   const size_t nw = cell_mask_words(nx, ny, nz);
   uint32_t* mp = masks;
@@ -214,7 +227,11 @@ cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, 
   long long gy = (nrows + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
   if (gy > BITS_BLOCKS_Y) gy = BITS_BLOCKS_Y;
   dim3 block(32, ROWS_PER_BLOCK), grid(words, (unsigned)gy);
-  k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq);
+  if (ge4) {
+    cudaError_t e0 = cudaMemsetAsync(ge4, 0, 2 * sizeof(unsigned long long), st);
+    if (e0 != cudaSuccess) return e0;
+  }
+  k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq, ge4);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part, mpq);
@@ -223,9 +240,9 @@ cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, 
 
 cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart, int ncblocks,
                             RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol,
-                            cudaStream_t st) {
+                            cudaStream_t st, const unsigned long long* ge4) {
   k_finalize<<<1, FIN_THREADS, 0, st>>>(part, nblocks, cpart, ncblocks, rec, n, has_diag, has_gauss, has_strings,
-                                        tol);
+                                        tol, ge4);
   return cudaGetLastError();
 }
 

@@ -183,6 +183,8 @@ k_simple(LatticeView<T> v, Coef<T> c, MeasureOut mo) {
       acc.s[S_MAG_P] += (double)d[0].mag;
       acc.s[S_MAG_Q] += (double)d[1].mag;
       acc.s[S_POT] += (double)pot;
+      acc.s[S_POT_P] += (double)(c.cV * c.lam4[0] * rp * rp);
+      acc.s[S_POT_Q] += (double)(c.cV * c.lam4[1] * rq * rq);
       acc.s[S_VINT] += (double)vint;
       acc.s[S_RL_NUM] += (double)(kt * L);
       acc.s[S_RL_DEN] += (double)(gt * L);
@@ -253,6 +255,7 @@ k_simple(LatticeView<T> v, Coef<T> c, MeasureOut mo) {
           acc.cnt[s == 0 ? C_NZP : C_NZQ] += (a != 0);
           acc.cnt[C_FLAGGED] += cutk[s][k] ? 1 : 0;
           acc.cnt[C_MAXW] = max(acc.cnt[C_MAXW], (long long)a);
+          acc.cnt[s == 0 ? C_W2P : C_W2Q] += (a >= 2);
           byte |= (unsigned)min(a, 3) << FACE_SHIFT(k);
           if (cutk[s][k]) byte |= FACE_FLAG;
           if (mo.windings) mo.windings[(3 * s + k) * V + site] = (int8_t)max(-127, min(127, W[s][k]));

@@ -153,6 +153,7 @@ __device__ __forceinline__ void emit_windings(const int W01[2], const T S02[2], 
       cnt[s == 0 ? C_NZP : C_NZQ] += (aw != 0);
       cnt[C_FLAGGED] += ck[s][k] ? 1 : 0;
       cnt[C_MAXW] = max(cnt[C_MAXW], aw);
+      cnt[s == 0 ? C_W2P : C_W2Q] += (aw >= 2);
       byte |= (unsigned)min(aw, 3) << FACE_SHIFT(k);
       if (ck[s][k]) byte |= FACE_FLAG;
       if (mo.windings) mo.windings[(3 * s + k) * V + gs] = (int8_t)max(-127, min(127, W[s][k]));
@@ -466,6 +467,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
         tv[S_MAG_P] = d[0].mag;
         tv[S_MAG_Q] = d[1].mag;
         tv[S_POT] = pot;
+        tv[S_POT_P] = c.cV * c.lam4[0] * rp * rp;
+        tv[S_POT_Q] = c.cV * c.lam4[1] * rq * rq;
         tv[S_VINT] = vint;
         tv[S_RL_NUM] = kt * L;
         tv[S_RL_DEN] = gt * L;

@@ -18,6 +18,7 @@ enum SumIdx {
   S_KIN_P, S_KIN_Q, S_GRAD_P, S_GRAD_Q, S_EL_P, S_EL_Q, S_MAG_P, S_MAG_Q, S_POT, S_VINT,
   S_LAG, S_ENERGY, S_RL_NUM, S_RL_DEN, S_RPQ_NUM, S_RPQ_DEN,
   S_GAUSS_P, S_GAUSS_Q, S_CHARGE_P, S_CHARGE_Q,
+  S_POT_P, S_POT_Q,  // c_n lambda_s/4 (|phi_s|^2 - sigma_s^2)^2 per sector
   NSUM
 };
 enum MaxIdx {
@@ -26,6 +27,7 @@ enum MaxIdx {
 };
 enum CntIdx {
   C_NP, C_NQ, C_NZP, C_NZQ, C_NPQ_PLAQ, C_FLAGGED, C_MAXW, C_NAN,
+  C_W2P, C_W2Q,  // plaquettes with |W| >= 2 per sector
   NCNT
 };
 
@@ -44,12 +46,12 @@ struct RawRecord {
   double sum[NSUM];
   double mx[NMAX];
   long long cnt[NCNT];
-  long long cells[2];
+  long long cells[4];  // overlap p-anchored, q-anchored; cells with value >= 4, p and q
   long long n;
   int has_diag, has_gauss, has_strings, tol;
 };
 // bytes moved device -> host per detection record read
-static_assert(sizeof(RawRecord) == 312, "record layout changed: update the benchmark's byte count");
+static_assert(sizeof(RawRecord) == 360, "record layout changed: update the benchmark's byte count");
 
 // Bits of a per-site, per-sector "face byte": |W| (saturated at 3) of the
 // three plaquettes anchored at the site, plus a branch-cut flag.
@@ -153,9 +155,10 @@ cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, cudaSt
 int cells_grid_blocks();
 size_t cell_mask_words(int nx, int ny, int nz);
 // mpq (optional, cell_mask_words words): the p-anchored bound-state cells.
+// ge4 (optional, 2 counters): cells of value >= 4 per sector.
 cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, uint8_t* cell_p,
                          uint8_t* cell_q, uint32_t* masks, CellPartial* part, cudaStream_t st,
-                         uint32_t* mpq = nullptr);
+                         uint32_t* mpq = nullptr, unsigned long long* ge4 = nullptr);
 
 // Connected components of the bound-state cells (robust method).
 struct SegCounts {
@@ -172,6 +175,7 @@ cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n
 // Merge partials into a record.
 cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart,
                             int ncblocks, RawRecord* rec, long long n, int has_diag, int has_gauss,
-                            int has_strings, int tol, cudaStream_t st);
+                            int has_strings, int tol, cudaStream_t st,
+                            const unsigned long long* ge4 = nullptr);
 
 }  // namespace u1u1

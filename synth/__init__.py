@@ -72,6 +72,18 @@ def vortex_map(shape, sigma=1.0):
     return sigma * (np.sin(2 * np.pi * (X + 0.5) / nx) + 1j * np.sin(2 * np.pi * (Y + 0.5) / ny))
 
 
+def crossing_vortices(shape, sigma=1.0):
+    """Product of the four-string map in the (x, y) plane and the same map in
+    the (y, z) plane: four z-directed and four x-directed straight strings,
+    which pass through common cells at the 8 positions
+    X + 1/2 in {0, nx/2}, Y + 1/2 in {0, ny/2}, Z + 1/2 in {0, nz/2}."""
+    X, Y, Z = _grid(shape)
+    nz, ny, nx = shape
+    fxy = np.sin(2 * np.pi * (X + 0.5) / nx) + 1j * np.sin(2 * np.pi * (Y + 0.5) / ny)
+    fyz = np.sin(2 * np.pi * (Y + 0.5) / ny) + 1j * np.sin(2 * np.pi * (Z + 0.5) / nz)
+    return sigma * fxy * fyz
+
+
 def gauge_parameter(shape, seed):
     """Uniform random gauge angle Lambda in [0, 2 pi) per site."""
     rng = np.random.default_rng(seed)

@@ -545,6 +545,48 @@ def pin_string_tension():
     assert errs[1] < 0.7 * errs[0], errs
 
 
+def pin_unequal_tensions():
+    """Unequal tensions (the next step the paper names, Sec. VI): with
+    sigma_q = 0.8 and lambda_q = 2 e_q^2 the q strings are BPS with tension
+    2 pi sigma_q^2; after cooling, each sector's static energy per length
+    is 4 x 2 pi sigma_s^2 within the lattice and finite-box error, and its
+    Lagrangian separation xi_L,s = sqrt(-mu_s V / L_s), mu_s = 2 pi sigma_s^2,
+    equals the winding separation sqrt(V / L) of its four planted strings."""
+    n, dx = 32, 0.5
+    p = O.Params(n, n, 2, dx=dx, m=0.0, kappa=0.0, lam=(2.0, 1.62), e=(1.0, 0.9), sigma=(1.0, 0.8))
+    st = O.new_state(p)
+    f = synth.vortex_map(p.shape, sigma=1.0)
+    g = synth.vortex_map(p.shape, sigma=0.8)
+    st[0], st[1], st[2], st[3] = f.real, f.imag, g.real, g.imag
+    O.cool(p, st, 0.16 * dx * dx, 900)
+    d = O.diagnostics(p, st, 0)
+    vol = p.nsites * dx ** 3
+    for k, sec in enumerate("pq"):
+        e_static = dx ** 3 * (d["grad_" + sec] + d["mag_" + sec] + d["pot_" + sec])
+        tension = e_static / (p.nz * dx) / 4.0
+        assert abs(tension / (TWO_PI * p.sigma[k] ** 2) - 1.0) < 0.02, (sec, tension)
+        assert abs(d["xi_l_" + sec] / math.sqrt(vol / (4 * p.nz * dx)) - 1.0) < 0.01, sec
+
+
+def pin_higher_winding_census():
+    """Cells carrying more than one unit of winding (value >= 4, the
+    signature of a (2,0) string, Sec. III.B): four z-strings crossing four
+    x-strings (synth.crossing_vortices) share exactly 8 cells, which read 4;
+    every other pierced cell reads 2 and no plaquette carries |W| >= 2."""
+    shape = (8, 12, 16)
+    nz, ny, nx = shape
+    p = O.Params(nx, ny, nz, m=0.0)
+    st = O.new_state(p)
+    f = synth.crossing_vortices(shape)
+    st[0], st[1] = f.real, f.imag
+    st[2] = 1.0
+    r = O.strings(p, st)
+    assert r["n_p"] == 4 * nz + 4 * nx and r["max_abs_w"] == 1
+    assert r["n_w2_p"] == 0 and r["n_cells_ge4_p"] == 8 and r["n_cells_ge4_q"] == 0
+    vals, counts = np.unique(r["cells"][0], return_counts=True)
+    assert set(vals.tolist()) == {0, 2, 4} and counts[list(vals).index(4)] == 8
+
+
 def pin_random_phase_ic():
     """Initial conditions of Sec. III: |phi_s| = sigma_s at every site with a
     uniform random phase (Kolmogorov-Smirnov test against U[0, 2 pi)),
@@ -645,5 +687,5 @@ ALL_PINS = [
     pin_linear_dispersion, pin_homogeneous_modes, pin_gauge_covariance, pin_sector_swap,
     pin_kappa_decoupling, pin_winding_topology, pin_planted_vortices, pin_bruteforce_windings, pin_bruteforce_overlap,
     pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic, pin_components,
-    pin_segments_planted,
+    pin_segments_planted, pin_unequal_tensions, pin_higher_winding_census,
 ]

@@ -100,7 +100,7 @@ def _windings_compare(p, st_gpu_lat):
     assert abs(res["n_p"] - ores["n_p"]) <= nflag and abs(res["n_q"] - ores["n_q"]) <= nflag
     if nflag == 0:
         for k in ("n_p", "n_q", "nonzero_p", "nonzero_q", "n_pq_plaq", "n_pq_cell", "n_pq_cell_q",
-                  "max_abs_w"):
+                  "max_abs_w", "n_w2_p", "n_w2_q", "n_cells_ge4_p", "n_cells_ge4_q"):
             assert res[k] == ores[k], (k, res[k], ores[k])
         assert np.array_equal(res["cells"].cpu().numpy(), ores["cells"])
         for k in ("L_p", "L_q", "L_pq", "xi_p", "xi_q", "xi_pq", "xi_w", "f_total", "f_p"):
@@ -127,6 +127,24 @@ def test_windings_rough_random_state(kernel):
     lat.set_state(synth.random_state(p.shape, seed=4, a_amp=4.0))
     res, ores, nflag = _windings_compare(p, lat)
     assert res["max_abs_w"] >= 1
+
+
+def test_higher_winding_census():
+    """Crossing strings: the cells shared by two strings read 4 and are
+    counted as the oracle counts them."""
+    shape = (8, 12, 16)
+    nz, ny, nx = shape
+    for prec in (U.FP32, U.FP64):
+        p = U.Params(nx=nx, ny=ny, nz=nz, m=0.0, precision=prec)
+        st = np.zeros((20,) + shape)
+        f = synth.crossing_vortices(shape)
+        st[0], st[1] = f.real, f.imag
+        st[2] = 1.0
+        lat = U.Lattice(p)
+        lat.set_state(st)
+        r = lat.detect_strings(tol=1)
+        assert r["n_cells_ge4_p"] == 8 and r["n_w2_p"] == 0 and r["max_abs_w"] == 1
+        assert r["n_cells_ge4_q"] == 0 and r["n_p"] == 4 * nz + 4 * nx
 
 
 def test_planted_vortices_detected():
@@ -161,13 +179,13 @@ def test_diagnostics_match_oracle(prec, tol, kernel):
     od = O.diagnostics(to_oracle(p), snap, 25)
     scale = abs(od["energy"])
     for k in ("kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q", "pot", "vint",
-              "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den"):
+              "pot_p", "pot_q", "lag", "energy", "rl_num", "rl_den", "rpq_num", "rpq_den"):
         ref = od[k]
         s = scale if k in ("lag", "pot", "vint") else max(abs(ref), 1e-300)
         if k.startswith("r"):
             s = max(abs(od["rl_den"]), abs(od["rl_num"]), abs(ref))
         assert abs(d[k] - ref) <= tol * s, (k, d[k], ref)
-    for k in ("xi_l", "v2_l", "v2_pq"):
+    for k in ("xi_l", "xi_l_p", "xi_l_q", "v2_l", "v2_pq"):
         if math.isnan(od[k]):  # xi_L is undefined while the Lagrangian sum is positive
             assert math.isnan(d[k]), k
         else:
