@@ -47,6 +47,38 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# sources the leapfrog step kernel is compiled from: a recorded DRAM count is
+# used only while their hash is the one it was taken with
+STEP_KERNEL_SOURCES = ("paper_2208_01525_gb300/csrc/k_tiled.cu", "paper_2208_01525_gb300/csrc/site_math.cuh",
+                       "paper_2208_01525_gb300/csrc/u1u1_internal.cuh")
+TRAFFIC_RECORD = "profiles/leapfrog_step_fp32_1024cubed_dram.md"
+
+
+def step_kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(n, tag):
+    """DRAM bytes (read + write) of one step-kernel launch from the committed
+    ncu summary, or None when it was taken on another lattice, precision or
+    kernel source."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_RECORD)) as f:
+            kv = dict(line.split(":", 1) for line in f if line.startswith("record-"))
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if (int(kv["record-lattice"]) != n or kv["record-precision"] != tag
+                or kv["record-source-sha256"] != step_kernel_hash()):
+            return None
+        return float(kv["record-dram-bytes-per-launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload_params(U, n, precision, beta=1.0, seed=2024):
     # 2560 steps to eta = 257 for the 1024^3 box; a = 1 at the end of the run
     return U.Params.cube(n, m=0.5, beta=beta, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=seed,
@@ -358,7 +390,8 @@ def run_ours(args):
                        "lattice": n, "dx": 0.5, "deta": 0.1, "detect_every": de,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": recorded_traffic(n, tag),
+                         "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
                          "kernel": "leapfrog step", "bytes_per_site": BYTES_PER_SITE[tag],
                          "ms_per_launch": plain_ms},
             "detect_ms_per_period": det_ms,

@@ -312,6 +312,17 @@ int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
 /* Step kernel used by a handle: U1U1_KERNEL_AUTO picks the tuned one,
  * U1U1_KERNEL_SIMPLE is one thread per site with cached global loads,
  * U1U1_KERNEL_TILED the z-marching shared-memory kernel. */
+/* Autotuner: choose the step kernel and the tiled kernel's z-chunking for
+ * this handle's lattice by timing one plain step of each candidate (tiled
+ * kernel with 8, 16, 32 or 64 target waves of CTAs; the simple kernel) on
+ * the handle's own state, saving and restoring the momenta around every
+ * trial so the state is unchanged (needs 10 field arrays of temporary device
+ * memory).  The choice is applied to the handle and, when cache_path is not
+ * NULL, looked up first in / appended to that text file, keyed by GPU name,
+ * lattice and precision.  *kernel_out and *waves_out (may be NULL) receive
+ * the choice.  Synchronises `stream`.  Errors: OUT_OF_MEMORY, IO, CUDA. */
+int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kernel_out, int* waves_out, void* stream);
+
 #define U1U1_KERNEL_AUTO 0
 #define U1U1_KERNEL_SIMPLE 1
 #define U1U1_KERNEL_TILED 2
@@ -365,6 +376,15 @@ int u1u1_ensemble_set_wait_limit(u1u1_ensemble* e, int64_t ns);
  * a completion count that is never reached, so the run ends with
  * U1U1_ERR_TIMEOUT after the wait limit instead of hanging. */
 int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enable);
+
+/* Autotuner for ensembles: times a probe run of probe_steps steps of every
+ * box for each work-item z-chunk (16, 32, 64, 128 planes) and schedule
+ * (persistent, per-step), restoring every box's state and step index after
+ * each trial (needs a temporary copy of the ensemble state), keeps the
+ * fastest z-chunk and returns the fastest schedule in *mode_out for later
+ * u1u1_ensemble_run calls.  Synchronises `stream`.
+ * Errors: INVALID_ARG, STATE, OUT_OF_MEMORY, CUDA. */
+int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mode_out, int* item_lz_out, void* stream);
 
 void u1u1_ensemble_destroy(u1u1_ensemble* e);
 

@@ -184,6 +184,13 @@ class Lattice:
     def set_kernel(self, kernel: int):
         check(lib().u1u1_set_kernel(self._h, int(kernel)))
 
+    def autotune(self, cache_path=None, stream=None) -> dict:
+        """Pick the step kernel and z-chunking by timing (state unchanged)."""
+        k, w = ctypes.c_int(), ctypes.c_int()
+        check(lib().u1u1_autotune(self._h, str(cache_path).encode() if cache_path else None, ctypes.byref(k),
+                                  ctypes.byref(w), _stream_ptr(stream)))
+        return {"kernel": k.value, "waves": w.value}
+
     def kernel(self) -> int:
         k = ctypes.c_int()
         check(lib().u1u1_get_kernel(self._h, ctypes.byref(k)))
@@ -320,6 +327,13 @@ class Ensemble:
     def run(self, steps, mode: int = ENS_PERSISTENT, use_graph: bool = False, stream=None):
         arr = (ctypes.c_int * len(self.params))(*[int(s) for s in steps])
         check(lib().u1u1_ensemble_run(self._h, arr, int(mode), int(bool(use_graph)), _stream_ptr(stream)))
+
+    def autotune(self, probe_steps: int = 4, stream=None) -> dict:
+        """Pick the work-item z-chunk and schedule by timing (states unchanged)."""
+        m, lz = ctypes.c_int(), ctypes.c_int()
+        check(lib().u1u1_ensemble_autotune(self._h, int(probe_steps), ctypes.byref(m), ctypes.byref(lz),
+                                           _stream_ptr(stream)))
+        return {"mode": m.value, "item_lz": lz.value}
 
     def status(self, stream=None) -> int:
         v = ctypes.c_int()

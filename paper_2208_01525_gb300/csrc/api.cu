@@ -38,6 +38,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 namespace {
 constexpr double TWO_PI = 6.283185307179586476925286766559;
+// z-chunk targets the autotuner tries for the tiled kernel
+constexpr int AUTOTUNE_WAVES[] = {8, 16, 32, 64};
 }  // namespace
 
 
@@ -223,9 +225,12 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   memcpy(h->mom, b->mom, sizeof(h->mom));
   h->kernel = U1U1_KERNEL_AUTO;
   h->overlap_tol = 1;
+  h->tile_waves = TILE_WAVES_DEFAULT;
   h->npartials = simple_grid_blocks();
-  int tb = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)h->esize);
-  if (tb > h->npartials) h->npartials = tb;
+  for (int w : AUTOTUNE_WAVES) {  // room for every grid the tuner may choose
+    const int tb = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)h->esize, w);
+    if (tb > h->npartials) h->npartials = tb;
+  }
   h->ncpartials = cells_grid_blocks();
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->faces, 2 * h->V);
@@ -341,21 +346,19 @@ extern "C" int u1u1_set_overlap_tol(u1u1_lattice* h, int tol) {
 // stepping and measuring
 // ---------------------------------------------------------------------------
 
-static bool use_tiled(const u1u1_lattice* h) {
-  if (h->kernel == U1U1_KERNEL_SIMPLE) return false;
-  return tiled_grid_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize) > 0;
-}
+static bool use_tiled(const u1u1_lattice* h) { return h->kernel != U1U1_KERNEL_SIMPLE; }
 
 template <typename T>
 static cudaError_t run_kernel(u1u1_lattice* h, int mode, const MeasureOut& mo, cudaStream_t st) {
   LatticeView<T> v = view<T>(h);
   Coef<T> c = make_coef<T>(&h->p, h->n);
-  if (use_tiled(h)) return launch_tiled<T>(mode, v, c, mo, st);
+  if (use_tiled(h)) return launch_tiled<T>(mode, v, c, mo, st, h->tile_waves);
   return launch_simple<T>(mode, v, c, mo, st);
 }
 
 static int measure_blocks(const u1u1_lattice* h) {
-  return use_tiled(h) ? tiled_grid_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize) : simple_grid_blocks();
+  return use_tiled(h) ? tiled_grid_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize, h->tile_waves)
+                      : simple_grid_blocks();
 }
 
 static cudaError_t dispatch(u1u1_lattice* h, int mode, const MeasureOut& mo, cudaStream_t st) {
@@ -429,7 +432,8 @@ static cudaError_t cool_t(u1u1_lattice* h, double dt, int nsteps, cudaStream_t s
   const MeasureOut mo{nullptr, nullptr, nullptr};
   for (int k = 0; k < nsteps; ++k) {
     LatticeView<T> v = view<T>(h);
-    cudaError_t e = use_tiled(h) ? launch_tiled<T>(MODE_WRITE, v, c, mo, st) : launch_simple<T>(MODE_WRITE, v, c, mo, st);
+    cudaError_t e = use_tiled(h) ? launch_tiled<T>(MODE_WRITE, v, c, mo, st, h->tile_waves)
+                                 : launch_simple<T>(MODE_WRITE, v, c, mo, st);
     if (e != cudaSuccess) return e;
     h->cur ^= 1;
   }
@@ -817,3 +821,128 @@ extern "C" int u1u1_eval_link_phase(const float* theta, float* sin_out, float* c
 
 template Coef<float> u1u1::make_coef<float>(const u1u1_params*, int64_t);
 template Coef<double> u1u1::make_coef<double>(const u1u1_params*, int64_t);
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+void tune_key(const u1u1_lattice* h, char* key, size_t n) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) snprintf(prop.name, sizeof(prop.name), "unknown");
+  char name[64];
+  snprintf(name, sizeof(name), "%s", prop.name);
+  for (char* c = name; *c; ++c)
+    if (*c == ' ') *c = '_';
+  snprintf(key, n, "%s/%dx%dx%d/%s", name, h->p.nx, h->p.ny, h->p.nz, h->esize == 8 ? "fp64" : "fp32");
+}
+
+// cache lines: "<key> <kernel> <waves>"
+bool cache_lookup(const char* path, const char* key, int* kernel, int* waves) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char k[256];
+  int kk = 0, ww = 0;
+  bool found = false;
+  while (fscanf(f, "%255s %d %d", k, &kk, &ww) == 3)
+    if (strcmp(k, key) == 0) {
+      *kernel = kk;
+      *waves = ww;
+      found = true;
+    }
+  fclose(f);
+  return found;
+}
+
+}  // namespace
+
+extern "C" int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kernel_out, int* waves_out, void* stream) {
+  if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  char key[256];
+  tune_key(h, key, sizeof(key));
+  int kernel = 0, waves = 0;
+  if (cache_lookup(cache_path, key, &kernel, &waves)) {
+    h->kernel = kernel;
+    h->tile_waves = waves;
+  } else {
+    // time one plain step per candidate on the handle's own state: the step
+    // reads the current position buffer, writes the other one and updates
+    // the momenta, which are saved here and restored after every trial, so
+    // the state is unchanged afterwards
+    const size_t bytes = h->V * h->esize;
+    void* save = nullptr;
+    cudaError_t e = cudaMalloc(&save, bytes * U1U1_NMOM);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(U1U1_ERR_OUT_OF_MEMORY, "autotune needs %zu bytes to save the momenta", bytes * U1U1_NMOM);
+    }
+    auto copy_mom = [&](bool to_save) -> cudaError_t {
+      for (int f = 0; f < U1U1_NMOM; ++f) {
+        char* s = (char*)save + (size_t)f * bytes;
+        cudaError_t r = to_save ? cudaMemcpyAsync(s, h->mom[f], bytes, cudaMemcpyDeviceToDevice, st)
+                                : cudaMemcpyAsync(h->mom[f], s, bytes, cudaMemcpyDeviceToDevice, st);
+        if (r != cudaSuccess) return r;
+      }
+      return cudaSuccess;
+    };
+    const int kernel0 = h->kernel, waves0 = h->tile_waves;
+    struct Cand { int kernel, waves; };
+    Cand cands[6];
+    int nc = 0;
+    for (int w : AUTOTUNE_WAVES) cands[nc++] = {U1U1_KERNEL_TILED, w};
+    cands[nc++] = {U1U1_KERNEL_SIMPLE, TILE_WAVES_DEFAULT};
+    float best = 1e30f;
+    int bk = U1U1_KERNEL_TILED, bw = TILE_WAVES_DEFAULT;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = U1U1_OK;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) rc = cuda_fail(e, "events");
+    if (!rc && (e = copy_mom(true)) != cudaSuccess) rc = cuda_fail(e, "autotune save");
+    const MeasureOut none{nullptr, nullptr, nullptr};
+    for (int k = 0; k < nc && !rc; ++k) {
+      h->kernel = cands[k].kernel;
+      h->tile_waves = cands[k].waves;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {  // the first repetition also warms up
+        if ((e = copy_mom(false)) != cudaSuccess) { rc = cuda_fail(e, "autotune restore"); break; }
+        cudaEventRecord(e0, st);
+        if ((e = dispatch(h, MODE_WRITE, none, st)) != cudaSuccess) { rc = cuda_fail(e, "autotune step"); break; }
+        cudaEventRecord(e1, st);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "autotune sync"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < ms_best) ms_best = ms;
+      }
+      if (ms_best < best) {
+        best = ms_best;
+        bk = cands[k].kernel;
+        bw = cands[k].waves;
+      }
+    }
+    if (!rc && (e = copy_mom(false)) != cudaSuccess) rc = cuda_fail(e, "autotune restore");
+    if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "autotune sync");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (rc) {
+      h->kernel = kernel0;
+      h->tile_waves = waves0;
+      return rc;
+    }
+    h->kernel = bk;
+    h->tile_waves = bw;
+    if (cache_path) {
+      FILE* f = fopen(cache_path, "a");
+      if (!f) return fail(U1U1_ERR_IO, "cannot append to %s", cache_path);
+      fprintf(f, "%s %d %d\n", key, bk, bw);
+      fclose(f);
+    }
+  }
+  if (kernel_out) *kernel_out = h->kernel;
+  if (waves_out) *waves_out = h->tile_waves;
+  return U1U1_OK;
+}

@@ -60,6 +60,7 @@ struct u1u1_ensemble {
   long long wait_limit_ns = 2000000000LL;
   int inject = 0;
   int poisoned = 0;
+  int item_lz = ENS_LZ;  // z-chunk of a work item (tuning knob)
   std::map<std::vector<int>, std::unique_ptr<Schedule>> schedules;
   cudaStream_t capture_stream = nullptr;
 };
@@ -79,12 +80,13 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
     B.nx = h->p.nx;
     B.ny = h->p.ny;
     B.nz = h->p.nz;
-    e->ntiles[b] = ens_tile_grid(B.nx, B.ny, B.nz, &B.gx, &B.gy, &B.lz, &B.gz);
+    e->ntiles[b] = ens_tile_grid(B.nx, B.ny, B.nz, &B.gx, &B.gy, &B.lz, &B.gz, e->item_lz);
     B.ntiles = e->ntiles[b];
     B.coef0 = (long long)b * e->horizon;
   }
-  U1U1_CUDA_TRY(cudaMalloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
+  if (!e->d_boxes) U1U1_CUDA_TRY(cudaMalloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_boxes, hb.data(), sizeof(EnsBox<T>) * nb, cudaMemcpyHostToDevice), "box table copy");
+  if (e->d_coef) return U1U1_OK;  // a re-tiling keeps the coefficient table
   // per-step coefficients of every box up to the horizon
   std::vector<Coef<T>> hc((size_t)nb * e->horizon);
   for (int b = 0; b < nb; ++b)
@@ -356,5 +358,114 @@ extern "C" int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enabl
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
+  return U1U1_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: work-item z-chunk and schedule
+// ---------------------------------------------------------------------------
+
+extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mode_out, int* item_lz_out,
+                                      void* stream) {
+  if (!e) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  if (probe_steps < 1) return fail(U1U1_ERR_INVALID_ARG, "probe_steps must be >= 1");
+  if (e->poisoned) return fail(U1U1_ERR_STATE, "an earlier persistent run timed out");
+  cudaStream_t st = (cudaStream_t)stream;
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  // save every box's state (current positions and momenta) and step index
+  const int nb = e->nboxes;
+  std::vector<void*> saves(nb, nullptr);
+  std::vector<long long> n0(nb);
+  std::vector<int> c0(nb);
+  int rc = U1U1_OK;
+  for (int b = 0; b < nb && !rc; ++b) {
+    u1u1_lattice* h = e->boxes[b];
+    n0[b] = h->n;
+    c0[b] = h->cur;
+    const size_t bytes = h->V * h->esize;
+    cudaError_t err = cudaMalloc(&saves[b], bytes * U1U1_NFIELDS);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(U1U1_ERR_OUT_OF_MEMORY, "autotune needs a copy of the ensemble state");
+      break;
+    }
+    for (int f = 0; f < U1U1_NFIELDS && !rc; ++f) {
+      void* src = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
+      err = cudaMemcpy((char*)saves[b] + f * bytes, src, bytes, cudaMemcpyDeviceToDevice);
+      if (err != cudaSuccess) rc = cuda_fail(err, "autotune save");
+    }
+  }
+  auto restore = [&]() -> int {
+    for (int b = 0; b < nb; ++b) {
+      u1u1_lattice* h = e->boxes[b];
+      h->n = n0[b];
+      h->cur = c0[b];
+      const size_t bytes = h->V * h->esize;
+      for (int f = 0; f < U1U1_NFIELDS; ++f) {
+        void* dst = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
+        U1U1_CUDA_TRY(cudaMemcpy(dst, (char*)saves[b] + f * bytes, bytes, cudaMemcpyDeviceToDevice), "autotune restore");
+      }
+    }
+    return U1U1_OK;
+  };
+  const int lz0 = e->item_lz;
+  const int lzs[] = {16, 32, 64, 128};
+  const int modes[] = {U1U1_ENS_PERSISTENT, U1U1_ENS_PER_STEP};
+  float best = 1e30f;
+  int best_mode = U1U1_ENS_PERSISTENT, best_lz = lz0;
+  std::vector<int> steps(nb);
+  for (int b = 0; b < nb; ++b) steps[b] = (int)std::min<long long>(probe_steps, e->horizon - n0[b]);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (!rc && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess))
+    rc = fail(U1U1_ERR_CUDA, "events");
+  for (int lz : lzs) {
+    if (rc) break;
+    e->item_lz = lz;
+    e->schedules.clear();
+    rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
+    for (int mode : modes) {
+      if (rc) break;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first repetition also warms up
+        rc = restore();
+        if (rc) break;
+        cudaEventRecord(ev0, st);
+        rc = u1u1_ensemble_run(e, steps.data(), mode, 0, stream);
+        cudaEventRecord(ev1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(ev1) != cudaSuccess) {
+          rc = fail(U1U1_ERR_CUDA, "autotune sync");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        if (rep > 0) ms_best = ms;
+      }
+      int status = 0;
+      if (!rc) rc = u1u1_ensemble_status(e, &status, stream);
+      if (!rc && status != 0) rc = fail(status, "autotune run failed on the device");
+      if (!rc && ms_best < best) {
+        best = ms_best;
+        best_mode = mode;
+        best_lz = lz;
+      }
+    }
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  const int rrc = restore();
+  for (void* s : saves) cudaFree(s);
+  if (!rc) rc = rrc;
+  e->item_lz = rc ? lz0 : best_lz;
+  e->schedules.clear();
+  const int brc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
+  // re-sync the device step table with the restored host bookkeeping
+  for (int b = 0; b < nb; ++b) e->shadow_n[b] = -1;
+  const int src = sync_dyn(e, st);
+  if (rc) return rc;
+  if (brc) return brc;
+  if (src) return src;
+  if (mode_out) *mode_out = best_mode;
+  if (item_lz_out) *item_lz_out = best_lz;
   return U1U1_OK;
 }

@@ -46,6 +46,7 @@ struct u1u1_lattice {
   int cur;
   int64_t n;
   int kernel;       // U1U1_KERNEL_*
+  int tile_waves;   // z-chunk target of the tiled kernel (tuning knob)
   int overlap_tol;
   // scratch (owned)
   uint8_t* faces;

@@ -69,7 +69,11 @@ struct Smem {
   T chi[2][3][PM];                     // [sector][dir] edge phases (detection)
   T Eg[2][2][PG];                      // [sector][dir 0,1] E for the Gauss divergence
   uint8_t chif[2][PM];                 // [sector] branch-cut flags, bit i per dir
-  double wsum[MEAS ? TL::NT / 32 : 1][NSUM];  // per-warp FP64 running sums (detection)
+  // per-warp running sums of the detection densities, compensated (value,
+  // correction) pairs in the working precision: adding in FP64 here would
+  // run on GB300's narrow FP64 pipe once per warp, sum and plane
+  T wsum[MEAS ? TL::NT / 32 : 1][NSUM];
+  T wcmp[MEAS ? TL::NT / 32 : 1][NSUM];
 };
 
 // Copy plan of one thread: every copy moves one 16-byte chunk of one row of
@@ -215,7 +219,7 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   long long pgsite = -1;
   if (MEAS) {
     if ((tid & 31) == 0)
-      for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = 0.0;
+      for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = sm.wcmp[tid >> 5][k] = T(0);
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;  // -inf is representable in T
 #pragma unroll
@@ -528,7 +532,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
     }
     if (MEAS) {
       // one row of 32 sites per warp: reduce the plane's densities across the
-      // warp in FP32 and add them to the warp's FP64 running sums
+      // warp in the working precision and add them to the warp's compensated
+      // running sums
 #pragma unroll
       for (int k = 0; k < NSUM; ++k) {
         if (k == S_LAG || k == S_ENERGY) continue;
@@ -536,7 +541,12 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
         T v2 = tv[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v2 += __shfl_down_sync(0xffffffffu, v2, o);
-        if ((tid & 31) == 0) sm.wsum[tid >> 5][k] += (double)v2;
+        if ((tid & 31) == 0) {  // Kahan step
+          const T y = v2 - sm.wcmp[tid >> 5][k];
+          const T t = sm.wsum[tid >> 5][k] + y;
+          sm.wcmp[tid >> 5][k] = (t - sm.wsum[tid >> 5][k]) - y;
+          sm.wsum[tid >> 5][k] = t;
+        }
       }
     }
     // carries for plane z+1
@@ -568,7 +578,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
     }
     ThreadAcc ta;
 #pragma unroll
-    for (int k = 0; k < NSUM; ++k) ta.s[k] = ((tid & 31) == 0) ? sm.wsum[tid >> 5][k] : 0.0;
+    for (int k = 0; k < NSUM; ++k)
+      ta.s[k] = ((tid & 31) == 0) ? (double)sm.wsum[tid >> 5][k] - (double)sm.wcmp[tid >> 5][k] : 0.0;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) ta.mx[k] = (double)mx[k];
 #pragma unroll
@@ -594,11 +605,12 @@ struct TileShape {
   static constexpr int TX = 32, TY = 8;
 };
 
-// About 32 waves at three CTAs per SM: shorter z-chunks keep neighbouring
+// The z-chunk length follows from the number of CTAs aimed at: 152 SMs x 3
+// resident CTAs x `waves`.  About 32 waves (the default) keeps neighbouring
 // tiles close in z, so halo rows are still in L2 when the neighbour needs
 // them (measured 4% faster than 8 waves at 1024^3); at least 32 planes per
-// chunk keep the extra prologue plane below 3%.
-constexpr int TARGET_CTAS = 152 * 3 * 32;
+// chunk keep the extra prologue plane below 3%.  The autotuner may pick
+// another value per lattice shape.
 constexpr int MIN_LZ = 32;
 
 struct Grid {
@@ -606,13 +618,15 @@ struct Grid {
 };
 
 template <typename T>
-Grid tiled_grid(int nx, int ny, int nz) {
+Grid tiled_grid(int nx, int ny, int nz, int waves) {
   constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
   Grid g;
   g.gx = (nx + TX - 1) / TX;
   g.gy = (ny + TY - 1) / TY;
   const int tiles = g.gx * g.gy;
-  int chunks = (TARGET_CTAS + tiles - 1) / tiles;
+  const long long target = 152LL * 3 * (waves > 0 ? waves : TILE_WAVES_DEFAULT);
+  int chunks = (int)((target + tiles - 1) / tiles);
+  if (chunks < 1) chunks = 1;
   int lz = (nz + chunks - 1) / chunks;
   if (lz < MIN_LZ) lz = MIN_LZ;
   if (lz > nz) lz = nz;
@@ -622,7 +636,8 @@ Grid tiled_grid(int nx, int ny, int nz) {
 }
 
 template <typename T, int MODE>
-cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo, cudaStream_t st) {
+cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo, cudaStream_t st,
+                        int waves) {
   constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
   constexpr bool MEAS = (MODE & MODE_MEASURE) != 0;
   constexpr bool GAUSS = (MODE & MODE_GAUSS) != 0;
@@ -637,7 +652,7 @@ cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const Measure
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  Grid g = tiled_grid<T>(v.nx, v.ny, v.nz);
+  Grid g = tiled_grid<T>(v.nx, v.ny, v.nz, waves);
   dim3 grid(g.gx, g.gy, g.gz);
   k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz);
   return cudaGetLastError();
@@ -645,8 +660,8 @@ cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const Measure
 
 }  // namespace
 
-int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t) {
-  Grid g = sizeof_t == 8 ? tiled_grid<double>(nx, ny, nz) : tiled_grid<float>(nx, ny, nz);
+int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves) {
+  Grid g = sizeof_t == 8 ? tiled_grid<double>(nx, ny, nz, waves) : tiled_grid<float>(nx, ny, nz, waves);
   return g.gx * g.gy * g.gz;
 }
 
@@ -804,10 +819,11 @@ cudaError_t set_smem_attr(KernelT kernel, size_t bytes) {
 
 }  // namespace
 
-int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz) {
+int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, int item_lz) {
   *gx = (nx + 31) / 32;
   *gy = (ny + 7) / 8;
-  *lz = nz < ENS_LZ ? nz : ENS_LZ;
+  if (item_lz < 1) item_lz = ENS_LZ;
+  *lz = nz < item_lz ? nz : item_lz;
   *gz = (nz + *lz - 1) / *lz;
   return *gx * *gy * *gz;
 }
@@ -860,24 +876,24 @@ template cudaError_t launch_ens_step<double>(const EnsBox<double>*, const EnsDyn
 
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
-                         cudaStream_t st) {
+                         cudaStream_t st, int waves) {
   switch (mode) {
     case MODE_WRITE:
-      return launch_mode<T, MODE_WRITE>(v, c, mo, st);
+      return launch_mode<T, MODE_WRITE>(v, c, mo, st, waves);
     case MODE_WRITE | MODE_MEASURE:
-      return launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st);
+      return launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st, waves);
     case MODE_MEASURE:
-      return launch_mode<T, MODE_MEASURE>(v, c, mo, st);
+      return launch_mode<T, MODE_MEASURE>(v, c, mo, st, waves);
     case MODE_MEASURE | MODE_GAUSS:
-      return launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st);
+      return launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st, waves);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_tiled<float>(int, const LatticeView<float>&, const Coef<float>&, const MeasureOut&,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 template cudaError_t launch_tiled<double>(int, const LatticeView<double>&, const Coef<double>&,
-                                          const MeasureOut&, cudaStream_t);
+                                          const MeasureOut&, cudaStream_t, int);
 
 }  // namespace u1u1

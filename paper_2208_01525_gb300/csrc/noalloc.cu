@@ -2,8 +2,8 @@
 //
 // u1u1_detect_strings_noalloc runs the same measuring kernel, cell pass and
 // finalize as u1u1_detect_strings, but without a lattice handle: its scratch
-// (per-site winding bytes, packed cell masks, block partials and the result
-// record) is carved out of one file-scope static device array, so the call
+// (per-site winding bytes, packed cell masks, block partials, the census
+// counters and the result record) is carved out of one file-scope static device array, so the call
 // itself never calls cudaMalloc, cudaFree or any allocating routine.
 #include <cuda_runtime.h>
 #include <string.h>
@@ -53,12 +53,14 @@ int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int
   const size_t V = (size_t)p->nx * p->ny * p->nz;
   const int nblocks = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)sizeof(T));
   const int ncblocks = cells_grid_blocks();
-  // carve the scratch: face bytes, cell masks, block partials, cell partials, record
+  // carve the scratch: face bytes, cell masks, block partials, cell partials,
+  // census counters, record
   const size_t off_faces = 0;
   const size_t off_masks = off_faces + round_up(2 * V);
   const size_t off_part = off_masks + round_up(2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
   const size_t off_cpart = off_part + round_up(sizeof(BlockPartial) * (size_t)nblocks);
-  const size_t off_rec = off_cpart + round_up(sizeof(CellPartial) * (size_t)ncblocks);
+  const size_t off_ge4 = off_cpart + round_up(sizeof(CellPartial) * (size_t)ncblocks);
+  const size_t off_rec = off_ge4 + round_up(2 * sizeof(unsigned long long));
   const size_t need = off_rec + round_up(sizeof(RawRecord));
   if (need > NOALLOC_BYTES)
     return fail(U1U1_ERR_INVALID_ARG, "lattice %dx%dx%d needs %zu bytes of scratch; the static array holds %zu", p->nx,
@@ -67,10 +69,12 @@ int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int
   uint32_t* masks = (uint32_t*)(base + off_masks);
   BlockPartial* part = (BlockPartial*)(base + off_part);
   CellPartial* cpart = (CellPartial*)(base + off_cpart);
+  unsigned long long* ge4 = (unsigned long long*)(base + off_ge4);
   RawRecord* rec = (RawRecord*)(base + off_rec);
   // every scratch word read below is first written by the same call (face
-  // bytes and masks for every site, one partial per block, the record), so
-  // nothing needs clearing
+  // bytes and masks for every site, one partial per block, the record; the
+  // cell pass clears the census counters with a memset), so nothing needs
+  // clearing here
 
   LatticeView<T> v;
   for (int f = 0; f < U1U1_NPOS; ++f) {
@@ -85,9 +89,9 @@ int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int
   MeasureOut mo{part, faces, nullptr};
   cudaError_t e = launch_tiled<T>(MODE_MEASURE, v, c, mo, st);
   if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
-  e = launch_cells(faces, p->nx, p->ny, p->nz, tol, nullptr, nullptr, masks, cpart, st);
+  e = launch_cells(faces, p->nx, p->ny, p->nz, tol, nullptr, nullptr, masks, cpart, st, nullptr, ge4);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
-  e = launch_finalize(part, nblocks, cpart, ncblocks, rec, (long long)n, 1, 0, 1, tol, st);
+  e = launch_finalize(part, nblocks, cpart, ncblocks, rec, (long long)n, 1, 0, 1, tol, st, ge4);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   RawRecord r;
   U1U1_CUDA_TRY(cudaMemcpyAsync(&r, rec, sizeof(RawRecord), cudaMemcpyDeviceToHost, st), "record copy");

@@ -110,10 +110,13 @@ cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, c
                           cudaStream_t st);
 
 // Tiled z-marching kernel (FP32 and FP64).
-int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t);
+// waves: CTAs per SM-slot the z-chunking aims at (tuning knob; grid about
+// 152 x 3 x waves CTAs).
+constexpr int TILE_WAVES_DEFAULT = 32;
+int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves = TILE_WAVES_DEFAULT);
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
-                         cudaStream_t st);
+                         cudaStream_t st, int waves = TILE_WAVES_DEFAULT);
 
 // ---------------------------------------------------------------------------
 // Ensembles: per-box tables for the batched kernels.
@@ -139,9 +142,9 @@ struct EnsSched {              // one run's work-item order
   int nboxes, smax;
   long long total;
 };
-constexpr int ENS_LZ = 32;     // z-chunk of an ensemble work item
+constexpr int ENS_LZ = 32;     // default z-chunk of an ensemble work item
 
-int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz);
+int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, int item_lz = ENS_LZ);
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                                   unsigned long long* ticket, unsigned* done, int* err, long long limit_ns,

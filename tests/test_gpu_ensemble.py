@@ -110,3 +110,19 @@ def test_ensemble_errors():
     assert all(b.n == 0 for b in ens.boxes)
     with pytest.raises(U.U1U1Error):
         U.Ensemble([ps[0], U.Params(nx=8, ny=8, nz=8, precision=U.FP64)])
+
+
+def test_ensemble_autotune_keeps_states():
+    """The ensemble tuner's probe runs leave every box's state and step index
+    as they were; runs after tuning still equal the boxes stepped alone."""
+    ps = box_params()
+    ens = U.Ensemble(ps)
+    ens.run([2] * 6)
+    before = [b.state().clone() for b in ens.boxes]
+    choice = ens.autotune(probe_steps=3)
+    assert choice["mode"] in (U.ENS_PERSISTENT, U.ENS_PER_STEP) and choice["item_lz"] in (16, 32, 64, 128)
+    for b, s in zip(ens.boxes, before):
+        assert b.n == 2 and torch.equal(b.state(), s)
+    ens.run([4] * 6, mode=choice["mode"])
+    for b, p in enumerate(ps):
+        assert torch.equal(ens.boxes[b].state(), alone(p, 6)), b

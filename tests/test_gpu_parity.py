@@ -378,3 +378,30 @@ def test_link_phase_routine_accuracy():
     es = (sn.double() - torch.sin(ref)).abs().max().item()
     ec = (cs.double() - torch.cos(ref)).abs().max().item()
     assert es < 2.4e-7 and ec < 2.4e-7, (es, ec)
+
+
+def test_autotune_keeps_state_and_reuses_cache(tmp_path):
+    """The autotuner times its candidates on the handle's own state and
+    restores it; a tuned handle then steps like an untuned one (bit for bit
+    when the tiled kernel family is kept, to FP32 rounding otherwise); a
+    second handle of the same shape takes the choice from the cache file."""
+    p = radiation(96, 640, precision=U.FP32, seed=5)
+    a = U.Lattice(p)
+    a.step(5)
+    s0 = a.state().clone()
+    cache = str(tmp_path / "tune.txt")
+    choice = a.autotune(cache_path=cache)
+    assert torch.equal(a.state(), s0) and a.n == 5
+    assert choice["kernel"] in (U.KERNEL_TILED, U.KERNEL_SIMPLE)
+    b = U.Lattice(p)
+    b.step(5)
+    a.step(7)
+    b.step(7)
+    if choice["kernel"] == U.KERNEL_TILED:
+        assert torch.equal(a.state(), b.state())
+    else:
+        err = field_maxrel(host_state(a), host_state(b))
+        assert err.max() < 1e-6, err
+    c = U.Lattice(p)
+    assert c.autotune(cache_path=cache) == choice
+    assert open(cache).read().count("96x96x96") == 1
