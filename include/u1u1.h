@@ -428,6 +428,14 @@ int u1u1_detect_strings_noalloc(const u1u1_params* p, const void* const fields[U
  * reference.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
 int u1u1_eval_link_phase(const float* theta, float* sin_out, float* cos_out, int64_t n, void* stream);
 
+/* Evaluate, on n device pairs (re[k], im[k]), the FP32 routine the kernels
+ * use for the gauge-invariant edge phase chi = arg(re + i im) in [-pi, pi]
+ * of the plaquette windings (Sec. III.A: octant reduction and a minimax
+ * polynomial), writing out[k] (device array).  Lets tests bound its error
+ * against a double-precision arctangent.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+int u1u1_eval_edge_phase(const float* re, const float* im, float* out, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

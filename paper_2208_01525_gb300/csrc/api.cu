@@ -819,6 +819,15 @@ extern "C" int u1u1_eval_link_phase(const float* theta, float* sin_out, float* c
   return U1U1_OK;
 }
 
+extern "C" int u1u1_eval_edge_phase(const float* re, const float* im, float* out, int64_t n, void* stream) {
+  if (n < 0) return fail(U1U1_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return U1U1_OK;
+  if (!re || !im || !out) return fail(U1U1_ERR_INVALID_ARG, "NULL array");
+  cudaError_t e = launch_edge_phase(re, im, out, (long long)n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "edge phase kernel");
+  return U1U1_OK;
+}
+
 template Coef<float> u1u1::make_coef<float>(const u1u1_params*, int64_t);
 template Coef<double> u1u1::make_coef<double>(const u1u1_params*, int64_t);
 

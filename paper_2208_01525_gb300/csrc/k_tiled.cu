@@ -74,7 +74,15 @@ struct Smem {
   // run on GB300's narrow FP64 pipe once per warp, sum and plane
   T wsum[MEAS ? TL::NT / 32 : 1][NSUM];
   T wcmp[MEAS ? TL::NT / 32 : 1][NSUM];
+  // FP32 detection: each thread's plain sums over up to ACC_PLANES planes,
+  // folded into the warp sums once per ACC_PLANES planes
+  static constexpr bool ACC = MEAS && sizeof(T) == 4;
+  T tacc[ACC ? NSUM : 1][ACC ? TL::NT : 1];
 };
+
+// Planes a thread sums in plain FP32 before its partials join the warp's
+// compensated sums (bounds that stage's rounding by 15 ulp of the partial).
+constexpr int ACC_PLANES = 16;
 
 // Copy plan of one thread: every copy moves one 16-byte chunk of one row of
 // one field.  A row of the smem ring holds TX + 2 VEC elements: the chunk
@@ -220,6 +228,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   if (MEAS) {
     if ((tid & 31) == 0)
       for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = sm.wcmp[tid >> 5][k] = T(0);
+    if (SM::ACC)
+      for (int k = 0; k < NSUM; ++k) sm.tacc[SM::ACC ? k : 0][SM::ACC ? tid : 0] = T(0);
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;  // -inf is representable in T
 #pragma unroll
@@ -531,21 +541,30 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
       }
     }
     if (MEAS) {
-      // one row of 32 sites per warp: reduce the plane's densities across the
-      // warp in the working precision and add them to the warp's compensated
-      // running sums
+      // one row of 32 sites per warp.  FP32: add the site's densities to the
+      // thread's plain partials and, every ACC_PLANES planes and at the last
+      // plane, reduce those across the warp into the warp's compensated sums.
+      // FP64: reduce every plane.
+      const bool fold = !SM::ACC || ((z - z0) % ACC_PLANES) == ACC_PLANES - 1 || z == z1 - 1;
 #pragma unroll
       for (int k = 0; k < NSUM; ++k) {
         if (k == S_LAG || k == S_ENERGY) continue;
         if (!GAUSS && (k == S_GAUSS_P || k == S_GAUSS_Q || k == S_CHARGE_P || k == S_CHARGE_Q)) continue;
         T v2 = tv[k];
+        if (SM::ACC) {
+          T& acc = sm.tacc[SM::ACC ? k : 0][SM::ACC ? tid : 0];
+          v2 += acc;
+          acc = fold ? T(0) : v2;
+        }
+        if (fold) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v2 += __shfl_down_sync(0xffffffffu, v2, o);
-        if ((tid & 31) == 0) {  // Kahan step
-          const T y = v2 - sm.wcmp[tid >> 5][k];
-          const T t = sm.wsum[tid >> 5][k] + y;
-          sm.wcmp[tid >> 5][k] = (t - sm.wsum[tid >> 5][k]) - y;
-          sm.wsum[tid >> 5][k] = t;
+          for (int o = 16; o > 0; o >>= 1) v2 += __shfl_down_sync(0xffffffffu, v2, o);
+          if ((tid & 31) == 0) {  // Kahan step
+            const T y = v2 - sm.wcmp[tid >> 5][k];
+            const T t = sm.wsum[tid >> 5][k] + y;
+            sm.wcmp[tid >> 5][k] = (t - sm.wsum[tid >> 5][k]) - y;
+            sm.wsum[tid >> 5][k] = t;
+          }
         }
       }
     }

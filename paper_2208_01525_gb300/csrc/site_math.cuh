@@ -54,9 +54,6 @@ template <> __device__ __forceinline__ void link_sincos<float>(float x, float* s
 }
 template <> __device__ __forceinline__ void link_sincos<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
-template <typename T> __device__ __forceinline__ T atan2_t(T y, T x);
-template <> __device__ __forceinline__ float atan2_t<float>(float y, float x) { return atan2f(y, x); }
-template <> __device__ __forceinline__ double atan2_t<double>(double y, double x) { return atan2(y, x); }
 
 template <typename T> __device__ __forceinline__ T rint_t(T x);
 template <> __device__ __forceinline__ float rint_t<float>(float x) { return rintf(x); }
@@ -136,11 +133,43 @@ __device__ __forceinline__ void gauge_kick(const SectorIn<T>& in, const T E[3], 
   En[2] = c.kEa * E[2] - c.kE1 * C2 + c.kE2[s] * current_im(in, 2);
 }
 
+// arg(re + i im) in [-pi, pi] in FP32 for the edge phases.  Octant
+// reduction t = min(|re|, |im|) / max(|re|, |im|) in [0, 1], the minimax
+// odd polynomial atan(t) ~ t P(t^2) of degree 15 (Remez exchange, derived by
+// fit_atan.py; 3.7e-8 in exact arithmetic, 3.1e-7 rad measured in FP32),
+// then the octant, half-plane and sign fix-ups: pi/2 - r when |im| > |re|,
+// pi - r when re carries a minus sign (so arg(+-0 - 0 i) = +-pi), and the
+// sign of im.  A winding only needs the four edge phases of a plaquette to
+// within pi in total, and the branch is decided by the signs of re and im
+// exactly; the accuracy kept here makes the cut flag agree with a
+// correctly rounded arctangent except within rounding of its threshold.
+__device__ __forceinline__ float edge_phase_f32(float re, float im) {
+  const float ax = fabsf(re), ay = fabsf(im);
+  const float mn = fminf(ax, ay), mx = fmaxf(ax, ay);
+  const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+  const float s = t * t;
+  float p = fmaf(s, -4.054567212e-03f, 2.186295787e-02f);
+  p = fmaf(s, p, -5.591232676e-02f);
+  p = fmaf(s, p, 9.642197328e-02f);
+  p = fmaf(s, p, -1.390862955e-01f);
+  p = fmaf(s, p, 1.994656565e-01f);
+  p = fmaf(s, p, -3.332986078e-01f);
+  p = fmaf(s, p, 9.999993356e-01f);
+  float r = t * p;
+  r = ay > ax ? 1.57079632679489662f - r : r;
+  r = signbit(re) ? 3.14159265358979324f - r : r;
+  return copysignf(r, im);
+}
+
+template <typename T> __device__ __forceinline__ T edge_phase(T re, T im);
+template <> __device__ __forceinline__ float edge_phase<float>(float re, float im) { return edge_phase_f32(re, im); }
+template <> __device__ __forceinline__ double edge_phase<double>(double re, double im) { return atan2(im, re); }
+
 // Edge phase chi = arg(Re + i Im) and its branch-cut flag (pi - |chi| < 1e-4
 // or a zero product).
 template <typename T>
 __device__ __forceinline__ T edge_chi(T re, T im, bool* cut) {
-  T chi = atan2_t<T>(im, re);
+  T chi = edge_phase<T>(re, im);
   if (Consts<T>::pi() - fabs(chi) < T(1e-4) || (re == T(0) && im == T(0))) *cut = true;
   return chi;
 }
