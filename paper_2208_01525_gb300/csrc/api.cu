@@ -228,7 +228,7 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   h->tile_waves = TILE_WAVES_DEFAULT;
   h->npartials = simple_grid_blocks();
   for (int w : AUTOTUNE_WAVES) {  // room for every grid the tuner may choose
-    const int tb = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)h->esize, w);
+    const int tb = tiled_measure_blocks(p->nx, p->ny, p->nz, (int)h->esize, w, true);
     if (tb > h->npartials) h->npartials = tb;
   }
   h->ncpartials = cells_grid_blocks();
@@ -237,7 +237,9 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ge4, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&h->masks, 2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->partials, sizeof(BlockPartial) * (size_t)h->npartials);
+  // block partials, plus the finalize's first-stage slots after the last one
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&h->partials, sizeof(BlockPartial) * (size_t)(h->npartials + FIN_STAGE_BLOCKS));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->cpartials, sizeof(CellPartial) * (size_t)h->ncpartials);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ring, sizeof(RawRecord) * RING_CAP);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->scratch_rec, sizeof(RawRecord));
@@ -356,8 +358,10 @@ static cudaError_t run_kernel(u1u1_lattice* h, int mode, const MeasureOut& mo, c
   return launch_simple<T>(mode, v, c, mo, st);
 }
 
-static int measure_blocks(const u1u1_lattice* h) {
-  return use_tiled(h) ? tiled_grid_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize, h->tile_waves)
+// block partials of a measuring launch: the step kernel's, plus (tiled
+// path, when windings are taken) the windings kernel's
+static int measure_blocks(const u1u1_lattice* h, bool windings) {
+  return use_tiled(h) ? tiled_measure_blocks(h->p.nx, h->p.ny, h->p.nz, (int)h->esize, h->tile_waves, windings)
                       : simple_grid_blocks();
 }
 
@@ -391,7 +395,7 @@ extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* st
                        h->cpartials, st, nullptr, h->ge4);
       if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
       RawRecord* slot = h->ring + (h->rec_written % RING_CAP);
-      e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, slot, (long long)h->n,
+      e = launch_finalize(h->partials, measure_blocks(h, true), h->cpartials, h->ncpartials, slot, (long long)h->n,
                           1, 0, 1, h->overlap_tol, st, h->ge4);
       if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
       h->rec_written++;
@@ -591,7 +595,7 @@ extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* ce
   e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->masks, h->cpartials, st,
                    nullptr, h->ge4);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
-  e = launch_finalize(h->partials, measure_blocks(h), h->cpartials, h->ncpartials, h->scratch_rec,
+  e = launch_finalize(h->partials, measure_blocks(h, true), h->cpartials, h->ncpartials, h->scratch_rec,
                       (long long)h->n, 1, 0, 1, overlap_tol, st, h->ge4);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   RawRecord r;
@@ -659,10 +663,10 @@ extern "C" int u1u1_diagnostics(u1u1_lattice* h, u1u1_diag* out, void* stream) {
   if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
   if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  MeasureOut mo{h->partials, h->faces, nullptr};
+  MeasureOut mo{h->partials, nullptr, nullptr};  // no windings
   cudaError_t e = dispatch(h, MODE_MEASURE | MODE_GAUSS, mo, st);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics kernel");
-  e = launch_finalize(h->partials, measure_blocks(h), nullptr, 0, h->scratch_rec, (long long)h->n, 1, 1, 0,
+  e = launch_finalize(h->partials, measure_blocks(h, false), nullptr, 0, h->scratch_rec, (long long)h->n, 1, 1, 0,
                       0, st);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   RawRecord r;

@@ -33,6 +33,7 @@ k_cellbits(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words,
   const int lane = threadIdx.x;
   const int w = blockIdx.x;
   const int x = w * 32 + lane;
+  unsigned long long n4[2] = {0ull, 0ull};  // this warp's cells of value >= 4 (lane 0)
   for (long long row = (long long)blockIdx.y * ROWS_PER_BLOCK + threadIdx.y; row < nrows;
        row += (long long)gridDim.y * ROWS_PER_BLOCK) {
     const int y = (int)(row % ny), z = (int)(row / ny);
@@ -59,12 +60,111 @@ k_cellbits(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words,
     }
     if (ge4) {
       // census of cells pierced by winding two or more (value >= 4)
-      const uint32_t b4p = __ballot_sync(0xffffffffu, c[0] >= 4);
-      const uint32_t b4q = __ballot_sync(0xffffffffu, c[1] >= 4);
-      if (lane == 0 && (b4p | b4q)) {
-        atomicAdd(&ge4[0], (unsigned long long)__popc(b4p));
-        atomicAdd(&ge4[1], (unsigned long long)__popc(b4q));
+      n4[0] += (unsigned long long)__popc(__ballot_sync(0xffffffffu, c[0] >= 4));
+      n4[1] += (unsigned long long)__popc(__ballot_sync(0xffffffffu, c[1] >= 4));
+    }
+  }
+  if (ge4) {
+    // one atomic per block and sector: the dense early network has value-4
+    // cells in most rows, and per-row atomics on two counters serialised
+    __shared__ unsigned long long s4[ROWS_PER_BLOCK][2];
+    if (lane == 0) {
+      s4[threadIdx.y][0] = n4[0];
+      s4[threadIdx.y][1] = n4[1];
+    }
+    __syncthreads();
+    if (threadIdx.y == 0 && lane < 2) {
+      unsigned long long t = 0;
+      for (int r = 0; r < ROWS_PER_BLOCK; ++r) t += s4[r][lane];
+      if (t) atomicAdd(&ge4[lane], t);
+    }
+  }
+}
+
+// k_cellbits for rows whose length nx is a multiple of 32, four cells per
+// lane: 32-bit loads of four face bytes of the row, of the row above (y+1) and
+// of the plane above (z+1), the x+1 face byte of the fourth cell from the next
+// lane (from memory at a segment's end).  A warp covers a 128-cell segment of
+// one row; the pierced bits of eight lanes form one mask word.
+constexpr int SEG = 128;
+constexpr int BITS4_THREADS = 256;
+constexpr int BITS4_BLOCKS = 152 * 8;
+
+__device__ __forceinline__ int fw4(uint32_t word, int j, int k) { return (int)(word >> (8 * j + FACE_SHIFT(k))) & 3; }
+
+__global__ void __launch_bounds__(BITS4_THREADS)
+k_cellbits4(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words, uint8_t* cell_p, uint8_t* cell_q,
+            uint32_t* mp, uint32_t* mq, unsigned long long* ge4) {
+  const long long V = (long long)nx * ny * nz;
+  const long long nrows = (long long)ny * nz;
+  const int lane = threadIdx.x & 31;
+  const int segs = (nx + SEG - 1) / SEG;
+  const long long items = nrows * segs;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long n4[2] = {0ull, 0ull};
+  for (long long it = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+    const long long row = it / segs;
+    const int sg = (int)(it % segs);
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const int x = sg * SEG + 4 * lane;  // this lane's first cell
+    const bool act = x < nx;            // whole groups of eight lanes (nx % 32 == 0)
+    const long long rb = row * nx;
+    const long long rby = ((long long)z * ny + (y + 1 == ny ? 0 : y + 1)) * nx;
+    const long long rbz = ((long long)(z + 1 == nz ? 0 : z + 1) * ny + y) * nx;
+    uint32_t nib[2], nib4[2];
+    uint32_t packed[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const uint8_t* f = faces + s * V;
+      const uint32_t own = act ? __ldg((const uint32_t*)(f + rb + x)) : 0u;
+      const uint32_t up = act ? __ldg((const uint32_t*)(f + rby + x)) : 0u;
+      const uint32_t ab = act ? __ldg((const uint32_t*)(f + rbz + x)) : 0u;
+      uint32_t nxt = __shfl_down_sync(0xffffffffu, own, 1);
+      if (act && (lane == 31 || x + 4 >= nx)) nxt = __ldg((const uint32_t*)(f + rb + (x + 4 >= nx ? 0 : x + 4)));
+      nib[s] = nib4[s] = packed[s] = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t xb = j < 3 ? own >> (8 * (j + 1)) : nxt;  // face byte of x+1 in the low byte
+        const int cv = fw4(own, j, 0) + fw4(ab, j, 0) + fw4(own, j, 1) + fw4(up, j, 1) + fw4(own, j, 2) +
+                       (int)((xb >> FACE_SHIFT(2)) & 3u);
+        nib[s] |= (cv > 0 ? 1u : 0u) << j;
+        nib4[s] |= (cv >= 4 ? 1u : 0u) << j;
+        packed[s] |= (uint32_t)cv << (8 * j);
       }
+    }
+    if (act) {
+      if (cell_p) *(uint32_t*)(cell_p + rb + x) = packed[0];
+      if (cell_q) *(uint32_t*)(cell_q + rb + x) = packed[1];
+    }
+    // eight lanes' nibbles form one word
+    uint32_t wp = nib[0] << (4 * (lane & 7)), wq = nib[1] << (4 * (lane & 7));
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      wp |= __shfl_xor_sync(0xffffffffu, wp, o);
+      wq |= __shfl_xor_sync(0xffffffffu, wq, o);
+    }
+    if (act && (lane & 7) == 0) {
+      const long long wi = row * words + sg * (SEG / 32) + (lane >> 3);
+      mp[wi] = wp;
+      mq[wi] = wq;
+    }
+    n4[0] += (unsigned long long)__popc(nib4[0]);
+    n4[1] += (unsigned long long)__popc(nib4[1]);
+  }
+  if (ge4) {
+    __shared__ unsigned long long s4[BITS4_THREADS / 32][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      unsigned long long v = n4[s];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) s4[threadIdx.x >> 5][s] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      unsigned long long t = 0;
+      for (int w = 0; w < BITS4_THREADS / 32; ++w) t += s4[w][threadIdx.x];
+      if (t) atomicAdd(&ge4[threadIdx.x], t);
     }
   }
 }
@@ -138,6 +238,50 @@ constexpr int FIN_THREADS = 256;
 __device__ __forceinline__ void merge_pair(double& s, double& c, double s2, double c2) {
   neumaier_add(s, c, s2);
   c += c2;
+}
+
+// First stage: CTA j merges the contiguous slice j of the partials into
+// mid[j].  Warp w takes the quantities w, w + 8, ...; its lanes run over the
+// slice with a stride of 32 and merge their results in a fixed shuffle tree.
+__global__ void __launch_bounds__(FIN_THREADS)
+k_fin_stage(const BlockPartial* __restrict__ part, int nb, BlockPartial* __restrict__ mid) {
+  const int per = (nb + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * per, b1 = min(nb, b0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  BlockPartial* out = mid + blockIdx.x;
+  constexpr int NQ = NSUM + NMAX + NCNT;
+  for (int q = warp; q < NQ; q += FIN_THREADS / 32) {
+    if (q < NSUM) {
+      double s = 0.0, c = 0.0;
+      for (int b = b0 + lane; b < b1; b += 32) merge_pair(s, c, part[b].sum[q], part[b].comp[q]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_down_sync(0xffffffffu, s, o), c2 = __shfl_down_sync(0xffffffffu, c, o);
+        merge_pair(s, c, s2, c2);
+      }
+      if (lane == 0) {
+        out->sum[q] = s;
+        out->comp[q] = c;
+      }
+    } else if (q < NSUM + NMAX) {
+      const int k = q - NSUM;
+      double m = -INFINITY;
+      for (int b = b0 + lane; b < b1; b += 32) m = fmax(m, part[b].mx[k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+      if (lane == 0) out->mx[k] = m;
+    } else {
+      const int k = q - NSUM - NMAX;
+      long long v = 0;
+      for (int b = b0 + lane; b < b1; b += 32) v = (k == C_MAXW) ? max(v, part[b].cnt[k]) : v + part[b].cnt[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long u = __shfl_down_sync(0xffffffffu, v, o);
+        v = (k == C_MAXW) ? max(v, u) : v + u;
+      }
+      if (lane == 0) out->cnt[k] = v;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(FIN_THREADS)
@@ -231,18 +375,31 @@ cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, 
     cudaError_t e0 = cudaMemsetAsync(ge4, 0, 2 * sizeof(unsigned long long), st);
     if (e0 != cudaSuccess) return e0;
   }
-  k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq, ge4);
+  if (nx % 32 == 0)
+    k_cellbits4<<<BITS4_BLOCKS, BITS4_THREADS, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq, ge4);
+  else
+    k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq, ge4);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part, mpq);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart, int ncblocks,
+cudaError_t launch_finalize(BlockPartial* part, int nblocks, const CellPartial* cpart, int ncblocks,
                             RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol,
                             cudaStream_t st, const unsigned long long* ge4) {
-  k_finalize<<<1, FIN_THREADS, 0, st>>>(part, nblocks, cpart, ncblocks, rec, n, has_diag, has_gauss, has_strings,
-                                        tol, ge4);
+  const BlockPartial* src = part;
+  int nsrc = nblocks;
+  if (part && nblocks > FIN_STAGE_MIN) {
+    BlockPartial* mid = part + nblocks;
+    k_fin_stage<<<FIN_STAGE_BLOCKS, FIN_THREADS, 0, st>>>(part, nblocks, mid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = mid;
+    nsrc = FIN_STAGE_BLOCKS;
+  }
+  k_finalize<<<1, FIN_THREADS, 0, st>>>(src, nsrc, cpart, ncblocks, rec, n, has_diag, has_gauss, has_strings, tol,
+                                        ge4);
   return cudaGetLastError();
 }
 

@@ -61,14 +61,11 @@ struct Tile {
 template <typename T, int TX, int TY, bool MEAS = true, bool GAUSS = true>
 struct Smem {
   using TL = Tile<T, TX, TY>;
-  static constexpr int PM = MEAS ? TL::PLANE : 1;
   static constexpr int PG = GAUSS ? TL::PLANE : 1;
   T pos[3][U1U1_NPOS][TL::PLANE];      // position ring
   T P[2][2][2][TL::PLANE];             // [sector][dir 0,1][re,im] conj(U_i) phi
   T Ft[2][3][TL::PLANE];               // [sector][plane] dx F at this plane
-  T chi[2][3][PM];                     // [sector][dir] edge phases (detection)
   T Eg[2][2][PG];                      // [sector][dir 0,1] E for the Gauss divergence
-  uint8_t chif[2][PM];                 // [sector] branch-cut flags, bit i per dir
   // per-warp running sums of the detection densities, compensated (value,
   // correction) pairs in the working precision: adding in FP64 here would
   // run on GB300's narrow FP64 pipe once per warp, sum and plane
@@ -122,60 +119,6 @@ struct CopyPlan {
       if (s[k] >= 0) cp_async16(ring_buf + s[k], g[k] + zoff);
   }
 };
-// Edge phase of link d at smem point (ly, lx) of plane buffer b, to the
-// neighbour (ly + oy, lx + ox) of plane buffer bn (which is b except for d = 2).
-template <typename SM, typename T, int TX, int TY>
-__device__ __forceinline__ T chi_at(const SM& sm, int s, int d, int b, int bn, int ly, int lx,
-                                    int oy, int ox, T dx, bool* cut) {
-  using TL = Tile<T, TX, TY>;
-  const int a = TL::at(ly, lx), nb = TL::at(ly + oy, lx + ox);
-  T sn, cs;
-  link_sincos<T>(dx * sm.pos[b][4 + 3 * s + d][a], &sn, &cs);
-  T fr, fi;
-  transport_fwd<T>(cs, sn, sm.pos[bn][2 * s][nb], sm.pos[bn][2 * s + 1][nb], &fr, &fi);
-  const T ar = sm.pos[b][2 * s][a], ai = sm.pos[b][2 * s + 1][a];
-  return edge_chi<T>(ar * fr + ai * fi, ar * fi - ai * fr, cut);
-}
-
-// Finish the windings of the plane below: W_02 and W_12 from their partial
-// sums and the own edge phases chi_0, chi_1 (c0n, c1n, flags f0n) of the
-// plane above, then count and emit all three plaquettes of both sectors.
-template <typename T>
-__device__ __forceinline__ void emit_windings(const int W01[2], const T S02[2], const T S12[2], const unsigned cut[2],
-                                              const T c0n[2], const T c1n[2], const unsigned f0n[2], long long gs,
-                                              int* cnt, const MeasureOut& mo, long long V) {
-  int W[2][3];
-  bool ck[2][3];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    W[s][0] = W01[s];
-    W[s][1] = (int)rint_t<T>((S02[s] - c0n[s]) * Consts<T>::inv_two_pi());
-    W[s][2] = (int)rint_t<T>((S12[s] - c1n[s]) * Consts<T>::inv_two_pi());
-    ck[s][0] = (cut[s] & 1u) != 0;
-    ck[s][1] = (cut[s] & 2u) != 0 || (f0n[s] & 1u) != 0;
-    ck[s][2] = (cut[s] & 4u) != 0 || (f0n[s] & 2u) != 0;
-  }
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    unsigned byte = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int aw = abs(W[s][k]);
-      cnt[s == 0 ? C_NP : C_NQ] += aw;
-      cnt[s == 0 ? C_NZP : C_NZQ] += (aw != 0);
-      cnt[C_FLAGGED] += ck[s][k] ? 1 : 0;
-      cnt[C_MAXW] = max(cnt[C_MAXW], aw);
-      cnt[s == 0 ? C_W2P : C_W2Q] += (aw >= 2);
-      byte |= (unsigned)min(aw, 3) << FACE_SHIFT(k);
-      if (ck[s][k]) byte |= FACE_FLAG;
-      if (mo.windings) mo.windings[(3 * s + k) * V + gs] = (int8_t)max(-127, min(127, W[s][k]));
-    }
-    if (mo.faces) mo.faces[s * V + gs] = (uint8_t)byte;
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) cnt[C_NPQ_PLAQ] += (W[0][k] != 0 && W[1][k] != 0) ? 1 : 0;
-}
-
 // Halo point handled by thread tid, or -1: the TX + TY halo points of a
 // plane go to the first threads, so they cost one or two warp passes
 // (spreading them over all warps costs one pass per warp, measured slower).
@@ -218,13 +161,6 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
 
   T mx[NMAX];
   int cnt[NCNT];
-  // windings of plane z-1 whose (x,z) and (y,z) plaquettes still need the
-  // edge phases of plane z: W_01, the partial sums of W_02 and W_12 and the
-  // branch-cut bits, per sector
-  int pW01[2] = {0, 0};
-  T pS02[2] = {T(0), T(0)}, pS12[2] = {T(0), T(0)};
-  unsigned pcut[2] = {0u, 0u};
-  long long pgsite = -1;
   if (MEAS) {
     if ((tid & 31) == 0)
       for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = sm.wcmp[tid >> 5][k] = T(0);
@@ -382,37 +318,6 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
       q.F[2] = F[s][2];
     }
 
-    if (MEAS) {
-      // edge phases of the own site, and of the right column / top row halo
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        uint8_t fl = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          bool cut = false;
-          sm.chi[s][i][a] = edge_chi<T>(current_re(in[s], i), current_im(in[s], i), &cut);
-          fl |= cut ? (1u << i) : 0u;
-        }
-        sm.chif[s][a] = fl;
-      }
-      if (const int h = halo_point<TL::NT, TX + TY>(tid); h >= 0) {
-        const bool right = h < TY;
-        const int hy = right ? h : TY;
-        const int hx = right ? TX : h - TY;
-        const int ha = TL::at(hy, hx);
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          bool c1 = false, c2 = false;
-          const int d1 = right ? 1 : 0;  // right column needs chi_1, top row chi_0
-          T ch1 = right ? chi_at<SM, T, TX, TY>(sm, s, 1, bc, bc, hy, hx, 1, 0, dx, &c1)
-                        : chi_at<SM, T, TX, TY>(sm, s, 0, bc, bc, hy, hx, 0, 1, dx, &c1);
-          T ch2 = chi_at<SM, T, TX, TY>(sm, s, 2, bc, bn, hy, hx, 0, 0, dx, &c2);
-          sm.chi[s][d1][ha] = ch1;
-          sm.chi[s][2][ha] = ch2;
-          sm.chif[s][ha] = (uint8_t)((c1 ? (1u << d1) : 0u) | (c2 ? 4u : 0u));
-        }
-      }
-    }
     __syncthreads();
 
     // ---- phase 2: assemble the update of the own site ----
@@ -516,28 +421,6 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
             tv[s == 0 ? S_CHARGE_P : S_CHARGE_Q] = fabs(rho);
           }
         }
-
-        // plaquette windings (Sec. III.A).  The (x,y) plaquette of plane z is
-        // complete now; the (x,z) and (y,z) ones need the edge phases of
-        // plane z+1, which this thread computes as its own at the next
-        // iteration, so they are finished (and plane z emitted) there.
-        const T c0n[2] = {sm.chi[0][0][a], sm.chi[1][0][a]};
-        const T c1n[2] = {sm.chi[0][1][a], sm.chi[1][1][a]};
-        const unsigned f0n[2] = {sm.chif[0][a], sm.chif[1][a]};
-        if (pgsite >= 0) emit_windings(pW01, pS02, pS12, pcut, c0n, c1n, f0n, pgsite, cnt, mo, V);
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const T c0 = c0n[s], c1 = c1n[s], c2 = sm.chi[s][2][a];
-          const unsigned f0 = f0n[s];
-          const int ax = TL::at(ly, lx + 1), ay = TL::at(ly + 1, lx);
-          pW01[s] = plaquette_winding<T>(c0, sm.chi[s][1][ax], sm.chi[s][0][ay], c1, dx, in[s].F[0]);
-          pS02[s] = (c0 + sm.chi[s][2][ax]) - c2 + dx * in[s].F[1];
-          pS12[s] = (c1 + sm.chi[s][2][ay]) - c2 + dx * in[s].F[2];
-          const unsigned fx = sm.chif[s][ax], fy = sm.chif[s][ay];
-          pcut[s] = (((f0 & 3u) || (fx & 2u) || (fy & 1u)) ? 1u : 0u) |
-                    (((f0 & 5u) || (fx & 4u)) ? 2u : 0u) | (((f0 & 6u) || (fy & 4u)) ? 4u : 0u);
-        }
-        pgsite = gsite;
       }
     }
     if (MEAS) {
@@ -581,20 +464,6 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   cp_async_wait0();
 
   if (MEAS) {
-    if (active && pgsite >= 0) {
-      // edge phases of plane z1 (still in the ring) finish the last plane
-      const int bl = (z1 - z0 + 1) % 3;
-      T c0n[2], c1n[2];
-      unsigned f0n[2];
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        bool n0 = false, n1 = false;
-        c0n[s] = chi_at<SM, T, TX, TY>(sm, s, 0, bl, bl, ly, lx, 0, 1, dx, &n0);
-        c1n[s] = chi_at<SM, T, TX, TY>(sm, s, 1, bl, bl, ly, lx, 1, 0, dx, &n1);
-        f0n[s] = (n0 ? 1u : 0u) | (n1 ? 2u : 0u);
-      }
-      emit_windings(pW01, pS02, pS12, pcut, c0n, c1n, f0n, pgsite, cnt, mo, V);
-    }
     ThreadAcc ta;
 #pragma unroll
     for (int k = 0; k < NSUM; ++k)
@@ -896,18 +765,36 @@ template cudaError_t launch_ens_step<double>(const EnsBox<double>*, const EnsDyn
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
                          cudaStream_t st, int waves) {
+  cudaError_t e;
   switch (mode) {
     case MODE_WRITE:
       return launch_mode<T, MODE_WRITE>(v, c, mo, st, waves);
     case MODE_WRITE | MODE_MEASURE:
-      return launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st, waves);
+      e = launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st, waves);
+      break;
     case MODE_MEASURE:
-      return launch_mode<T, MODE_MEASURE>(v, c, mo, st, waves);
+      e = launch_mode<T, MODE_MEASURE>(v, c, mo, st, waves);
+      break;
     case MODE_MEASURE | MODE_GAUSS:
-      return launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st, waves);
+      e = launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st, waves);
+      break;
     default:
       return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess || !mo.faces) return e;
+  // windings on the step's input positions (a writing step leaves them in
+  // place: it writes the other position buffer)
+  PosView<T> pv;
+  for (int f = 0; f < U1U1_NPOS; ++f) pv.pos[f] = v.pin[f];
+  pv.nx = v.nx;
+  pv.ny = v.ny;
+  pv.nz = v.nz;
+  return launch_windings<T>(pv, c.dx, mo.partial + tiled_grid_blocks(v.nx, v.ny, v.nz, (int)sizeof(T), waves),
+                            mo.faces, mo.windings, st);
+}
+
+int tiled_measure_blocks(int nx, int ny, int nz, int sizeof_t, int waves, bool windings) {
+  return tiled_grid_blocks(nx, ny, nz, sizeof_t, waves) + (windings ? wind_grid_blocks(nx, ny, nz) : 0);
 }
 
 template cudaError_t launch_tiled<float>(int, const LatticeView<float>&, const Coef<float>&, const MeasureOut&,

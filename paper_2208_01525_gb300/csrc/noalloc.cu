@@ -51,14 +51,14 @@ template <typename T>
 int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int64_t n, int tol, unsigned char* base,
                u1u1_strings* out, cudaStream_t st) {
   const size_t V = (size_t)p->nx * p->ny * p->nz;
-  const int nblocks = tiled_grid_blocks(p->nx, p->ny, p->nz, (int)sizeof(T));
+  const int nblocks = tiled_measure_blocks(p->nx, p->ny, p->nz, (int)sizeof(T), TILE_WAVES_DEFAULT, true);
   const int ncblocks = cells_grid_blocks();
   // carve the scratch: face bytes, cell masks, block partials, cell partials,
   // census counters, record
   const size_t off_faces = 0;
   const size_t off_masks = off_faces + round_up(2 * V);
   const size_t off_part = off_masks + round_up(2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
-  const size_t off_cpart = off_part + round_up(sizeof(BlockPartial) * (size_t)nblocks);
+  const size_t off_cpart = off_part + round_up(sizeof(BlockPartial) * (size_t)(nblocks + FIN_STAGE_BLOCKS));
   const size_t off_ge4 = off_cpart + round_up(sizeof(CellPartial) * (size_t)ncblocks);
   const size_t off_rec = off_ge4 + round_up(2 * sizeof(unsigned long long));
   const size_t need = off_rec + round_up(sizeof(RawRecord));

@@ -88,6 +88,13 @@ struct LatticeView {
   int nx, ny, nz;
 };
 
+// Read-only view of the ten position fields (windings kernel).
+template <typename T>
+struct PosView {
+  const T* pos[U1U1_NPOS];
+  int nx, ny, nz;
+};
+
 // Outputs of a measuring kernel.
 struct MeasureOut {
   BlockPartial* partial;  // one per block
@@ -112,11 +119,22 @@ cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, c
 // Tiled z-marching kernel (FP32 and FP64).
 // waves: CTAs per SM-slot the z-chunking aims at (tuning knob; grid about
 // 152 x 3 x waves CTAs).
+// A measuring launch (MODE_MEASURE) with mo.faces set also runs the windings
+// kernel on v.pin, whose block partials follow the step kernel's.
 constexpr int TILE_WAVES_DEFAULT = 32;
 int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves = TILE_WAVES_DEFAULT);
+// block partials a tiled measuring launch writes (with or without windings)
+int tiled_measure_blocks(int nx, int ny, int nz, int sizeof_t, int waves, bool windings);
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
                          cudaStream_t st, int waves = TILE_WAVES_DEFAULT);
+
+// Windings kernel (k_wind.cu): face bytes, optional int8 windings and one
+// block partial (counts only) per block.
+int wind_grid_blocks(int nx, int ny, int nz);
+template <typename T>
+cudaError_t launch_windings(const PosView<T>& v, T dx, BlockPartial* part, uint8_t* faces, int8_t* windings,
+                            cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Ensembles: per-box tables for the batched kernels.
@@ -176,8 +194,13 @@ cudaError_t launch_segments(const uint32_t* mpq, int nx, int ny, int nz, int min
 cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n, cudaStream_t st);
 cudaError_t launch_edge_phase(const float* re, const float* im, float* out, long long n, cudaStream_t st);
 
-// Merge partials into a record.
-cudaError_t launch_finalize(const BlockPartial* part, int nblocks, const CellPartial* cpart,
+// Merge partials into a record.  part must have room for nblocks +
+// FIN_STAGE_BLOCKS entries: above FIN_STAGE_MIN partials a first stage of
+// FIN_STAGE_BLOCKS CTAs merges contiguous slices of them into the entries
+// after the last one (fixed slices and order: the result is reproducible).
+constexpr int FIN_STAGE_BLOCKS = 128;
+constexpr int FIN_STAGE_MIN = 2048;
+cudaError_t launch_finalize(BlockPartial* part, int nblocks, const CellPartial* cpart,
                             int ncblocks, RawRecord* rec, long long n, int has_diag, int has_gauss,
                             int has_strings, int tol, cudaStream_t st,
                             const unsigned long long* ge4 = nullptr);
