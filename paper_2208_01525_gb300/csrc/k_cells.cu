@@ -90,8 +90,6 @@ constexpr int SEG = 128;
 constexpr int BITS4_THREADS = 256;
 constexpr int BITS4_BLOCKS = 152 * 8;
 
-__device__ __forceinline__ int fw4(uint32_t word, int j, int k) { return (int)(word >> (8 * j + FACE_SHIFT(k))) & 3; }
-
 __global__ void __launch_bounds__(BITS4_THREADS)
 k_cellbits4(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words, uint8_t* cell_p, uint8_t* cell_q,
             uint32_t* mp, uint32_t* mq, unsigned long long* ge4) {
@@ -121,16 +119,19 @@ k_cellbits4(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words
       const uint32_t ab = act ? __ldg((const uint32_t*)(f + rbz + x)) : 0u;
       uint32_t nxt = __shfl_down_sync(0xffffffffu, own, 1);
       if (act && (lane == 31 || x + 4 >= nx)) nxt = __ldg((const uint32_t*)(f + rb + (x + 4 >= nx ? 0 : x + 4)));
-      nib[s] = nib4[s] = packed[s] = 0u;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t xb = j < 3 ? own >> (8 * (j + 1)) : nxt;  // face byte of x+1 in the low byte
-        const int cv = fw4(own, j, 0) + fw4(ab, j, 0) + fw4(own, j, 1) + fw4(up, j, 1) + fw4(own, j, 2) +
-                       (int)((xb >> FACE_SHIFT(2)) & 3u);
-        nib[s] |= (cv > 0 ? 1u : 0u) << j;
-        nib4[s] |= (cv >= 4 ? 1u : 0u) << j;
-        packed[s] |= (uint32_t)cv << (8 * j);
-      }
+      // all four cells at once, one byte each: six 2-bit |W| fields summed
+      // bytewise (at most 18, so no carry crosses a byte)
+      const uint32_t M = 0x03030303u;
+      const uint32_t ox = (own >> 8) | (nxt << 24);  // byte j: face byte of x + j + 1
+      const uint32_t cv = (own & M) + (ab & M) + ((own >> 2) & M) + ((up >> 2) & M) + ((own >> 4) & M) +
+                          ((ox >> 4) & M);
+      // bit 7 of byte j set when cell j is > 0 (>= 4): adding 127 (124) cannot
+      // carry out of a byte below 129
+      const uint32_t gt0 = ((cv + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
+      const uint32_t ge4b = ((cv + 0x7C7C7C7Cu) & 0x80808080u) >> 7;
+      nib[s] = (gt0 * 0x01020408u) >> 24;  // gathers bit 0 of bytes 0..3 into bits 0..3
+      nib4[s] = ge4b;
+      packed[s] = cv;
     }
     if (act) {
       if (cell_p) *(uint32_t*)(cell_p + rb + x) = packed[0];
@@ -148,8 +149,10 @@ k_cellbits4(const uint8_t* __restrict__ faces, int nx, int ny, int nz, int words
       mp[wi] = wp;
       mq[wi] = wq;
     }
-    n4[0] += (unsigned long long)__popc(nib4[0]);
-    n4[1] += (unsigned long long)__popc(nib4[1]);
+    if (act) {
+      n4[0] += (unsigned long long)__popc(nib4[0]);  // one bit per byte
+      n4[1] += (unsigned long long)__popc(nib4[1]);
+    }
   }
   if (ge4) {
     __shared__ unsigned long long s4[BITS4_THREADS / 32][2];

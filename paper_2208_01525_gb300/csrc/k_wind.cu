@@ -151,36 +151,33 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
     // finish and emit the plane below
     if (z > z0 && out) {
       const long long gs = (long long)(z - 1) * plane + col;
-      int W[2][3];
-      bool ck[2][3];
+      unsigned nzm[2];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        W[s][0] = pW01[s];
-        W[s][1] = (int)rint_t<T>((pS02[s] - chi[s][0]) * Consts<T>::inv_two_pi());
-        W[s][2] = (int)rint_t<T>((pS12[s] - chi[s][1]) * Consts<T>::inv_two_pi());
-        ck[s][0] = (pcut[s] & 1u) != 0;
-        ck[s][1] = (pcut[s] & 2u) != 0 || (f[s] & 1u) != 0;
-        ck[s][2] = (pcut[s] & 4u) != 0 || (f[s] & 2u) != 0;
-      }
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        unsigned byte = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int aw = abs(W[s][k]);
-          cnt[s == 0 ? C_NP : C_NQ] += aw;
-          cnt[s == 0 ? C_NZP : C_NZQ] += (aw != 0);
-          cnt[C_FLAGGED] += ck[s][k] ? 1 : 0;
-          cnt[C_MAXW] = max(cnt[C_MAXW], aw);
-          cnt[s == 0 ? C_W2P : C_W2Q] += (aw >= 2);
-          byte |= (unsigned)min(aw, 3) << FACE_SHIFT(k);
-          if (ck[s][k]) byte |= FACE_FLAG;
-          if (windings) windings[(3 * s + k) * V + gs] = (int8_t)max(-127, min(127, W[s][k]));
-        }
+        const int W0 = pW01[s];
+        const int W1 = (int)rint_t<T>((pS02[s] - chi[s][0]) * Consts<T>::inv_two_pi());
+        const int W2 = (int)rint_t<T>((pS12[s] - chi[s][1]) * Consts<T>::inv_two_pi());
+        // flagged plaquettes: an edge of this plane or of the plane above on the cut
+        const unsigned ckm = (pcut[s] & 1u) | (((pcut[s] & 2u) || (f[s] & 1u)) ? 2u : 0u) |
+                             (((pcut[s] & 4u) || (f[s] & 2u)) ? 4u : 0u);
+        const int a0 = abs(W0), a1 = abs(W1), a2 = abs(W2);
+        unsigned byte = (unsigned)min(a0, 3) | ((unsigned)min(a1, 3) << FACE_SHIFT(1)) |
+                        ((unsigned)min(a2, 3) << FACE_SHIFT(2));
+        nzm[s] = (byte | (byte >> 1)) & 0x15u;  // bit 2k: |W_k| >= 1
+        cnt[s == 0 ? C_NP : C_NQ] += a0 + a1 + a2;
+        cnt[s == 0 ? C_NZP : C_NZQ] += __popc(nzm[s]);
+        cnt[s == 0 ? C_W2P : C_W2Q] += __popc((byte >> 1) & 0x15u);  // |W_k| >= 2
+        cnt[C_FLAGGED] += __popc(ckm);
+        cnt[C_MAXW] = max(cnt[C_MAXW], max(a0, max(a1, a2)));
+        if (ckm) byte |= FACE_FLAG;
         faces[s * V + gs] = (uint8_t)byte;
+        if (windings) {
+          windings[(3 * s + 0) * V + gs] = (int8_t)max(-127, min(127, W0));
+          windings[(3 * s + 1) * V + gs] = (int8_t)max(-127, min(127, W1));
+          windings[(3 * s + 2) * V + gs] = (int8_t)max(-127, min(127, W2));
+        }
       }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cnt[C_NPQ_PLAQ] += (W[0][k] != 0 && W[1][k] != 0) ? 1 : 0;
+      cnt[C_NPQ_PLAQ] += __popc(nzm[0] & nzm[1]);
     }
     if (last) break;
 
