@@ -80,6 +80,23 @@ def recorded_traffic(n, tag):
         return None
 
 
+def combine_ranks(ms, units_local, world, device=None):
+    """Whole-job figures from each rank's timed region: the slowest rank's
+    time (max over ranks) and the units all ranks processed (sum), giving
+    value = units / time.  Without a process group (world 1) the local
+    figures are returned."""
+    units = float(units_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        tu = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        ms, units = float(tm.item()), float(tu.item())
+    return ms, units / (ms * 1e-3)
+
+
 def workload_params(U, n, precision, beta=1.0, seed=2024):
     # 2560 steps to eta = 257 for the 1024^3 box; a = 1 at the end of the run
     return U.Params.cube(n, m=0.5, beta=beta, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=seed,
@@ -114,9 +131,16 @@ class ClockSampler:
                 self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        rows = [ln.strip().split(", ") for ln in self.f if ln.strip()]
+        lines = list(self.f)
         os.unlink(self.f.name)
-        mine = [r for r in rows if self.uuid is None or self.uuid in r[0]] or rows
+        return self.summarize(lines, self.uuid)
+
+    @staticmethod
+    def summarize(lines, uuid=None):
+        """Median SM clock under load, maximum clock and the throttle reasons
+        seen Active, from nvidia-smi CSV lines (FIELDS order, no header)."""
+        rows = [ln.strip().split(", ") for ln in lines if ln.strip()]
+        mine = [r for r in rows if uuid is None or uuid in r[0]] or rows
         sm = [float(r[1].split()[0]) for r in mine if len(r) > 2 and r[1].split()[0].replace(".", "").isdigit()]
         mx = [float(r[2].split()[0]) for r in mine if len(r) > 2 and r[2].split()[0].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -303,19 +327,36 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = combine_ranks(t_start.elapsed_time(t_end), args.steps * de * V, world, dev)
     recs, lost = lat.read_records()
     plain_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / (args.steps * (de - 1))
     det_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
-    site_updates = args.steps * de * V * world
-    value = site_updates / (ms * 1e-3)
     peak, peak_kind = peaks()
     achieved = BYTES_PER_SITE[tag] * V / (plain_ms * 1e-3) / 1e9
     last = recs[-1] if recs else None
+
+    # standalone passes on the current state (no step): the diagnostics pass
+    # (all sums and the Gauss residual; reads positions and momenta, 80 B/site
+    # in FP32) and string detection (sums, windings, cells, overlap); each
+    # call ends with its record copied to the host
+    passes = None
+    if args.passes:
+        passes = {}
+        for name, fn in (("diagnostics", lat.diagnostics), ("detect_strings", lat.detect_strings)):
+            fn()
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            t_ms = min(ts)
+            passes[name] = {"ms": t_ms, "sites_per_s": V / (t_ms * 1e-3)}
+        rd = BYTES_PER_SITE[tag] // 2 * V  # the pass reads the 20 words of every site once
+        passes["diagnostics"]["hbm_frac"] = rd / (passes["diagnostics"]["ms"] * 1e-3) / 1e9 / peak
+        passes["diagnostics"]["bytes_per_site"] = BYTES_PER_SITE[tag] // 2
 
     # end-to-end through the public API with host buffers
     e2e = None
@@ -335,7 +376,8 @@ def run_ours(args):
         e2e_s = time.perf_counter() - t0
         state_bytes = 20 * V * lat.dtype.itemsize
         rec_bytes = 360  # one detection record copied per period
-        e2e = {"value": site_updates / e2e_s, "unit": "site-updates/s",
+        _, e2e_value = combine_ranks(e2e_s * 1e3, args.steps * de * V, world, dev)
+        e2e = {"value": e2e_value, "unit": "site-updates/s",
                "h2d_bytes_per_step": state_bytes / args.steps,
                "d2h_bytes_per_step": state_bytes / args.steps + rec_bytes,
                "what": "upload state from pinned host, K periods each followed by a record read, "
@@ -397,6 +439,7 @@ def run_ours(args):
                          "kernel": "leapfrog step", "bytes_per_site": BYTES_PER_SITE[tag],
                          "ms_per_launch": plain_ms},
             "detect_ms_per_period": det_ms,
+            "passes": passes,
             "clocks": clocks,
             # per period: de step launches (the first one measuring), the
             # windings kernel (tiled path), cell bits, overlap, finalize
@@ -433,6 +476,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-ensemble", dest="ensemble", action="store_false")
+    ap.add_argument("--no-passes", dest="passes", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -422,9 +422,9 @@ int u1u1_detect_strings_noalloc(const u1u1_params* p, const void* const fields[U
 /* ---- check entry points ---------------------------------------------------- */
 
 /* Evaluate, on n device values theta, the FP32 routine the kernels use for
- * the link variable U = exp(-i theta) (sin and cos of theta, Cody-Waite
- * reduction plus Taylor series), writing sin_out[k] and cos_out[k] (device
- * arrays).  Lets tests bound its error against a double-precision
+ * the link variable U = exp(-i theta) (sin and cos of theta: reduction by
+ * 2 pi split in two floats, then the hardware sine and cosine), writing
+ * sin_out[k] and cos_out[k] (device arrays).  Lets tests bound its error against a double-precision
  * reference.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
 int u1u1_eval_link_phase(const float* theta, float* sin_out, float* cos_out, int64_t n, void* stream);
 

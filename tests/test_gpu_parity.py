@@ -360,9 +360,13 @@ def test_edge_cases_and_errors():
 
 
 def test_link_phase_routine_accuracy():
-    """The FP32 cos/sin of link angles (Cody-Waite reduction + Taylor series)
-    stays within 2 ulp-scale (2.4e-7 absolute) of the double-precision values
-    over the angle range lattices reach, and handles the far-range fallback."""
+    """The FP32 cos/sin of link angles (reduction by 2 pi split in two
+    floats, then the hardware sine and cosine, documented to 2^-21.41 on
+    [-pi, pi]) stays within 6e-7 absolute of the double-precision values of
+    the same FP32 angles, over the range lattices reach and far beyond it.
+    The bound is set by what the step needs: with it the FP32 step stays
+    within max-rel 6e-7 of the FP64 oracle after 20 steps at 64^3, against
+    the 1e-5 the FP32 bulk is held to."""
     import ctypes
     th64 = torch.cat([torch.linspace(-50.0, 50.0, 2_000_001, dtype=torch.float64),
                       torch.tensor([0.0, -0.0, 1e-30, 3.0e3, -4095.0, 4097.0, 1.0e5, -2.5e6],
@@ -377,7 +381,7 @@ def test_link_phase_routine_accuracy():
     ref = th.double()
     es = (sn.double() - torch.sin(ref)).abs().max().item()
     ec = (cs.double() - torch.cos(ref)).abs().max().item()
-    assert es < 2.4e-7 and ec < 2.4e-7, (es, ec)
+    assert es < 6e-7 and ec < 6e-7, (es, ec)
 
 
 def test_edge_phase_routine_accuracy():
