@@ -36,6 +36,11 @@ if ROOT not in sys.path:
 
 METRIC = "site-updates/s & % HBM roofline, FP32 vs FP64, U(1)xU(1) step at 1024^3"
 BYTES_PER_SITE = {"fp32": 160, "fp64": 320}  # read 20 + write 20 words
+# FP64 step: 177 DFMA + 60 DADD + 64 DMUL per site (ncu thread-instruction
+# counts of one launch at 256^3) = 478 FP64 operations; nominal FP64 rate of
+# the GB300 (non-tensor) 1.25 TFLOP/s
+FP64_FLOPS_PER_SITE = 478
+FP64_PEAK_TFLOPS = 1.25
 
 
 def peaks():
@@ -354,6 +359,7 @@ def run_ours(args):
                 ts.append(a.elapsed_time(b))
             t_ms = min(ts)
             passes[name] = {"ms": t_ms, "sites_per_s": V / (t_ms * 1e-3)}
+        del fn  # the bound method would keep the lattice (and its fields) alive
         rd = BYTES_PER_SITE[tag] // 2 * V  # the pass reads the 20 words of every site once
         passes["diagnostics"]["hbm_frac"] = rd / (passes["diagnostics"]["ms"] * 1e-3) / 1e9 / peak
         passes["diagnostics"]["bytes_per_site"] = BYTES_PER_SITE[tag] // 2
@@ -404,9 +410,16 @@ def run_ours(args):
             b.record(stream)
             torch.cuda.synchronize()
             t64 = a.elapsed_time(b) / args.fp64_steps
+            # the FP64 step is bound by GB300's FP64 arithmetic, not by HBM:
+            # FP64_FLOPS_PER_SITE from ncu instruction counts (DFMA x 2 + DADD
+            # + DMUL per site) against the nominal FP64 rate
+            tflops = FP64_FLOPS_PER_SITE * p64.nsites / (t64 * 1e-3) / 1e12
             fp64 = {"lattice": n64, "value": p64.nsites / (t64 * 1e-3), "unit": "site-updates/s",
                     "ms_per_step": t64,
                     "hbm_frac": BYTES_PER_SITE["fp64"] * p64.nsites / (t64 * 1e-3) / 1e9 / peak,
+                    "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                                 "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
+                                 "peak_kind": "nominal", "flops_per_site": FP64_FLOPS_PER_SITE},
                     "steps": args.fp64_steps}
             lat64.close()
             del lat64
