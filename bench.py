@@ -22,6 +22,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -69,15 +70,16 @@ def step_kernel_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(n, tag):
+def recorded_traffic(n, tag, waves):
     """DRAM bytes (read + write) of one step-kernel launch from the committed
-    ncu summary, or None when it was taken on another lattice, precision or
-    kernel source."""
+    ncu summary, or None when it was taken on another lattice, precision,
+    z-chunking (wave target) or kernel source."""
     try:
         with open(os.path.join(ROOT, TRAFFIC_RECORD)) as f:
             kv = dict(line.split(":", 1) for line in f if line.startswith("record-"))
         kv = {k.strip(): v.strip() for k, v in kv.items()}
         if (int(kv["record-lattice"]) != n or kv["record-precision"] != tag
+                or int(kv["record-waves"]) != waves
                 or kv["record-source-sha256"] != step_kernel_hash()):
             return None
         return float(kv["record-dram-bytes-per-launch"])
@@ -305,7 +307,8 @@ def run_ours(args):
         # the library's autotuner picks the step kernel and its z-chunking
         # on this lattice (timed on the lattice's own state, restored)
         tune = lat.autotune()
-    kernel_used = lat.kernel
+    kernel_used = lat.kernel()
+    waves_used = tune["waves"] if tune else 32  # the library's default wave target
     de = args.detect_every
     V = p.nsites
     stream = torch.cuda.current_stream()
@@ -397,6 +400,7 @@ def run_ours(args):
 
     lat.close()
     del lat
+    gc.collect()
     torch.cuda.empty_cache()
 
     # FP64 step throughput (same box when it fits)
@@ -404,8 +408,12 @@ def run_ours(args):
     if args.fp64_n > 0 and prec == U.FP32:
         n64 = args.fp64_n
         p64 = workload_params(U, n64, U.FP64, seed=2024 + rank)
-        need = 30 * p64.nsites * 8 * 1.05
-        if torch.cuda.mem_get_info(dev)[0] > need:
+        # 30 field arrays plus the handle's scratch (face bytes, masks, partials)
+        need = (30 * 8 + 3) * p64.nsites
+        free = torch.cuda.mem_get_info(dev)[0]
+        if free <= need:
+            fp64 = {"lattice": n64, "skipped": f"needs {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free"}
+        else:
             lat64 = U.Lattice(p64, device=dev, kernel=args.kernel)
             lat64.step(2)
             torch.cuda.synchronize()
@@ -453,7 +461,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "autotuned": tune},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(n, tag),
+                         "frac": achieved / peak, "traffic": (recorded_traffic(n, tag, waves_used)
+                                                                if kernel_used != U.KERNEL_SIMPLE else None),
                          "traffic_unit": "bytes per launch", "peak_kind": peak_kind,
                          "kernel": "leapfrog step", "bytes_per_site": BYTES_PER_SITE[tag],
                          "ms_per_launch": plain_ms},

@@ -320,7 +320,10 @@ int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
  * memory).  The choice is applied to the handle and, when cache_path is not
  * NULL, looked up first in / appended to that text file, keyed by GPU name,
  * lattice and precision.  *kernel_out and *waves_out (may be NULL) receive
- * the choice.  Synchronises `stream`.  Errors: OUT_OF_MEMORY, IO, CUDA. */
+ * the choice.  A cache entry for this key that names a choice the tuner
+ * does not make (another kernel id or wave count) is refused with
+ * INVALID_ARG and the handle is left unchanged.  Synchronises `stream`.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, IO, CUDA. */
 int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kernel_out, int* waves_out, void* stream);
 
 #define U1U1_KERNEL_AUTO 0

@@ -880,8 +880,17 @@ extern "C" int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kerne
   tune_key(h, key, sizeof(key));
   int kernel = 0, waves = 0;
   if (cache_lookup(cache_path, key, &kernel, &waves)) {
+    // accept only choices the tuner itself can make: the block-partial
+    // buffers are sized for the candidate grids, and a larger one would
+    // overrun them
+    bool known = kernel == U1U1_KERNEL_SIMPLE;
+    if (kernel == U1U1_KERNEL_TILED)
+      for (int w : AUTOTUNE_WAVES) known = known || w == waves;
+    if (!known)
+      return fail(U1U1_ERR_INVALID_ARG, "autotune cache %s: entry '%s %d %d' is not a choice the tuner makes",
+                  cache_path, key, kernel, waves);
     h->kernel = kernel;
-    h->tile_waves = waves;
+    h->tile_waves = kernel == U1U1_KERNEL_TILED ? waves : TILE_WAVES_DEFAULT;
   } else {
     // time one plain step per candidate on the handle's own state: the step
     // reads the current position buffer, writes the other one and updates

@@ -9,15 +9,33 @@
 // phases run at the occupancy of a small kernel: inside the step kernel they
 // lengthened every thread's dependency chain at two resident CTAs per SM.
 //
+// Per-site phases.  With alpha(x) = arg phi(x), the edge phase
+// chi_i(x) = arg(conj(phi(x)) U_i(x) phi(x+i)) is the principal value of
+// d_i(x) = alpha(x+i) - alpha(x) - theta_i(x), theta_i = dx A_i, i.e.
+// chi_i = d_i - 2 pi k_i with the integer k_i = rint(d_i / 2 pi).  Around a
+// plaquette the alpha differences cancel exactly and the thetas cancel
+// against those of the curl term, so the winding of plaquette (x; i, j) is the
+// integer
+//   W_ij(x) = -(k_i(x) + k_j(x+i) - k_i(x+j) - k_j(x)),
+// equal to the rounded sum of the four chi plus dx^2 F_ij over 2 pi.  That
+// takes one arctangent per site and sector instead of one per link; the k
+// and the flag depend on the rounding of d only within rounding of an odd
+// multiple of pi, where chi is within rounding of +-pi and the edge is
+// flagged (pi - |chi| < 1e-4).  A zero field makes alpha undefined: alpha is
+// stored as NaN there, so every edge touching the site is flagged (and gets
+// k = 0).
+//
 // CTA: 8 warps x 32 lanes on a (32 x 8)-site window that advances by 31 in x
 // and 7 in y, so that lane 31 and warp 7 hold the right column and the top
-// row of the tile's halo: every thread computes the three edge phases of its
-// own site per sector and no thread does extra halo work.  Neighbours in x
-// come by warp shuffle, neighbours in y through a double-buffered shared
-// plane (one barrier per plane), neighbours in z from the same thread's
-// previous plane.  The CTA marches a chunk of planes [z0, z1) and emits the
-// face byte of plane z-1 at plane z, like the step kernel's measuring pass
-// did.
+// row of the tile's halo.  Each thread computes alpha of its own site once
+// per sector and plane.  alpha of x+1 comes by warp shuffle; alpha, A_0 and
+// A_2 of the row above come from a three-plane shared ring (one barrier per
+// plane), from which each thread also recomputes the two edges of the row
+// above that its plaquettes need (k_0 and k_2 at x+y); alpha of z+1 is the
+// thread's next plane, whose raw fields are prefetched a plane ahead.  The
+// CTA marches a chunk of planes [z0, z1) and emits the face byte of plane z-1
+// at plane z, once that plane's k_0 and k_1 complete the 02 and 12
+// plaquettes.
 #include <stdint.h>
 
 #include "reduce.cuh"
@@ -34,132 +52,135 @@ constexpr int WOX = WW - 1;   // output columns per tile
 constexpr int WOY = WH - 1;   // output rows per tile
 constexpr int WNT = WW * WH;  // threads per CTA
 constexpr int WIND_MIN_LZ = 32;
-constexpr int WIND_TARGET_CTAS = 152 * 4 * 16;  // 4 resident CTAs per SM, about 16 waves
+constexpr int WIND_TARGET_CTAS = 152 * 3 * 16;  // 3 resident CTAs per SM, about 16 waves
 
-// What the row below needs of a site: chi_0, chi_2, A_0, A_2 and the flags.
+// What the row below needs of a site in one plane: alpha, A_0, A_2 per sector.
 template <typename T>
-struct WindRow {
-  T chi0[2][WNT], chi2[2][WNT], a0[2][WNT], a2[2][WNT];
-  uint8_t fl[2][WNT];
+struct WindPlane {
+  T al[2][WNT], a0[2][WNT], a2[2][WNT];
 };
 
 template <typename T>
 struct WindSmem {
-  WindRow<T> row[2];  // by plane parity
+  WindPlane<T> q[3];  // by plane index mod 3
   int cnt[WH][NCNT];
 };
 
-// The three edge phases chi_i(x) = arg(conj(phi(x)) U_i(x) phi(x+i)) of one
-// sector at one site, with their branch-cut bits (bit i: edge i).  Since
-// |U_i| = 1 and arg U_i = -theta_i, chi_i is the principal value of
-// alpha_i - theta_i with alpha_i = arg(conj(phi(x)) phi(x+i)) and
-// theta_i = dx A_i(x): one arctangent and a reduction by the nearest multiple
-// of 2 pi (2 pi split in two floats, Cody & Waite), instead of the link
-// variable's cosine and sine, a transport and an arctangent.  Equal to the
-// direct form up to rounding; the two can pick different branches only
-// within rounding of +-pi, where the edge is flagged either way.
-template <typename T> struct TwoPi;
-template <> struct TwoPi<float> {
-  static __device__ __forceinline__ float hi() { return 6.28318548202514648f; }   // fl(2 pi)
-  static __device__ __forceinline__ float lo() { return -1.74845553e-07f; }       // 2 pi - fl(2 pi)
-};
-template <> struct TwoPi<double> {
-  static __device__ __forceinline__ double hi() { return 6.28318530717958623; }
-  static __device__ __forceinline__ double lo() { return 2.44929359829470641e-16; }
-};
-
+// alpha = arg(re + i im), NaN for a zero field
 template <typename T>
-__device__ __forceinline__ unsigned edge_phases(T fr, T fi, const T nbr[3], const T nbi[3], const T A[3], T dx,
-                                                T chi[3]) {
-  unsigned f = 0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const T zr = fr * nbr[i] + fi * nbi[i], zi = fr * nbi[i] - fi * nbr[i];
-    T d = edge_phase<T>(zr, zi) - dx * A[i];
-    const T k = rint_t<T>(d * Consts<T>::inv_two_pi());
-    d = fma(-k, TwoPi<T>::hi(), d);
-    d = fma(-k, TwoPi<T>::lo(), d);
-    chi[i] = d;
-    const bool cut = Consts<T>::pi() - fabs(d) < T(1e-4) || (zr == T(0) && zi == T(0));
-    f |= cut ? (1u << i) : 0u;
-  }
-  return f;
+__device__ __forceinline__ T site_phase(T re, T im) {
+  const T a = edge_phase<T>(re, im);
+  return (re == T(0) && im == T(0)) ? T(NAN) : a;
+}
+
+template <typename T> __device__ __forceinline__ int round_int(T x);
+template <> __device__ __forceinline__ int round_int<float>(float x) { return __float2int_rn(x); }  // NaN -> 0
+template <> __device__ __forceinline__ int round_int<double>(double x) { return __double2int_rn(x); }
+
+// |chi| > pi - 1e-4 in units of 2 pi: |d / 2 pi - k| > 1/2 - 1e-4 / (2 pi)
+template <typename T> __device__ __forceinline__ T cut_frac();
+template <> __device__ __forceinline__ float cut_frac<float>() { return 0.49998408451f; }
+template <> __device__ __forceinline__ double cut_frac<double>() { return 0.49998408450991098; }
+
+// Branch integer k of the edge from a site of phase a_t to a site of phase
+// a_h across a link of angle theta, and whether the edge is flagged (near the
+// cut, or a zero field at either end: then d is NaN, k = 0 and the test below
+// fails).
+template <typename T>
+__device__ __forceinline__ int edge_k(T a_h, T a_t, T theta, bool* cut) {
+  const T t = ((a_h - a_t) - theta) * Consts<T>::inv_two_pi();
+  const int k = round_int<T>(t);
+  *cut = !(fabs(t - T(k)) <= cut_frac<T>());
+  return k;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 3)
 k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_t* windings) {
   __shared__ WindSmem<T> sm;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
   const int nx = v.nx, ny = v.ny, nz = v.nz;
   const int x0 = blockIdx.x * WOX, y0 = blockIdx.y * WOY;
   const int z0 = blockIdx.z * lz, z1 = min(z0 + lz, nz);
   const int gx = (x0 + lane) % nx, gy = (y0 + w) % ny;
-  const int gyn = gy + 1 == ny ? 0 : gy + 1;
   const bool out = lane < WOX && w < WOY && x0 + lane < nx && y0 + w < ny;
   const long long plane = (long long)nx * ny;
   const long long V = plane * nz;
-  const long long col = (long long)gy * nx + gx, coln = (long long)gyn * nx + gx;
+  const long long col = (long long)gy * nx + gx;
+  const int ty = w + 1 < WH ? t + WW : t;  // the row above (the top row reads itself; unused)
 
   int cnt[NCNT];
 #pragma unroll
   for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
 
-  // own phi and A of the current plane (loaded one plane ahead)
-  T fr[2], fi[2], A[2][3];
-  {
-    const long long o = (long long)z0 * plane + col;
+  // own alpha and A of the current plane; raw fields of the next plane
+  T al[2], A[2][3], nfr[2], nfi[2], nA[2][3];
+  auto load_plane = [&](int zz, T fr_[2], T fi_[2], T A_[2][3]) {
+    const long long o = (long long)(zz >= nz ? zz - nz : zz) * plane + col;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      fr[s] = __ldg(v.pos[2 * s] + o);
-      fi[s] = __ldg(v.pos[2 * s + 1] + o);
+      fr_[s] = __ldg(v.pos[2 * s] + o);
+      fi_[s] = __ldg(v.pos[2 * s + 1] + o);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) A[s][i] = __ldg(v.pos[4 + 3 * s + i] + o);
+      for (int i = 0; i < 3; ++i) A_[s][i] = __ldg(v.pos[4 + 3 * s + i] + o);
+    }
+  };
+  {
+    T fr[2], fi[2];
+    load_plane(z0, fr, fi, A);
+    load_plane(z0 + 1, nfr, nfi, nA);
+    WindPlane<T>& q = sm.q[z0 % 3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      al[s] = site_phase<T>(fr[s], fi[s]);
+      q.al[s][t] = al[s];
+      q.a0[s][t] = A[s][0];
+      q.a2[s][t] = A[s][2];
     }
   }
-  // plaquettes of the plane below still waiting for this plane's chi_0, chi_1
-  int pW01[2] = {0, 0};
-  T pS02[2] = {T(0), T(0)}, pS12[2] = {T(0), T(0)};
+  // plaquettes of the plane below waiting for this plane's k_0, k_1
+  int pW01[2] = {0, 0}, pW02[2] = {0, 0}, pW12[2] = {0, 0};
   unsigned pcut[2] = {0u, 0u};
 
   for (int z = z0; z <= z1; ++z) {
-    const int zc = z == nz ? 0 : z;            // plane z1 may wrap
-    const int zn = zc + 1 == nz ? 0 : zc + 1;  // plane above
-    const long long oc = (long long)zc * plane, on = (long long)zn * plane;
     const bool last = z == z1;
-    // neighbours of the own site: x+1 by shuffle, y+1 and z+1 from memory
-    T nbr[2][3], nbi[2][3], An[2][3];
-    T frn[2], fin[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      nbr[s][0] = __shfl_down_sync(0xffffffffu, fr[s], 1);
-      nbi[s][0] = __shfl_down_sync(0xffffffffu, fi[s], 1);
-      nbr[s][1] = __ldg(v.pos[2 * s] + oc + coln);
-      nbi[s][1] = __ldg(v.pos[2 * s + 1] + oc + coln);
-      frn[s] = __ldg(v.pos[2 * s] + on + col);
-      fin[s] = __ldg(v.pos[2 * s + 1] + on + col);
-      nbr[s][2] = frn[s];
-      nbi[s][2] = fin[s];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) An[s][i] = last ? T(0) : __ldg(v.pos[4 + 3 * s + i] + on + col);
-    }
-    T chi[2][3];
-    unsigned f[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) f[s] = edge_phases<T>(fr[s], fi[s], nbr[s], nbi[s], A[s], dx, chi[s]);
-
-    // finish and emit the plane below
-    if (z > z0 && out) {
-      const long long gs = (long long)(z - 1) * plane + col;
-      unsigned nzm[2];
+    // next plane: alpha from the prefetched fields, into the ring; prefetch
+    // the plane after it
+    T aln[2], An[2][3];
+    if (!last) {
+      WindPlane<T>& qn = sm.q[(z + 1) % 3];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
+        aln[s] = site_phase<T>(nfr[s], nfi[s]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) An[s][i] = nA[s][i];
+        qn.al[s][t] = aln[s];
+        qn.a0[s][t] = An[s][0];
+        qn.a2[s][t] = An[s][2];
+      }
+      if (z + 1 < z1) load_plane(z + 2, nfr, nfi, nA);
+    }
+    __syncthreads();
+    const WindPlane<T>& qc = sm.q[z % 3];
+    const WindPlane<T>& qn = sm.q[(z + 1) % 3];
+
+    unsigned nzm[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      // own edges 0 and 1 of this plane
+      const T ax = __shfl_down_sync(0xffffffffu, al[s], 1);
+      const T ay = qc.al[s][ty];
+      bool c0, c1;
+      const int k0 = edge_k<T>(ax, al[s], dx * A[s][0], &c0);
+      const int k1 = edge_k<T>(ay, al[s], dx * A[s][1], &c1);
+
+      // finish and emit the plane below
+      if (z > z0 && out) {
+        const long long gs = (long long)(z - 1) * plane + col;
         const int W0 = pW01[s];
-        const int W1 = (int)rint_t<T>((pS02[s] - chi[s][0]) * Consts<T>::inv_two_pi());
-        const int W2 = (int)rint_t<T>((pS12[s] - chi[s][1]) * Consts<T>::inv_two_pi());
-        // flagged plaquettes: an edge of this plane or of the plane above on the cut
-        const unsigned ckm = (pcut[s] & 1u) | (((pcut[s] & 2u) || (f[s] & 1u)) ? 2u : 0u) |
-                             (((pcut[s] & 4u) || (f[s] & 2u)) ? 4u : 0u);
+        const int W1 = pW02[s] + k0;
+        const int W2 = pW12[s] + k1;
+        const unsigned ckm = pcut[s] | (c0 ? 2u : 0u) | (c1 ? 4u : 0u);
         const int a0 = abs(W0), a1 = abs(W1), a2 = abs(W2);
         unsigned byte = (unsigned)min(a0, 3) | ((unsigned)min(a1, 3) << FACE_SHIFT(1)) |
                         ((unsigned)min(a2, 3) << FACE_SHIFT(2));
@@ -177,46 +198,29 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
           windings[(3 * s + 2) * V + gs] = (int8_t)max(-127, min(127, W2));
         }
       }
-      cnt[C_NPQ_PLAQ] += __popc(nzm[0] & nzm[1]);
-    }
-    if (last) break;
+      if (last) continue;
 
-    // exchange with the row below: it needs chi_0, chi_2, A_0, A_2, flags
-    WindRow<T>& r = sm.row[z & 1];
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      r.chi0[s][t] = chi[s][0];
-      r.chi2[s][t] = chi[s][2];
-      r.a0[s][t] = A[s][0];
-      r.a2[s][t] = A[s][2];
-      r.fl[s][t] = (uint8_t)f[s];
-    }
-    __syncthreads();
-    const int ty = w + 1 < WH ? t + WW : t;  // the top row reads itself (its results are not used)
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const T c1x = __shfl_down_sync(0xffffffffu, chi[s][1], 1);
-      const T c2x = __shfl_down_sync(0xffffffffu, chi[s][2], 1);
-      const T a1x = __shfl_down_sync(0xffffffffu, A[s][1], 1);
-      const T a2x = __shfl_down_sync(0xffffffffu, A[s][2], 1);
-      const unsigned fx = __shfl_down_sync(0xffffffffu, f[s], 1);
-      const T c0y = r.chi0[s][ty], c2y = r.chi2[s][ty], a0y = r.a0[s][ty], a2y = r.a2[s][ty];
-      const unsigned fy = r.fl[s][ty];
-      const T F01 = curl_ft<T>(a1x, A[s][1], a0y, A[s][0]);
-      const T F02 = curl_ft<T>(a2x, A[s][2], An[s][0], A[s][0]);
-      const T F12 = curl_ft<T>(a2y, A[s][2], An[s][1], A[s][1]);
-      pW01[s] = plaquette_winding<T>(chi[s][0], c1x, c0y, chi[s][1], dx, F01);
-      pS02[s] = (chi[s][0] + c2x) - chi[s][2] + dx * F02;
-      pS12[s] = (chi[s][1] + c2y) - chi[s][2] + dx * F12;
-      const unsigned f0 = f[s];
-      pcut[s] = (((f0 & 3u) || (fx & 2u) || (fy & 1u)) ? 1u : 0u) | (((f0 & 5u) || (fx & 4u)) ? 2u : 0u) |
-                (((f0 & 6u) || (fy & 4u)) ? 4u : 0u);
-      fr[s] = frn[s];
-      fi[s] = fin[s];
+      // own edge 2, and edges 0 and 2 of the row above (x + y)
+      bool c2, c0y, c2y;
+      const int k2 = edge_k<T>(aln[s], al[s], dx * A[s][2], &c2);
+      const T axy = __shfl_down_sync(0xffffffffu, ay, 1);
+      const int k0y = edge_k<T>(axy, ay, dx * qc.a0[s][ty], &c0y);
+      const int k2y = edge_k<T>(qn.al[s][ty], ay, dx * qc.a2[s][ty], &c2y);
+      // edges 1 and 2 of x + x by shuffle
+      const unsigned cb = (c1 ? 1u : 0u) | (c2 ? 2u : 0u);
+      const int k1x = __shfl_down_sync(0xffffffffu, k1, 1);
+      const int k2x = __shfl_down_sync(0xffffffffu, k2, 1);
+      const unsigned cx = __shfl_down_sync(0xffffffffu, cb, 1);
+      pW01[s] = -(k0 + k1x - k0y - k1);
+      pW02[s] = -(k0 + k2x - k2);  // + k_0 of the plane above
+      pW12[s] = -(k1 + k2y - k2);  // + k_1 of the plane above
+      pcut[s] = ((c0 || (cx & 1u) || c0y || c1) ? 1u : 0u) | ((c0 || (cx & 2u) || c2) ? 2u : 0u) |
+                ((c1 || c2y || c2) ? 4u : 0u);
+      al[s] = aln[s];
 #pragma unroll
       for (int i = 0; i < 3; ++i) A[s][i] = An[s][i];
     }
+    if (z > z0 && out) cnt[C_NPQ_PLAQ] += __popc(nzm[0] & nzm[1]);
   }
 
   // block reduction of the counts (maximum for C_MAXW)
@@ -232,7 +236,6 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
   }
   __syncthreads();
   BlockPartial* p = part + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  const int t = threadIdx.x;
   if (t < NSUM) {
     p->sum[t] = 0.0;
     p->comp[t] = 0.0;

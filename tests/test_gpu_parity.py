@@ -129,6 +129,25 @@ def test_windings_rough_random_state(kernel):
     assert res["max_abs_w"] >= 1
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(9, 22, 40), (13, 7, 32)])
+def test_windings_fp32_rough_ragged_with_zero_field(kernel, shape):
+    """FP32 windings on a rough state, on boxes that leave ragged windows
+    in x and y, with phi = 0 planted at one site of each sector: every
+    unflagged plaquette matches the oracle, and the plaquettes around the
+    zero sites (12 per sector) are flagged."""
+    nz, ny, nx = shape
+    p = U.Params(nx=nx, ny=ny, nz=nz, m=0.0, precision=U.FP32)
+    st = synth.random_state(p.shape, seed=11, a_amp=4.0)
+    st[0][2, 3, 5] = st[1][2, 3, 5] = 0.0
+    st[2][4, 1, 7] = st[3][4, 1, 7] = 0.0
+    lat = U.Lattice(p, kernel=kernel)
+    lat.set_state(st)
+    res, ores, nflag = _windings_compare(p, lat)
+    assert ores["n_flagged"] >= 24 and res["n_flagged"] >= 24
+    assert res["max_abs_w"] >= 1
+
+
 def test_higher_winding_census():
     """Crossing strings: the cells shared by two strings read 4 and are
     counted as the oracle counts them."""
@@ -447,3 +466,28 @@ def test_autotune_keeps_state_and_reuses_cache(tmp_path):
     c = U.Lattice(p)
     assert c.autotune(cache_path=cache) == choice
     assert open(cache).read().count("96x96x96") == 1
+
+
+def test_autotune_refuses_foreign_cache_entry(tmp_path):
+    """A cache entry naming a wave count the tuner never picks (here 128) is
+    refused before any launch: the block-partial buffers are sized for the
+    tuner's own candidate grids.  The handle keeps its kernel choice."""
+    p = radiation(64, 640, precision=U.FP32, seed=6)
+    a = U.Lattice(p)
+    cache = str(tmp_path / "tune.txt")
+    choice = a.autotune(cache_path=cache)
+    key = open(cache).read().split()[0]
+    bad = str(tmp_path / "bad.txt")
+    with open(bad, "w") as f:
+        f.write(f"{key} {U.KERNEL_TILED} 128\n")
+    b = U.Lattice(p)
+    k0 = b.kernel()
+    with pytest.raises(U.U1U1Error) as ei:
+        b.autotune(cache_path=bad)
+    assert ei.value.code == -1 and "128" in str(ei.value)  # INVALID_ARG
+    assert b.kernel() == k0
+    with open(bad, "w") as f:
+        f.write(f"{key} 7 32\n")
+    with pytest.raises(U.U1U1Error):
+        b.autotune(cache_path=bad)
+    assert choice["kernel"] in (U.KERNEL_TILED, U.KERNEL_SIMPLE)
