@@ -314,7 +314,7 @@ int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
  * U1U1_KERNEL_TILED the z-marching shared-memory kernel. */
 /* Autotuner: choose the step kernel and the tiled kernel's z-chunking for
  * this handle's lattice by timing one plain step of each candidate (tiled
- * kernel with 8, 16, 32 or 64 target waves of CTAs; the simple kernel) on
+ * kernel with 8, 16, 32, 64, 128 or 256 target waves of CTAs; the simple kernel) on
  * the handle's own state, saving and restoring the momenta around every
  * trial so the state is unchanged (needs 10 field arrays of temporary device
  * memory).  The choice is applied to the handle and, when cache_path is not

@@ -39,7 +39,10 @@ int cuda_fail(cudaError_t e, const char* where) {
 namespace {
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 // z-chunk targets the autotuner tries for the tiled kernel
-constexpr int AUTOTUNE_WAVES[] = {8, 16, 32, 64};
+// (more waves: shorter z-chunks, so neighbouring tiles stay closer in z
+// and their halo rows are still in L2; fewer: fewer prologue planes)
+constexpr int AUTOTUNE_WAVES[] = {8, 16, 32, 64, 128, 256};
+constexpr int N_AUTOTUNE_WAVES = (int)(sizeof(AUTOTUNE_WAVES) / sizeof(AUTOTUNE_WAVES[0]));
 }  // namespace
 
 
@@ -914,7 +917,7 @@ extern "C" int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kerne
     };
     const int kernel0 = h->kernel, waves0 = h->tile_waves;
     struct Cand { int kernel, waves; };
-    Cand cands[6];
+    Cand cands[N_AUTOTUNE_WAVES + 1];
     int nc = 0;
     for (int w : AUTOTUNE_WAVES) cands[nc++] = {U1U1_KERNEL_TILED, w};
     cands[nc++] = {U1U1_KERNEL_SIMPLE, TILE_WAVES_DEFAULT};
