@@ -79,10 +79,9 @@ def recorded_traffic(n, tag, waves):
             kv = dict(line.split(":", 1) for line in f if line.startswith("record-"))
         kv = {k.strip(): v.strip() for k, v in kv.items()}
         if (int(kv["record-lattice"]) != n or kv["record-precision"] != tag
-                or int(kv["record-waves"]) != waves
                 or kv["record-source-sha256"] != step_kernel_hash()):
             return None
-        return float(kv["record-dram-bytes-per-launch"])
+        return float(kv[f"record-dram-bytes-per-launch-w{waves}"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -303,7 +302,12 @@ def run_ours(args):
     p = workload_params(U, n, prec, seed=2024 + rank)
     lat = U.Lattice(p, device=dev, kernel=args.kernel)
     tune = None
-    if args.tune and args.kernel == U.KERNEL_AUTO:
+    if args.waves > 0:
+        # a fixed z-chunking of the tiled kernel instead of the autotuner's
+        lat.set_kernel(U.KERNEL_TILED)
+        lat.set_tile_waves(args.waves)
+        tune = {"kernel": U.KERNEL_TILED, "waves": args.waves, "fixed": True}
+    elif args.tune and args.kernel == U.KERNEL_AUTO:
         # the library's autotuner picks the step kernel and its z-chunking
         # on this lattice (timed on the lattice's own state, restored)
         tune = lat.autotune()
@@ -506,6 +510,8 @@ def main():
     ap.add_argument("--no-ensemble", dest="ensemble", action="store_false")
     ap.add_argument("--no-passes", dest="passes", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--waves", type=int, default=0,
+                    help="fixed wave target of the tiled step kernel (8 .. 256) instead of autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -331,6 +331,12 @@ int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kernel_out, int*
 #define U1U1_KERNEL_TILED 2
 int u1u1_set_kernel(u1u1_lattice* h, int kernel);
 int u1u1_get_kernel(const u1u1_lattice* h, int* kernel);
+/* z-chunking of the tiled kernel's plain steps, as a target of `waves` x
+ * (SMs x 3 resident CTAs) CTAs per launch: one of the tuner's candidates
+ * (8, 16, 32, 64, 128, 256), else INVALID_ARG (the block-partial buffers are
+ * sized for those grids).  Measuring passes keep the default chunking.  Lets
+ * a caller reproduce a tuned choice without timing. */
+int u1u1_set_tile_waves(u1u1_lattice* h, int waves);
 
 /* ---- ensembles of independent boxes ---------------------------------------- */
 
@@ -430,6 +436,15 @@ int u1u1_detect_strings_noalloc(const u1u1_params* p, const void* const fields[U
  * sin_out[k] and cos_out[k] (device arrays).  Lets tests bound its error against a double-precision
  * reference.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
 int u1u1_eval_link_phase(const float* theta, float* sin_out, float* cos_out, int64_t n, void* stream);
+
+/* Evaluate, on n device angles theta[k], the FP64 routine the FP64 kernels
+ * use for the link variable U = exp(-i theta) (Sec. III, Eqs. 17-21): the
+ * table-driven method (theta = m 2 pi / 1024 + r, a table of sin and cos at
+ * the multiples, short Taylor polynomials in r), writing sin_out[k] and
+ * cos_out[k] (device arrays).  Lets tests bound its error against a
+ * correctly rounded reference.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+int u1u1_eval_link_phase64(const double* theta, double* sin_out, double* cos_out, int64_t n, void* stream);
 
 /* Evaluate, on n device pairs (re[k], im[k]), the FP32 routine the kernels
  * use for the gauge-invariant edge phase chi = arg(re + i im) in [-pi, pi]

@@ -184,6 +184,10 @@ class Lattice:
     def set_kernel(self, kernel: int):
         check(lib().u1u1_set_kernel(self._h, int(kernel)))
 
+    def set_tile_waves(self, waves: int):
+        """z-chunking of the tiled plain step (one of the tuner's wave targets)."""
+        check(lib().u1u1_set_tile_waves(self._h, int(waves)))
+
     def autotune(self, cache_path=None, stream=None) -> dict:
         """Pick the step kernel and z-chunking by timing (state unchanged)."""
         k, w = ctypes.c_int(), ctypes.c_int()

@@ -123,9 +123,11 @@ PROTOTYPES = {
     "u1u1_save": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "u1u1_load": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "u1u1_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "u1u1_set_tile_waves": (ctypes.c_int, [_vp, ctypes.c_int]),
     "u1u1_get_kernel": (ctypes.c_int, [_vp, _P(ctypes.c_int)]),
     "u1u1_autotune": (ctypes.c_int, [_vp, ctypes.c_char_p, _P(ctypes.c_int), _P(ctypes.c_int), _vp]),
     "u1u1_eval_link_phase": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
+    "u1u1_eval_link_phase64": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
     "u1u1_eval_edge_phase": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
     "u1u1_ensemble_create": (ctypes.c_int, [_P(CParams), ctypes.c_int, _P(CBuffers), ctypes.c_int, _vp, _P(_vp)]),
     "u1u1_ensemble_run": (ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_int, ctypes.c_int, _vp]),

@@ -277,6 +277,11 @@ __global__ void k_link_phase(const float* __restrict__ th, float* sn, float* cs,
     link_sincos<float>(th[i], &sn[i], &cs[i]);
 }
 
+__global__ void k_link_phase64(const double* __restrict__ th, double* sn, double* cs, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    link_sincos<double>(th[i], &sn[i], &cs[i]);
+}
+
 __global__ void k_edge_phase(const float* __restrict__ re, const float* __restrict__ im, float* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = edge_phase<float>(re[i], im[i]);
@@ -291,6 +296,11 @@ cudaError_t launch_edge_phase(const float* re, const float* im, float* out, long
 
 cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n, cudaStream_t st) {
   k_link_phase<<<152 * 4, 256, 0, st>>>(th, sn, cs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_link_phase64(const double* th, double* sn, double* cs, long long n, cudaStream_t st) {
+  k_link_phase64<<<152 * 4, 256, 0, st>>>(th, sn, cs, n);
   return cudaGetLastError();
 }
 

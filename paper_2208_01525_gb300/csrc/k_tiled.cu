@@ -56,6 +56,20 @@ struct Tile {
   static __device__ __forceinline__ int at(int ly, int lx) { return (ly + 1) * RS + OFF + lx; }
 };
 
+// Sums a thread accumulates per site: all but the Lagrangian and the energy
+// (formed from the component sums on the host), the Gauss-law sums only in
+// the variant that computes the residual.
+__host__ __device__ constexpr bool acc_used(int k, bool gauss) {
+  return k != S_LAG && k != S_ENERGY &&
+         (gauss || (k != S_GAUSS_P && k != S_GAUSS_Q && k != S_CHARGE_P && k != S_CHARGE_Q));
+}
+// slot of sum k among the accumulated ones
+__host__ __device__ constexpr int acc_slot(int k, bool gauss) {
+  int j = 0;
+  for (int i = 0; i < k; ++i) j += acc_used(i, gauss) ? 1 : 0;
+  return j;
+}
+
 // Shared memory of one CTA; the detection and Gauss arrays shrink to one
 // element when the kernel variant does not use them.
 template <typename T, int TX, int TY, bool MEAS = true, bool GAUSS = true>
@@ -74,7 +88,8 @@ struct Smem {
   // FP32 detection: each thread's plain sums over up to ACC_PLANES planes,
   // folded into the warp sums once per ACC_PLANES planes
   static constexpr bool ACC = MEAS && sizeof(T) == 4;
-  T tacc[ACC ? NSUM : 1][ACC ? TL::NT : 1];
+  static constexpr int NACC = acc_slot(NSUM, GAUSS);
+  T tacc[ACC ? NACC : 1][ACC ? TL::NT : 1];
 };
 
 // Planes a thread sums in plain FP32 before its partials join the warp's
@@ -165,7 +180,7 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
     if ((tid & 31) == 0)
       for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = sm.wcmp[tid >> 5][k] = T(0);
     if (SM::ACC)
-      for (int k = 0; k < NSUM; ++k) sm.tacc[SM::ACC ? k : 0][SM::ACC ? tid : 0] = T(0);
+      for (int k = 0; k < SM::NACC; ++k) sm.tacc[SM::ACC ? k : 0][SM::ACC ? tid : 0] = T(0);
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;  // -inf is representable in T
 #pragma unroll
@@ -438,11 +453,10 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
       const bool fold = !SM::ACC || ((z - z0) % ACC_PLANES) == ACC_PLANES - 1 || z == z1 - 1;
 #pragma unroll
       for (int k = 0; k < NSUM; ++k) {
-        if (k == S_LAG || k == S_ENERGY) continue;
-        if (!GAUSS && (k == S_GAUSS_P || k == S_GAUSS_Q || k == S_CHARGE_P || k == S_CHARGE_Q)) continue;
+        if (!acc_used(k, GAUSS)) continue;
         T v2 = tv[k];
         if (SM::ACC) {
-          T& acc = sm.tacc[SM::ACC ? k : 0][SM::ACC ? tid : 0];
+          T& acc = sm.tacc[SM::ACC ? acc_slot(k, GAUSS) : 0][SM::ACC ? tid : 0];
           v2 += acc;
           acc = fold ? T(0) : v2;
         }

@@ -7,6 +7,7 @@
 
 #include <math.h>
 
+#include "sincos_table.cuh"
 #include "u1u1_internal.cuh"
 
 namespace u1u1 {
@@ -32,7 +33,34 @@ template <> __device__ __forceinline__ void link_sincos<float>(float x, float* s
   r = fmaf(-k, -1.74845553e-07f, r);            // 2 pi - fl(2 pi)
   __sincosf(r, s, c);
 }
-template <> __device__ __forceinline__ void link_sincos<double>(double x, double* s, double* c) { sincos(x, s, c); }
+// FP64: the table-driven method (Tang 1989).  theta = m h + r with
+// h = 2 pi / 1024, m = rint(theta / h) and |r| <= h / 2 (h split in two
+// doubles so that m h1 is exact); sin(m h) and cos(m h) from the table of
+// sincos_table.cuh, indexed by m mod 1024; sin r = r - r^3/6 + r^5/120 and
+// cos r - 1 = -r^2/2 + r^4/24 (truncation below 6e-22 and 1.2e-18 at
+// |r| <= 3.1e-3), combined by the angle-addition formulas with cos r - 1
+// kept apart so that nothing cancels.  About 14 FP64 operations against the
+// library sincos' larger count, on a step that is bound by GB300's FP64
+// rate; within two ulp of the exact values (tested against a correctly
+// rounded reference).  Arguments beyond the exact range of the reduction
+// (|theta| > 5e4, far outside any link angle of a run) take the library
+// sincos.
+template <> __device__ __forceinline__ void link_sincos<double>(double x, double* s, double* c) {
+  if (fabs(x) > SINCOS_TAB_MAX_ARG) {
+    sincos(x, s, c);
+    return;
+  }
+  const double m = rint(x * SINCOS_TAB_INV_H);
+  double r = fma(-m, SINCOS_TAB_H1, x);
+  r = fma(-m, SINCOS_TAB_H2, r);
+  const int j = (int)((long long)m & (SINCOS_TAB_N - 1));
+  const double2 t = __ldg(&k_sincos_tab[j]);  // {sin(m h), cos(m h)}
+  const double r2 = r * r;
+  const double sr = fma(r * r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), r);
+  const double cm1 = r2 * fma(r2, 1.0 / 24.0, -0.5);
+  *s = fma(t.y, sr, fma(t.x, cm1, t.x));
+  *c = fma(-t.x, sr, fma(t.y, cm1, t.y));
+}
 
 
 template <typename T> __device__ __forceinline__ T rint_t(T x);

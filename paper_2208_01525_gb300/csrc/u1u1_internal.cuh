@@ -192,6 +192,7 @@ cudaError_t launch_segments(const uint32_t* mpq, int nx, int ny, int nz, int min
 
 // The FP32 link-phase routine on n values (check entry point).
 cudaError_t launch_link_phase(const float* th, float* sn, float* cs, long long n, cudaStream_t st);
+cudaError_t launch_link_phase64(const double* th, double* sn, double* cs, long long n, cudaStream_t st);
 cudaError_t launch_edge_phase(const float* re, const float* im, float* out, long long n, cudaStream_t st);
 
 // Merge partials into a record.  part must have room for nblocks +

@@ -72,8 +72,9 @@ def test_traffic_record_is_keyed_by_kernel_source(tmp_path, monkeypatch):
     rec = tmp_path / "profiles"
     rec.mkdir()
     (rec / os.path.basename(bench.TRAFFIC_RECORD)).write_text(
-        "text\nrecord-lattice: 1024\nrecord-precision: fp32\nrecord-waves: 64\n"
-        f"record-source-sha256: {bench.step_kernel_hash()}\nrecord-dram-bytes-per-launch: 1.5e11\n")
+        "text\nrecord-lattice: 1024\nrecord-precision: fp32\n"
+        f"record-source-sha256: {bench.step_kernel_hash()}\nrecord-dram-bytes-per-launch-w64: 1.5e11\n"
+        "record-dram-bytes-per-launch-w256: 1.4e11\n")
     for rel in bench.STEP_KERNEL_SOURCES:
         dst = tmp_path / rel
         dst.parent.mkdir(parents=True, exist_ok=True)
@@ -82,7 +83,8 @@ def test_traffic_record_is_keyed_by_kernel_source(tmp_path, monkeypatch):
     assert bench.recorded_traffic(1024, "fp32", 64) == 1.5e11
     assert bench.recorded_traffic(512, "fp32", 64) is None
     assert bench.recorded_traffic(1024, "fp64", 64) is None
-    assert bench.recorded_traffic(1024, "fp32", 32) is None  # another z-chunking
+    assert bench.recorded_traffic(1024, "fp32", 256) == 1.4e11
+    assert bench.recorded_traffic(1024, "fp32", 32) is None  # a z-chunking without a record
     # any change to the kernel's sources voids the record
     src = tmp_path / bench.STEP_KERNEL_SOURCES[0]
     src.write_bytes(src.read_bytes() + b"\n")

@@ -403,6 +403,36 @@ def test_link_phase_routine_accuracy():
     assert es < 6e-7 and ec < 6e-7, (es, ec)
 
 
+def test_fp64_link_phase_routine_accuracy():
+    """The FP64 link-phase routine (table-driven: theta = m 2 pi/1024 + r)
+    against the host's double-precision sine and cosine: within 2.5e-16
+    absolute (about one ulp at 1) over the range lattices reach, at the
+    rounding edges of m (odd multiples of pi/1024), on and beyond the exact
+    range of the reduction (|theta| > 5.1e4 takes the library routine), and
+    sin^2 + cos^2 = 1 to the same order."""
+    import ctypes
+    h = 2.0 * np.pi / 1024
+    edges = np.concatenate([(np.arange(-3000, 3000) + 0.5) * h, np.arange(-3000, 3000) * h])
+    edges = np.concatenate([edges, np.nextafter(edges, np.inf), np.nextafter(edges, -np.inf)])
+    special = np.array([0.0, -0.0, 1e-300, 5e-324, np.pi, -np.pi, 2 * np.pi, 4.0e4, -5.1e4, 5.2e4, -6.0e4,
+                        1.0e6, 1.0e9])
+    th_h = np.concatenate([np.linspace(-60.0, 60.0, 1_000_001), edges, special])
+    th = torch.from_numpy(th_h).cuda()
+    sn = torch.empty_like(th)
+    cs = torch.empty_like(th)
+    U.check(U.lib().u1u1_eval_link_phase64(ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(sn.data_ptr()),
+                                           ctypes.c_void_p(cs.data_ptr()), th.numel(),
+                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.cuda.synchronize()
+    s_g, c_g = sn.cpu().numpy(), cs.cpu().numpy()
+    es = np.abs(s_g - np.sin(th_h))
+    ec = np.abs(c_g - np.cos(th_h))
+    assert es.max() <= 2.5e-16 and ec.max() <= 2.5e-16, (es.max(), ec.max(), th_h[np.argmax(es)], th_h[np.argmax(ec)])
+    assert np.abs(s_g * s_g + c_g * c_g - 1.0).max() <= 8e-16
+    k0 = th_h.size - special.size
+    assert s_g[k0] == 0.0 and s_g[k0 + 1] == 0.0 and c_g[k0] == 1.0 and c_g[k0 + 1] == 1.0
+
+
 def test_edge_phase_routine_accuracy():
     """The FP32 edge phase arg(re + i im) (octant reduction + minimax
     polynomial) stays within 4e-7 rad of the double-precision arctangent of
@@ -469,7 +499,7 @@ def test_autotune_keeps_state_and_reuses_cache(tmp_path):
 
 
 def test_autotune_refuses_foreign_cache_entry(tmp_path):
-    """A cache entry naming a wave count the tuner never picks (here 128) is
+    """A cache entry naming a wave count the tuner never picks (here 96) is
     refused before any launch: the block-partial buffers are sized for the
     tuner's own candidate grids.  The handle keeps its kernel choice."""
     p = radiation(64, 640, precision=U.FP32, seed=6)
@@ -479,15 +509,19 @@ def test_autotune_refuses_foreign_cache_entry(tmp_path):
     key = open(cache).read().split()[0]
     bad = str(tmp_path / "bad.txt")
     with open(bad, "w") as f:
-        f.write(f"{key} {U.KERNEL_TILED} 128\n")
+        f.write(f"{key} {U.KERNEL_TILED} 96\n")
     b = U.Lattice(p)
     k0 = b.kernel()
     with pytest.raises(U.U1U1Error) as ei:
         b.autotune(cache_path=bad)
-    assert ei.value.code == -1 and "128" in str(ei.value)  # INVALID_ARG
+    assert ei.value.code == -1 and "96" in str(ei.value)  # INVALID_ARG
     assert b.kernel() == k0
     with open(bad, "w") as f:
         f.write(f"{key} 7 32\n")
     with pytest.raises(U.U1U1Error):
         b.autotune(cache_path=bad)
+    # the same rule for a directly set chunking
+    b.set_tile_waves(256)
+    with pytest.raises(U.U1U1Error):
+        b.set_tile_waves(96)
     assert choice["kernel"] in (U.KERNEL_TILED, U.KERNEL_SIMPLE)
