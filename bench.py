@@ -37,10 +37,10 @@ if ROOT not in sys.path:
 
 METRIC = "site-updates/s & % HBM roofline, FP32 vs FP64, U(1)xU(1) step at 1024^3"
 BYTES_PER_SITE = {"fp32": 160, "fp64": 320}  # read 20 + write 20 words
-# FP64 step: 177 DFMA + 60 DADD + 64 DMUL per site (ncu thread-instruction
-# counts of one launch at 256^3) = 478 FP64 operations; nominal FP64 rate of
+# FP64 step: 126 DFMA + 60 DADD + 77 DMUL per site (ncu thread-instruction
+# counts of one launch at 256^3) = 389 FP64 operations; nominal FP64 rate of
 # the GB300 (non-tensor) 1.25 TFLOP/s
-FP64_FLOPS_PER_SITE = 478
+FP64_FLOPS_PER_SITE = 389
 FP64_PEAK_TFLOPS = 1.25
 
 
@@ -385,13 +385,18 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         lat.upload(host)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         for _ in range(args.steps):
             lat.step(de, detect_every=de)
             lat.read_records()                # D2H of the period's record + host epilogue
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         lat.download(host)
         torch.cuda.synchronize()
         barrier()
-        e2e_s = time.perf_counter() - t0
+        t3 = time.perf_counter()
+        e2e_s = t3 - t0
         state_bytes = 20 * V * lat.dtype.itemsize
         rec_bytes = 360  # one detection record copied per period
         _, e2e_value = combine_ranks(e2e_s * 1e3, args.steps * de * V, world, dev)
@@ -399,7 +404,8 @@ def run_ours(args):
                "h2d_bytes_per_step": state_bytes / args.steps,
                "d2h_bytes_per_step": state_bytes / args.steps + rec_bytes,
                "what": "upload state from pinned host, K periods each followed by a record read, "
-                       "download state"}
+                       "download state",
+               "upload_s": t1 - t0, "periods_s": t2 - t1, "download_s": t3 - t2}
         del host
 
     lat.close()

@@ -85,11 +85,14 @@ struct Smem {
   // run on GB300's narrow FP64 pipe once per warp, sum and plane
   T wsum[MEAS ? TL::NT / 32 : 1][NSUM];
   T wcmp[MEAS ? TL::NT / 32 : 1][NSUM];
-  // FP32 detection: each thread's plain sums over up to ACC_PLANES planes,
-  // folded into the warp sums once per ACC_PLANES planes
+  // FP32 detection: each thread keeps plain sums over up to ACC_PLANES
+  // planes in registers (NACC of them), folded into the warp sums once per
+  // ACC_PLANES planes.  Registers rather than shared memory: the measuring
+  // variants run at two CTAs per SM and have the registers to spare, and a
+  // shared-memory read-modify-write per sum and site cost 2.5 ms per
+  // detection step and 4 ms per diagnostics pass at 1024^3.
   static constexpr bool ACC = MEAS && sizeof(T) == 4;
   static constexpr int NACC = acc_slot(NSUM, GAUSS);
-  T tacc[ACC ? NACC : 1][ACC ? TL::NT : 1];
 };
 
 // Planes a thread sums in plain FP32 before its partials join the warp's
@@ -176,11 +179,13 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
 
   T mx[NMAX];
   int cnt[NCNT];
+  T racc[SM::ACC ? SM::NACC : 1];
+#pragma unroll
+  for (int k = 0; k < (SM::ACC ? SM::NACC : 1); ++k) racc[k] = T(0);
   if (MEAS) {
     if ((tid & 31) == 0)
       for (int k = 0; k < NSUM; ++k) sm.wsum[tid >> 5][k] = sm.wcmp[tid >> 5][k] = T(0);
-    if (SM::ACC)
-      for (int k = 0; k < SM::NACC; ++k) sm.tacc[SM::ACC ? k : 0][SM::ACC ? tid : 0] = T(0);
+
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) mx[k] = -INFINITY;  // -inf is representable in T
 #pragma unroll
@@ -456,7 +461,7 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
         if (!acc_used(k, GAUSS)) continue;
         T v2 = tv[k];
         if (SM::ACC) {
-          T& acc = sm.tacc[SM::ACC ? acc_slot(k, GAUSS) : 0][SM::ACC ? tid : 0];
+          T& acc = racc[SM::ACC ? acc_slot(k, GAUSS) : 0];
           v2 += acc;
           acc = fold ? T(0) : v2;
         }

@@ -22,8 +22,10 @@
 // and the flag depend on the rounding of d only within rounding of an odd
 // multiple of pi, where chi is within rounding of +-pi and the edge is
 // flagged (pi - |chi| < 1e-4).  A zero field makes alpha undefined: alpha is
-// stored as NaN there, so every edge touching the site is flagged (and gets
-// k = 0).
+// stored as NaN there, so every edge touching the site is flagged and every
+// plaquette with such an edge gets W = 0.  The k are kept as floating-point
+// integers: their four-term sums are exact, and each winding is converted
+// to an integer once.
 //
 // CTA: 8 warps x 32 lanes on a (32 x 8)-site window that advances by 31 in x
 // and 7 in y, so that lane 31 and warp 7 hold the right column and the top
@@ -83,14 +85,15 @@ template <> __device__ __forceinline__ float cut_frac<float>() { return 0.499984
 template <> __device__ __forceinline__ double cut_frac<double>() { return 0.49998408450991098; }
 
 // Branch integer k of the edge from a site of phase a_t to a site of phase
-// a_h across a link of angle theta, and whether the edge is flagged (near the
-// cut, or a zero field at either end: then d is NaN, k = 0 and the test below
-// fails).
+// a_h across a link of angle theta, as a floating-point integer (sums of a
+// few k are exact), and whether the edge is flagged (near the cut, or a zero
+// field at either end: then d and k are NaN and the test below fails; a
+// plaquette with such an edge gets W = 0).
 template <typename T>
-__device__ __forceinline__ int edge_k(T a_h, T a_t, T theta, bool* cut) {
+__device__ __forceinline__ T edge_k(T a_h, T a_t, T theta, bool* cut) {
   const T t = ((a_h - a_t) - theta) * Consts<T>::inv_two_pi();
-  const int k = round_int<T>(t);
-  *cut = !(fabs(t - T(k)) <= cut_frac<T>());
+  const T k = rint_t<T>(t);
+  *cut = !(fabs(t - k) <= cut_frac<T>());
   return k;
 }
 
@@ -139,7 +142,7 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
     }
   }
   // plaquettes of the plane below waiting for this plane's k_0, k_1
-  int pW01[2] = {0, 0}, pW02[2] = {0, 0}, pW12[2] = {0, 0};
+  T pW01[2] = {T(0), T(0)}, pW02[2] = {T(0), T(0)}, pW12[2] = {T(0), T(0)};
   unsigned pcut[2] = {0u, 0u};
 
   for (int z = z0; z <= z1; ++z) {
@@ -171,15 +174,15 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
       const T ax = __shfl_down_sync(0xffffffffu, al[s], 1);
       const T ay = qc.al[s][ty];
       bool c0, c1;
-      const int k0 = edge_k<T>(ax, al[s], dx * A[s][0], &c0);
-      const int k1 = edge_k<T>(ay, al[s], dx * A[s][1], &c1);
+      const T k0 = edge_k<T>(ax, al[s], dx * A[s][0], &c0);
+      const T k1 = edge_k<T>(ay, al[s], dx * A[s][1], &c1);
 
       // finish and emit the plane below
       if (z > z0 && out) {
         const long long gs = (long long)(z - 1) * plane + col;
-        const int W0 = pW01[s];
-        const int W1 = pW02[s] + k0;
-        const int W2 = pW12[s] + k1;
+        const int W0 = round_int<T>(pW01[s]);  // NaN (flagged) -> 0
+        const int W1 = round_int<T>(pW02[s] + k0);
+        const int W2 = round_int<T>(pW12[s] + k1);
         const unsigned ckm = pcut[s] | (c0 ? 2u : 0u) | (c1 ? 4u : 0u);
         const int a0 = abs(W0), a1 = abs(W1), a2 = abs(W2);
         unsigned byte = (unsigned)min(a0, 3) | ((unsigned)min(a1, 3) << FACE_SHIFT(1)) |
@@ -202,14 +205,14 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
 
       // own edge 2, and edges 0 and 2 of the row above (x + y)
       bool c2, c0y, c2y;
-      const int k2 = edge_k<T>(aln[s], al[s], dx * A[s][2], &c2);
+      const T k2 = edge_k<T>(aln[s], al[s], dx * A[s][2], &c2);
       const T axy = __shfl_down_sync(0xffffffffu, ay, 1);
-      const int k0y = edge_k<T>(axy, ay, dx * qc.a0[s][ty], &c0y);
-      const int k2y = edge_k<T>(qn.al[s][ty], ay, dx * qc.a2[s][ty], &c2y);
+      const T k0y = edge_k<T>(axy, ay, dx * qc.a0[s][ty], &c0y);
+      const T k2y = edge_k<T>(qn.al[s][ty], ay, dx * qc.a2[s][ty], &c2y);
       // edges 1 and 2 of x + x by shuffle
       const unsigned cb = (c1 ? 1u : 0u) | (c2 ? 2u : 0u);
-      const int k1x = __shfl_down_sync(0xffffffffu, k1, 1);
-      const int k2x = __shfl_down_sync(0xffffffffu, k2, 1);
+      const T k1x = __shfl_down_sync(0xffffffffu, k1, 1);
+      const T k2x = __shfl_down_sync(0xffffffffu, k2, 1);
       const unsigned cx = __shfl_down_sync(0xffffffffu, cb, 1);
       pW01[s] = -(k0 + k1x - k0y - k1);
       pW02[s] = -(k0 + k2x - k2);  // + k_0 of the plane above
