@@ -103,6 +103,34 @@ def combine_ranks(ms, units_local, world, device=None):
     return ms, units / (ms * 1e-3)
 
 
+def _cdiv(a, b):
+    return -(-a // b)
+
+
+def measure_partials(n, tiled):
+    """Block partials a detection step of an n^3 lattice writes (the grid
+    formulas of the library's measuring kernels: the step kernel's 32-wave
+    z-chunking plus the windings kernel's on the tiled path; the simple
+    kernel's fixed grid otherwise)."""
+    if not tiled:
+        return 152 * 8
+    tiles = _cdiv(n, 32) * _cdiv(n, 8)
+    chunks = max(1, _cdiv(152 * 3 * 32, tiles))
+    lz = min(max(_cdiv(n, chunks), 32), n)
+    step = tiles * _cdiv(n, lz)
+    wt = _cdiv(n, 31) * _cdiv(n, 7)
+    wc = max(1, min(_cdiv(152 * 3 * 16, wt), n // 32))
+    return step + wt * _cdiv(n, _cdiv(n, wc))
+
+
+def launches_per_period(n, de, tiled):
+    """Kernel launches of one detection period: de step launches (the first
+    one measuring), the windings kernel (tiled path), cell bits, overlap and
+    the finalize (two stages above 2048 block partials)."""
+    stage = 1 if measure_partials(n, tiled) > 2048 else 0
+    return de + (1 if tiled else 0) + 2 + 1 + stage
+
+
 def workload_params(U, n, precision, beta=1.0, seed=2024):
     # 2560 steps to eta = 257 for the 1024^3 box; a = 1 at the end of the run
     return U.Params.cube(n, m=0.5, beta=beta, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=seed,
@@ -479,9 +507,7 @@ def run_ours(args):
             "detect_ms_per_period": det_ms,
             "passes": passes,
             "clocks": clocks,
-            # per period: de step launches (the first one measuring), the
-            # windings kernel (tiled path), cell bits, overlap, finalize
-            "gpu_launches": args.steps * (de + 3 if kernel_used != U.KERNEL_SIMPLE else de + 2),
+            "gpu_launches": args.steps * launches_per_period(n, de, kernel_used != U.KERNEL_SIMPLE),
             "e2e": e2e,
             "fp64": fp64,
             "ensemble": ens,

@@ -89,3 +89,13 @@ def test_traffic_record_is_keyed_by_kernel_source(tmp_path, monkeypatch):
     src = tmp_path / bench.STEP_KERNEL_SOURCES[0]
     src.write_bytes(src.read_bytes() + b"\n")
     assert bench.recorded_traffic(1024, "fp32", 64) is None
+
+
+def test_launch_count_per_detection_period():
+    """One period at 1024^3 on the tiled path: 16 step launches, windings,
+    cell bits, overlap and the two finalize stages (the launch list of the
+    benchmark shows 21 per period); small lattices skip the first stage."""
+    assert bench.launches_per_period(1024, 16, True) == 21
+    assert bench.measure_partials(1024, True) == 16384 + 34 * 147 * 2
+    assert bench.launches_per_period(64, 16, True) == 20
+    assert bench.launches_per_period(64, 16, False) == 19
