@@ -225,6 +225,21 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
     }
   }
 
+  // momenta of the next plane, issued a plane ahead so that their loads are
+  // in flight across the barrier and phase 1 (consumed in phase 2)
+  T npr[2], npim[2], nE[2][3];
+  auto load_mom = [&](int zz) {
+    const long long gs = (long long)zz * plane + (long long)gy * v.nx + gx;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      npr[s] = active ? ld_mom<COHERENT>(&v.mom[2 * s][gs]) : T(0);
+      npim[s] = active ? ld_mom<COHERENT>(&v.mom[2 * s + 1][gs]) : T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) nE[s][i] = active ? ld_mom<COHERENT>(&v.mom[4 + 3 * s + i][gs]) : T(0);
+    }
+  };
+  load_mom(z0);
+
   for (int z = z0; z < z1; ++z) {
     const int it = z - z0;
     const int bc = (it + 1) % 3, bn = (it + 2) % 3, bf = it % 3;
@@ -239,22 +254,14 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
     }
 
     const long long gsite = (long long)z * plane + (long long)gy * v.nx + gx;
-    // momenta of the own site (plain loads; consumed after phase 1)
+    // momenta of the own site, loaded during the previous plane
     T pr[2], pim[2], E[2][3];
-    if (active) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        pr[s] = ld_mom<COHERENT>(&v.mom[2 * s][gsite]);
-        pim[s] = ld_mom<COHERENT>(&v.mom[2 * s + 1][gsite]);
+    for (int s = 0; s < 2; ++s) {
+      pr[s] = npr[s];
+      pim[s] = npim[s];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) E[s][i] = ld_mom<COHERENT>(&v.mom[4 + 3 * s + i][gsite]);
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        pr[s] = pim[s] = T(0);
-        E[s][0] = E[s][1] = E[s][2] = T(0);
-      }
+      for (int i = 0; i < 3; ++i) E[s][i] = nE[s][i];
     }
 
     // ---- phase 1: site-local quantities of plane z ----
@@ -486,6 +493,7 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
       cF12[s] = F[s][2];
       cE2[s] = E[s][2];
     }
+    if (z + 1 < z1) load_mom(z + 1);
   }
   cp_async_wait0();
 
