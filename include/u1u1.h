@@ -258,7 +258,8 @@ int u1u1_set_overlap_tol(u1u1_lattice* h, int tol);
 
 /* Fast string detection on the current state without stepping (Sec. III.A-B).
  * Optional device outputs (NULL to skip): cell_p, cell_q (uint8 per site:
- * sum over the cell's six faces of |W|, each |W| counted up to 3),
+ * sum over the cell's six faces of |W|, each |W| counted up to 3; any
+ * alignment, 16-byte aligned arrays take the vectorised pass),
  * windings (int8, 6 arrays of nx*ny*nz: sector-major, plane (x,y), (x,z),
  * (y,z), the plaquette anchored at each site).  *out is filled on the host
  * (synchronises `stream`).  Errors: INVALID_ARG, CUDA. */

@@ -11,6 +11,7 @@ import pytest
 
 import oracle as O
 import paper_2208_01525_gb300 as U
+from paper_2208_01525_gb300 import _abi
 import synth
 from gpu_helpers import field_maxrel, gather_sites, host_state, patches, to_oracle
 
@@ -146,6 +147,34 @@ def test_windings_fp32_rough_ragged_with_zero_field(kernel, shape):
     res, ores, nflag = _windings_compare(p, lat)
     assert ores["n_flagged"] >= 24 and res["n_flagged"] >= 24
     assert res["max_abs_w"] >= 1
+
+
+def test_cell_arrays_any_alignment():
+    """Cell arrays written to 16-byte aligned buffers (the vectorised cell
+    pass) and to buffers offset by one byte (the bytewise pass) agree with
+    each other and with the oracle's cells, and so do the counts."""
+    import ctypes
+    p = radiation(64, 640, precision=U.FP32, seed=8)
+    lat = U.Lattice(p)
+    lat.step(24)
+    ref = lat.detect_strings(tol=1, cells=True)
+    V = p.nsites
+    raw = torch.zeros(2 * V + 32, dtype=torch.uint8, device="cuda")
+    cp, cq = raw.data_ptr() + 1, raw.data_ptr() + V + 17
+    out = _abi.CStrings()
+    U.check(U.lib().u1u1_detect_strings(lat._h, 1, ctypes.c_void_p(cp), ctypes.c_void_p(cq), None,
+                                        ctypes.byref(out), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    odd = _abi.struct_to_dict(out)
+    got = torch.stack([raw[1:1 + V], raw[V + 17:V + 17 + V]]).view(2, *p.shape)
+    assert torch.equal(got.cpu(), ref["cells"].cpu())
+    for k in ("n_p", "n_q", "n_pq_cell", "n_pq_cell_q", "n_cells_ge4_p", "n_cells_ge4_q", "n_flagged"):
+        assert odd[k] == ref[k], k
+    snap = host_state(lat)
+    ores = O.strings(to_oracle(p), snap, tol=1)
+    W, F = O.windings(to_oracle(p), snap)
+    if int((F != 0).sum()) == 0:
+        assert np.array_equal(ref["cells"].cpu().numpy(), ores["cells"])
+        assert ref["n_pq_cell"] == ores["n_pq_cell"]
 
 
 def test_higher_winding_census():
