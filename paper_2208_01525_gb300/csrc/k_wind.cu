@@ -56,15 +56,19 @@ constexpr int WNT = WW * WH;  // threads per CTA
 constexpr int WIND_MIN_LZ = 32;
 constexpr int WIND_TARGET_CTAS = 152 * 3 * 16;  // 3 resident CTAs per SM, about 16 waves
 
-// What the row below needs of a site in one plane: alpha, A_0, A_2 per sector.
+// What the row below needs of a site: alpha of each plane (three-plane
+// ring), and, one plane later, the branch integers of edges 0 and 2 with
+// their cut bits (two-plane ring).
 template <typename T>
-struct WindPlane {
-  T al[2][WNT], a0[2][WNT], a2[2][WNT];
+struct WindEdges {
+  T k0[2][WNT], k2[2][WNT];
+  uint8_t cut[2][WNT];  // bit 0: edge 0, bit 2: edge 2
 };
 
 template <typename T>
 struct WindSmem {
-  WindPlane<T> q[3];  // by plane index mod 3
+  T al[3][2][WNT];      // by plane index mod 3
+  WindEdges<T> e[2];    // by plane index mod 2
   int cnt[WH][NCNT];
 };
 
@@ -132,18 +136,17 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
     T fr[2], fi[2];
     load_plane(z0, fr, fi, A);
     load_plane(z0 + 1, nfr, nfi, nA);
-    WindPlane<T>& q = sm.q[z0 % 3];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       al[s] = site_phase<T>(fr[s], fi[s]);
-      q.al[s][t] = al[s];
-      q.a0[s][t] = A[s][0];
-      q.a2[s][t] = A[s][2];
+      sm.al[z0 % 3][s][t] = al[s];
     }
   }
-  // plaquettes of the plane below waiting for this plane's k_0, k_1
-  T pW01[2] = {T(0), T(0)}, pW02[2] = {T(0), T(0)}, pW12[2] = {T(0), T(0)};
-  unsigned pcut[2] = {0u, 0u};
+  // the plane below's plaquettes, short of the edges of this plane (and, for
+  // 01 and 12, of the row above): W01 = P01 + k0(x+y), W02 = P02 + k0(x+z),
+  // W12 = P12 - k2(x+y) + k1(x+z); cut bits likewise
+  T P01[2] = {T(0), T(0)}, P02[2] = {T(0), T(0)}, P12[2] = {T(0), T(0)};
+  unsigned pc[2] = {0u, 0u};  // bit 0: 01, bit 1: 02, bit 2: 12
 
   for (int z = z0; z <= z1; ++z) {
     const bool last = z == z1;
@@ -151,28 +154,25 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
     // the plane after it
     T aln[2], An[2][3];
     if (!last) {
-      WindPlane<T>& qn = sm.q[(z + 1) % 3];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         aln[s] = site_phase<T>(nfr[s], nfi[s]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) An[s][i] = nA[s][i];
-        qn.al[s][t] = aln[s];
-        qn.a0[s][t] = An[s][0];
-        qn.a2[s][t] = An[s][2];
+        sm.al[(z + 1) % 3][s][t] = aln[s];
       }
       if (z + 1 < z1) load_plane(z + 2, nfr, nfi, nA);
     }
     __syncthreads();
-    const WindPlane<T>& qc = sm.q[z % 3];
-    const WindPlane<T>& qn = sm.q[(z + 1) % 3];
+    const WindEdges<T>& eb = sm.e[(z + 1) & 1];  // the row above's edges of plane z-1
+    WindEdges<T>& ec = sm.e[z & 1];              // this row's edges of plane z
 
     unsigned nzm[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       // own edges 0 and 1 of this plane
       const T ax = __shfl_down_sync(0xffffffffu, al[s], 1);
-      const T ay = qc.al[s][ty];
+      const T ay = sm.al[z % 3][s][ty];
       bool c0, c1;
       const T k0 = edge_k<T>(ax, al[s], dx * A[s][0], &c0);
       const T k1 = edge_k<T>(ay, al[s], dx * A[s][1], &c1);
@@ -180,10 +180,11 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
       // finish and emit the plane below
       if (z > z0 && out) {
         const long long gs = (long long)(z - 1) * plane + col;
-        const int W0 = round_int<T>(pW01[s]);  // NaN (flagged) -> 0
-        const int W1 = round_int<T>(pW02[s] + k0);
-        const int W2 = round_int<T>(pW12[s] + k1);
-        const unsigned ckm = pcut[s] | (c0 ? 2u : 0u) | (c1 ? 4u : 0u);
+        const unsigned cy = eb.cut[s][ty];
+        const int W0 = round_int<T>(P01[s] + eb.k0[s][ty]);  // NaN (flagged) -> 0
+        const int W1 = round_int<T>(P02[s] + k0);
+        const int W2 = round_int<T>(P12[s] - eb.k2[s][ty] + k1);
+        const unsigned ckm = pc[s] | (cy & 1u) | (c0 ? 2u : 0u) | ((c1 || (cy & 4u)) ? 4u : 0u);
         const int a0 = abs(W0), a1 = abs(W1), a2 = abs(W2);
         unsigned byte = (unsigned)min(a0, 3) | ((unsigned)min(a1, 3) << FACE_SHIFT(1)) |
                         ((unsigned)min(a2, 3) << FACE_SHIFT(2));
@@ -203,22 +204,21 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
       }
       if (last) continue;
 
-      // own edge 2, and edges 0 and 2 of the row above (x + y)
-      bool c2, c0y, c2y;
+      // own edge 2; publish edges 0 and 2 for the row below
+      bool c2;
       const T k2 = edge_k<T>(aln[s], al[s], dx * A[s][2], &c2);
-      const T axy = __shfl_down_sync(0xffffffffu, ay, 1);
-      const T k0y = edge_k<T>(axy, ay, dx * qc.a0[s][ty], &c0y);
-      const T k2y = edge_k<T>(qn.al[s][ty], ay, dx * qc.a2[s][ty], &c2y);
+      ec.k0[s][t] = k0;
+      ec.k2[s][t] = k2;
+      ec.cut[s][t] = (uint8_t)((c0 ? 1u : 0u) | (c2 ? 4u : 0u));
       // edges 1 and 2 of x + x by shuffle
       const unsigned cb = (c1 ? 1u : 0u) | (c2 ? 2u : 0u);
       const T k1x = __shfl_down_sync(0xffffffffu, k1, 1);
       const T k2x = __shfl_down_sync(0xffffffffu, k2, 1);
       const unsigned cx = __shfl_down_sync(0xffffffffu, cb, 1);
-      pW01[s] = -(k0 + k1x - k0y - k1);
-      pW02[s] = -(k0 + k2x - k2);  // + k_0 of the plane above
-      pW12[s] = -(k1 + k2y - k2);  // + k_1 of the plane above
-      pcut[s] = ((c0 || (cx & 1u) || c0y || c1) ? 1u : 0u) | ((c0 || (cx & 2u) || c2) ? 2u : 0u) |
-                ((c1 || c2y || c2) ? 4u : 0u);
+      P01[s] = -(k0 + k1x - k1);  // + k_0 of the row above
+      P02[s] = -(k0 + k2x - k2);  // + k_0 of the plane above
+      P12[s] = -(k1 - k2);        // - k_2 of the row above + k_1 of the plane above
+      pc[s] = ((c0 || (cx & 1u) || c1) ? 1u : 0u) | ((c0 || (cx & 2u) || c2) ? 2u : 0u) | ((c1 || c2) ? 4u : 0u);
       al[s] = aln[s];
 #pragma unroll
       for (int i = 0; i < 3; ++i) A[s][i] = An[s][i];
