@@ -30,14 +30,15 @@
 // CTA: 8 warps x 32 lanes on a (32 x 8)-site window that advances by 31 in x
 // and 7 in y, so that lane 31 and warp 7 hold the right column and the top
 // row of the tile's halo.  Each thread computes alpha of its own site once
-// per sector and plane.  alpha of x+1 comes by warp shuffle; alpha, A_0 and
-// A_2 of the row above come from a three-plane shared ring (one barrier per
-// plane), from which each thread also recomputes the two edges of the row
-// above that its plaquettes need (k_0 and k_2 at x+y); alpha of z+1 is the
-// thread's next plane, whose raw fields are prefetched a plane ahead.  The
-// CTA marches a chunk of planes [z0, z1) and emits the face byte of plane z-1
-// at plane z, once that plane's k_0 and k_1 complete the 02 and 12
-// plaquettes.
+// per sector and plane, and the branch integers of its own three edges.
+// alpha of x+1 comes by warp shuffle, alpha of the row above from a
+// three-plane shared ring (one barrier per plane), alpha of z+1 from the
+// thread's next plane, whose raw fields are prefetched a plane ahead.  Each
+// row publishes its k_0 and k_2 (and cut bits) in a two-plane ring; the row
+// below reads them after the next barrier.  So the CTA marches a chunk of
+// planes [z0, z1) and emits the face byte of plane z-1 at plane z, when the
+// row above's edges of plane z-1 and its own k_0 and k_1 of plane z complete
+// the 01, 02 and 12 plaquettes.
 #include <stdint.h>
 
 #include "reduce.cuh"
