@@ -246,6 +246,66 @@ k_overlap(const uint32_t* __restrict__ mp, const uint32_t* __restrict__ mq, int 
   }
 }
 
+// k_overlap for rows of exactly 32 mask words (nx = 1024): one warp per row,
+// lane = word, so the words left and right of a lane's word come by shuffle
+// (periodic in x within the warp) and each of the nine neighbour rows costs
+// one load per mask.
+__global__ void __launch_bounds__(OVL_THREADS)
+k_overlap_row32(const uint32_t* __restrict__ mp, const uint32_t* __restrict__ mq, int ny, int nz, int tol,
+                CellPartial* part, uint32_t* mpq) {
+  const long long nrows = (long long)ny * nz;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long cnt[2] = {0, 0};
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < nrows; row += nwarps) {
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const long long idx = row * 32 + lane;
+    const uint32_t p = mp[idx], q = mq[idx];
+    if (tol == 0) {
+      cnt[0] += __popc(p & q);
+      cnt[1] += __popc(p & q);
+      if (mpq) mpq[idx] = p & q;
+      continue;
+    }
+    if (__all_sync(0xffffffffu, (p | q) == 0)) {
+      if (mpq) mpq[idx] = 0u;
+      continue;
+    }
+    // union of the 3 x 3 rows' bits, then dilation in x once
+    uint32_t uq = 0, up = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = z + dz < 0 ? nz - 1 : (z + dz >= nz ? 0 : z + dz);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy < 0 ? ny - 1 : (y + dy >= ny ? 0 : y + dy);
+        const long long rb = ((long long)zz * ny + yy) * 32;
+        uq |= mq[rb + lane];
+        up |= mp[rb + lane];
+      }
+    }
+    const uint32_t lq = __shfl_sync(0xffffffffu, uq, (lane + 31) & 31), rq = __shfl_sync(0xffffffffu, uq, (lane + 1) & 31);
+    const uint32_t lp = __shfl_sync(0xffffffffu, up, (lane + 31) & 31), rp = __shfl_sync(0xffffffffu, up, (lane + 1) & 31);
+    const uint32_t dq = uq | (uq << 1) | (uq >> 1) | (lq >> 31) | (rq << 31);
+    const uint32_t dp = up | (up << 1) | (up >> 1) | (lp >> 31) | (rp << 31);
+    cnt[0] += __popc(p & dq);
+    cnt[1] += __popc(q & dp);
+    if (mpq) mpq[idx] = p & dq;  // the p-anchored bound-state cells
+  }
+  __shared__ long long sm[OVL_THREADS / 32][2];
+  const int warp = threadIdx.x >> 5;
+  for (int a = 0; a < 2; ++a) {
+    const long long v = warp_sum_ll(cnt[a]);
+    if (lane == 0) sm[warp][a] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    long long v = 0;
+    for (int k = 0; k < OVL_THREADS / 32; ++k) v += sm[k][threadIdx.x];
+    part[blockIdx.x].pq[threadIdx.x] = v;
+  }
+}
+
 // ---- finalize: fixed-order compensated merge of the block partials --------
 
 constexpr int FIN_THREADS = 256;
@@ -398,7 +458,10 @@ cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, 
     k_cellbits<<<grid, block, 0, st>>>(faces, nx, ny, nz, words, cell_p, cell_q, mp, mq, ge4);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part, mpq);
+  if (words == 32 && nx == 1024)
+    k_overlap_row32<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, ny, nz, tol, part, mpq);
+  else
+    k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part, mpq);
   return cudaGetLastError();
 }
 

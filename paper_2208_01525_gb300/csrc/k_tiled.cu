@@ -427,20 +427,31 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
         tv[S_RL_DEN] = gt * L;
         tv[S_RPQ_NUM] = kt * vint;
         tv[S_RPQ_DEN] = gt * vint;
+        // extremes of |phi|^2 (|phi| after the block's last plane: the
+        // square root is monotonic and correctly rounded)
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const T m = sqrt(mod2[s]);
-          mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q] = fmax(mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q], -m);
-          mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q] = fmax(mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q], m);
+          mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q] = fmax(mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q], -mod2[s]);
+          mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q] = fmax(mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q], mod2[s]);
         }
-        int nan = 0;
+        // NaN entries among the site's 20 fields: their sum is finite unless
+        // one of them is NaN or infinite (or the sum overflows), and only
+        // then are they counted one by one
+        T all = pr[0] + pim[0] + pr[1] + pim[1];
 #pragma unroll
-        for (int f = 0; f < U1U1_NPOS; ++f) nan += isnan(sm.pos[bc][f][a]) ? 1 : 0;
+        for (int s = 0; s < 2; ++s) all += E[s][0] + E[s][1] + E[s][2];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          nan += isnan(pr[s]) + isnan(pim[s]) + isnan(E[s][0]) + isnan(E[s][1]) + isnan(E[s][2]);
+        for (int f = 0; f < U1U1_NPOS; ++f) all += sm.pos[bc][f][a];
+        if (!isfinite(all)) {
+          int nan = 0;
+#pragma unroll
+          for (int f = 0; f < U1U1_NPOS; ++f) nan += isnan(sm.pos[bc][f][a]) ? 1 : 0;
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            nan += isnan(pr[s]) + isnan(pim[s]) + isnan(E[s][0]) + isnan(E[s][1]) + isnan(E[s][2]);
+          }
+          cnt[C_NAN] += nan;
         }
-        cnt[C_NAN] += nan;
 
         if (GAUSS) {
 #pragma unroll
@@ -502,6 +513,13 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
 #pragma unroll
     for (int k = 0; k < NSUM; ++k)
       ta.s[k] = ((tid & 31) == 0) ? (double)sm.wsum[tid >> 5][k] - (double)sm.wcmp[tid >> 5][k] : 0.0;
+    // |phi| from the extremes of |phi|^2 (-inf: no site of this block)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int kn = s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q, kx = s == 0 ? M_PHIMAX_P : M_PHIMAX_Q;
+      if (mx[kn] != -INFINITY) mx[kn] = -sqrt(-mx[kn]);
+      if (mx[kx] != -INFINITY) mx[kx] = sqrt(mx[kx]);
+    }
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) ta.mx[k] = (double)mx[k];
 #pragma unroll

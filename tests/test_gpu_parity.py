@@ -177,6 +177,38 @@ def test_cell_arrays_any_alignment():
         assert ref["n_pq_cell"] == ores["n_pq_cell"]
 
 
+@pytest.mark.parametrize("tol", [1, 0])
+def test_overlap_rows_of_1024(tol):
+    """Rows of 1024 cells take the warp-per-row overlap pass (x neighbours
+    by shuffle, periodic across the row's ends).  On a 1024 x 10 x 6 box of a
+    rough state its counts equal a brute-force overlap of the same cell
+    arrays (27-cell neighbourhood for tol 1, the cell itself for tol 0), in
+    both anchorings; the windings match the oracle on unflagged plaquettes
+    and the overlap count is within the reach of the flagged ones."""
+    p = U.Params(nx=1024, ny=10, nz=6, m=0.0, precision=U.FP64)
+    lat = U.Lattice(p)
+    lat.set_state(synth.random_state(p.shape, seed=21, a_amp=1.5))
+    res, ores, nflag = _windings_compare(p, lat) if tol == 1 else (None, None, None)
+    res = lat.detect_strings(tol=tol, cells=True)
+    cells = res["cells"].cpu().numpy()
+    P, Q = cells[0] > 0, cells[1] > 0
+
+    def dilate(m):
+        out = np.zeros_like(m)
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    out |= np.roll(m, (dz, dy, dx), axis=(0, 1, 2))
+        return out
+
+    dq, dp = (dilate(Q), dilate(P)) if tol == 1 else (Q, P)
+    assert res["n_pq_cell"] == int((P & dq).sum())
+    assert res["n_pq_cell_q"] == int((Q & dp).sum())
+    assert res["n_pq_cell"] > 1000
+    if tol == 1:
+        assert abs(res["n_pq_cell"] - ores["n_pq_cell"]) <= 2 * 27 * nflag
+
+
 def test_higher_winding_census():
     """Crossing strings: the cells shared by two strings read 4 and are
     counted as the oracle counts them."""
