@@ -262,7 +262,8 @@ int u1u1_set_overlap_tol(u1u1_lattice* h, int tol);
  * alignment, 16-byte aligned arrays take the vectorised pass),
  * windings (int8, 6 arrays of nx*ny*nz: sector-major, plane (x,y), (x,z),
  * (y,z), the plaquette anchored at each site).  *out is filled on the host
- * (synchronises `stream`).  Errors: INVALID_ARG, CUDA. */
+ * (synchronises `stream`).  Errors: INVALID_ARG, CUDA, TIMEOUT (a tiled
+ * kernel's bounded wait for its shared-memory tensor copies ran out). */
 int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
                         int8_t* windings, u1u1_strings* out, void* stream);
 
@@ -283,13 +284,16 @@ int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells, int32_t* l
 
 /* All diagnostics of Sec. III.A on the current state, including the Gauss
  * law residual per sector at n-1/2 (Eqs. 9-10), without stepping.  Fills
- * *out on the host (synchronises `stream`).  Errors: CUDA. */
+ * *out on the host (synchronises `stream`).  Errors: CUDA, TIMEOUT (as for
+ * u1u1_detect_strings). */
 int u1u1_diagnostics(u1u1_lattice* h, u1u1_diag* out, void* stream);
 
 /* Copy up to max records of fused detection steps not read yet, oldest
  * first, into s_out[] and d_out[] (either may be NULL); *count receives the
  * number copied and *lost (may be NULL) the number overwritten in the
- * device ring (capacity 1024) before they were read.  Synchronises `stream`. */
+ * device ring (capacity 1024) before they were read.  Synchronises `stream`.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT (a step kernel's bounded wait for its
+ * shared-memory tensor copies ran out since the last check). */
 int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag* d_out, int max, int* count,
                       int64_t* lost, void* stream);
 

@@ -15,7 +15,9 @@
 // current one (z-direction backward terms) are carried in registers, so each
 // position value is read from HBM once per step and each link phase is
 // evaluated once.
+#include <cuda.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "reduce.cuh"
 #include "site_math.cuh"
@@ -43,12 +45,73 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// ---- tensor-memory-access (TMA) copies of the position ring ----------------
+// The tensor maps of the ten position fields of the step's input buffer
+// (box: one ring slot of one field, TX + 2 VEC columns x TY + 2 rows x one
+// plane); `enabled` is 0 when they could not be made (FP64, lattices without
+// an interior tile, no driver entry point).  Passed as a __grid_constant__
+// kernel parameter.
+struct TmaPlan {
+  CUtensorMap map[U1U1_NPOS];
+  int enabled;
+};
+
+// set when a wait for a tensor copy ran out (2 s); read by the host
+__device__ int g_tma_timeout = 0;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of m to complete, for at most 2 s; past that the
+// global flag is set and the caller carries on (every thread still reaches
+// every barrier, and the host reports the timeout).
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* m, unsigned parity) {
+  if (mbar_try_wait(m, parity)) return;
+  const long long t0 = gtimer_ns();
+  while (!mbar_try_wait(m, parity)) {
+    if (gtimer_ns() - t0 > 2000000000LL) {
+      atomicExch(&g_tma_timeout, 1);
+      return;
+    }
+  }
+}
+// tensor copy of the box at (x, y, z) of `map` into shared memory at dst,
+// completing on m
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(m))
+      : "memory");
+}
+
 template <typename T, int TX, int TY>
 struct Tile {
   static constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte chunk
   static constexpr int RS = TX + 2 * VEC;     // smem row stride (elements)
   static constexpr int ROWS = TY + 2;         // rows ly = -1 .. TY
   static constexpr int PLANE = ROWS * RS;     // one field, one plane
+  // field stride of the position ring: a plane rounded up to 128 bytes, the
+  // alignment of a tensor-copy destination
+  static constexpr int PSTRIDE = (PLANE * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
   static constexpr int OFF = VEC;             // column of lx = 0
   static constexpr int NT = TX * TY;
   static constexpr int CH = TX / VEC;         // interior chunks per row
@@ -76,7 +139,7 @@ template <typename T, int TX, int TY, bool MEAS = true, bool GAUSS = true>
 struct Smem {
   using TL = Tile<T, TX, TY>;
   static constexpr int PG = GAUSS ? TL::PLANE : 1;
-  T pos[3][U1U1_NPOS][TL::PLANE];      // position ring
+  T pos[3][U1U1_NPOS][TL::PSTRIDE];    // position ring
   T P[2][2][2][TL::PLANE];             // [sector][dir 0,1][re,im] conj(U_i) phi
   T Ft[2][3][TL::PLANE];               // [sector][plane] dx F at this plane
   T Eg[2][2][PG];                      // [sector][dir 0,1] E for the Gauss divergence
@@ -93,6 +156,8 @@ struct Smem {
   // detection step and 4 ms per diagnostics pass at 1024^3.
   static constexpr bool ACC = MEAS && sizeof(T) == 4;
   static constexpr int NACC = acc_slot(NSUM, GAUSS);
+  // completion of the tensor copies into each ring slot (interior tiles)
+  unsigned long long mbar[3];
 };
 
 // Planes a thread sums in plain FP32 before its partials join the warp's
@@ -127,7 +192,7 @@ struct CopyPlan {
         const int gy = wrapm(y0 + r - 1, v.ny);
         const int gx = wrapm(x0 + (c - 1) * TL::VEC, v.nx);
         g[k] = v.pin[f] + (long long)gy * v.nx + gx;
-        s[k] = f * TL::PLANE + r * TL::RS + c * TL::VEC;
+        s[k] = f * TL::PSTRIDE + r * TL::RS + c * TL::VEC;
       }
     }
   }
@@ -159,7 +224,8 @@ __device__ __forceinline__ T ld_mom(const T* p) {
 // pass; `bid` indexes the block partial of a measuring pass.
 template <typename T, int TX, int TY, int MODE, bool COHERENT>
 __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeView<T>& v, const Coef<T>& c,
-                                         const MeasureOut& mo, int bx, int by, int z0, int z1, int bid) {
+                                         const MeasureOut& mo, int bx, int by, int z0, int z1, int bid,
+                                         const TmaPlan* tma) {
   using TL = Tile<T, TX, TY>;
   constexpr bool WRITE = (MODE & MODE_WRITE) != 0;
   constexpr bool MEAS = (MODE & MODE_MEASURE) != 0;
@@ -193,16 +259,48 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   }
 
   // ---- prologue: planes z0-1, z0, z0+1 in flight; backward-z carries ----
+  // Interior tiles (the halo inside the lattice) load their ring slots with
+  // one tensor copy per field, issued by thread 0 and completing on the
+  // slot's mbarrier; tiles at the lattice's edges, whose halo wraps around,
+  // use the cp.async plan.  So does the Gauss-residual variant: with tensor
+  // copies it ran 15% slower (the other variants gain or break even).
+  const bool use_tma = !GAUSS && tma != nullptr && tma->enabled && x0 >= TL::VEC && x0 + TX + TL::VEC <= v.nx &&
+                       y0 >= 1 && y0 + TY + 1 <= v.ny;
+  constexpr unsigned SLOT_BYTES = U1U1_NPOS * TL::ROWS * TL::RS * sizeof(T);
+  unsigned phase = 0u;  // bit k: parity of slot k's next completion
   CopyPlan<T, TX, TY> cpl;
-  cpl.init(v, x0, y0);
   auto zoff = [&](int z) { return (long long)wrapm(z, v.nz) * plane; };
-  cpl.issue(&sm.pos[0][0][0], zoff(z0 - 1));
-  cp_async_commit();
-  cpl.issue(&sm.pos[1][0][0], zoff(z0));
-  cp_async_commit();
-  cpl.issue(&sm.pos[2][0][0], zoff(z0 + 1));
-  cp_async_commit();
-  cp_async_wait1();
+  auto tma_issue = [&](int slot, int z) {  // thread 0 only
+    mbar_expect_tx(&sm.mbar[slot], SLOT_BYTES);
+#pragma unroll
+    for (int f = 0; f < U1U1_NPOS; ++f)
+      tma_load_3d(&sm.pos[slot][f][0], &tma->map[f], x0 - TL::VEC, y0 - 1, wrapm(z, v.nz), &sm.mbar[slot]);
+  };
+  auto tma_wait = [&](int slot) {
+    mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u);
+    phase ^= 1u << slot;
+  };
+  if (use_tma) {
+    if (tid == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) mbar_init(&sm.mbar[k]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tma_issue(k, z0 - 1 + k);
+    }
+    __syncthreads();  // the barriers are initialised before anyone waits
+    tma_wait(0);
+    tma_wait(1);
+  } else {
+    cpl.init(v, x0, y0);
+    cpl.issue(&sm.pos[0][0][0], zoff(z0 - 1));
+    cp_async_commit();
+    cpl.issue(&sm.pos[1][0][0], zoff(z0));
+    cp_async_commit();
+    cpl.issue(&sm.pos[2][0][0], zoff(z0 + 1));
+    cp_async_commit();
+    cp_async_wait1();
+  }
   __syncthreads();
 
   // carries: conj(U_2) phi, dx F_02, dx F_12 at (x, z-1), and E_2(x, z-1)
@@ -243,14 +341,24 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   for (int z = z0; z < z1; ++z) {
     const int it = z - z0;
     const int bc = (it + 1) % 3, bn = (it + 2) % 3, bf = it % 3;
-    // plane z+1 (the only copy group in flight) has landed; after the barrier
+    // plane z+1 (the only copy in flight) has landed; after the barrier
     // every thread is done with iteration z-1, so buffer bf (plane z-1) and
     // the per-plane shared arrays may be overwritten
-    cp_async_wait0();
+    if (use_tma) tma_wait(bn);
+    else cp_async_wait0();
     __syncthreads();
     if (z + 2 <= z1) {
-      cpl.issue(&sm.pos[bf][0][0], zoff(z + 2));
-      cp_async_commit();
+      if (use_tma) {
+        if (tid == 0) {
+          // the slot's last reads were generic loads: order them before the
+          // tensor copy's writes
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          tma_issue(bf, z + 2);
+        }
+      } else {
+        cpl.issue(&sm.pos[bf][0][0], zoff(z + 2));
+        cp_async_commit();
+      }
     }
 
     const long long gsite = (long long)z * plane + (long long)gy * v.nx + gx;
@@ -532,12 +640,12 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
 
 template <typename T, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(TX* TY, sizeof(T) == 8 ? 1 : (MODE == MODE_WRITE ? 3 : 2))
-k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz, const __grid_constant__ TmaPlan tma) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int z0 = blockIdx.z * lz;
   const int z1 = min(z0 + lz, v.nz);
   const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  tile_run<T, TX, TY, MODE, false>(smem_raw, v, c, mo, blockIdx.x, blockIdx.y, z0, z1, bid);
+  tile_run<T, TX, TY, MODE, false>(smem_raw, v, c, mo, blockIdx.x, blockIdx.y, z0, z1, bid, &tma);
 }
 
 template <typename T>
@@ -575,6 +683,50 @@ Grid tiled_grid(int nx, int ny, int nz, int waves) {
   return g;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against the driver library); null when unavailable
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor maps of the step's input position fields for the FP32 tiled kernel:
+// a 3D view (x, y, z) of each field, box = one ring slot of one field.  The
+// plan stays disabled (every tile then uses cp.async) for FP64, for
+// lattices too small to have an interior tile, and when encoding fails.
+template <typename T>
+void make_tma_plan(const LatticeView<T>& v, TmaPlan* tp) {
+  memset(tp, 0, sizeof(*tp));
+  if (sizeof(T) != 4) return;
+  using TL = Tile<T, TileShape<T>::TX, TileShape<T>::TY>;
+  if (v.nx < TileShape<T>::TX + 2 * TL::VEC || v.ny < TileShape<T>::TY + 2) return;
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return;
+  const cuuint64_t dims[3] = {(cuuint64_t)v.nx, (cuuint64_t)v.ny, (cuuint64_t)v.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)v.nx * sizeof(T), (cuuint64_t)v.nx * v.ny * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)TL::RS, (cuuint32_t)TL::ROWS, 1u};
+  const cuuint32_t estride[3] = {1u, 1u, 1u};
+  for (int f = 0; f < U1U1_NPOS; ++f) {
+    if (enc(&tp->map[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<T*>(v.pin[f]), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return;
+  }
+  tp->enabled = 1;
+}
+
 template <typename T, int MODE>
 cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo, cudaStream_t st,
                         int waves) {
@@ -590,15 +742,39 @@ cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const Measure
   if (dev < 0 || dev >= 64 || !configured[dev]) {
     e = cudaFuncSetAttribute(k_tiled<T, TX, TY, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
+    // three plain-step CTAs of about 72 KB per SM need the largest
+    // shared-memory carveout; the two-CTA measuring variants keep the
+    // driver's choice (more L1 for their cached loads: forcing it made the
+    // diagnostics pass 15% slower)
+    if (MODE == MODE_WRITE) {
+      e = cudaFuncSetAttribute(k_tiled<T, TX, TY, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+    }
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   Grid g = tiled_grid<T>(v.nx, v.ny, v.nz, waves);
   dim3 grid(g.gx, g.gy, g.gz);
-  k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz);
+  TmaPlan tp;
+  make_tma_plan<T>(v, &tp);
+  k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz, tp);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+int tma_timeout_flag(bool clear) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tma_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v && clear) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_tma_timeout, &z, sizeof(int));
+  }
+  return v;
+}
 
 int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves) {
   Grid g = sizeof_t == 8 ? tiled_grid<double>(nx, ny, nz, waves) : tiled_grid<float>(nx, ny, nz, waves);
@@ -649,7 +825,7 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
   v.ny = B.ny;
   v.nz = B.nz;
   MeasureOut mo{nullptr, nullptr, nullptr};
-  tile_run<T, TX, TY, MODE_WRITE, COHERENT>(smem, v, c, mo, bx, by, z0, z1, 0);
+  tile_run<T, TX, TY, MODE_WRITE, COHERENT>(smem, v, c, mo, bx, by, z0, z1, 0, nullptr);
 }
 
 // Persistent ensemble kernel: CTAs take work items (step k, box, tile) in
@@ -662,7 +838,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
                  EnsSched sc, unsigned long long* ticket, unsigned* done, int* err, long long limit_ns, int inject) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   __shared__ long long s_t;
   __shared__ int s_box, s_k, s_go;
@@ -720,7 +896,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
            EnsSched sc, int k) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   const long long r = blockIdx.x;
   const int si = upper_index(sc.box_prefix, sc.nboxes + 1, r);

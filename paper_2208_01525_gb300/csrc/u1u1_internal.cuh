@@ -122,6 +122,10 @@ cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, c
 // A measuring launch (MODE_MEASURE) with mo.faces set also runs the windings
 // kernel on v.pin, whose block partials follow the step kernel's.
 constexpr int TILE_WAVES_DEFAULT = 32;
+// Nonzero when a tiled kernel's wait for a tensor copy into shared memory ran
+// out of time (the kernel then finished on stale data); `clear` resets it.
+// Reading it synchronises the device.
+int tma_timeout_flag(bool clear);
 int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves = TILE_WAVES_DEFAULT);
 // block partials a tiled measuring launch writes (with or without windings)
 int tiled_measure_blocks(int nx, int ny, int nz, int sizeof_t, int waves, bool windings);
