@@ -378,7 +378,8 @@ int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int mode, int use_grap
 int u1u1_ensemble_lattice(u1u1_ensemble* e, int box, u1u1_lattice** h);
 
 /* Device status word of the last persistent run: U1U1_OK or
- * U1U1_ERR_TIMEOUT.  Synchronises `stream`. */
+ * U1U1_ERR_TIMEOUT (a wait for another work item, or for a tensor copy into
+ * shared memory, ran out of time).  Synchronises `stream`. */
 int u1u1_ensemble_status(u1u1_ensemble* e, int* status, void* stream);
 
 /* Wait limit of the persistent kernel's per-item dependency wait, in

@@ -48,6 +48,7 @@ struct u1u1_ensemble {
   int horizon = 0;
   std::vector<u1u1_lattice*> boxes;
   void* d_boxes = nullptr;  // EnsBox<T>[nboxes]
+  TmaPlan* d_tma = nullptr;  // tensor maps, two position buffers per box
   EnsDyn* d_dyn = nullptr;
   void* d_coef = nullptr;   // Coef<T>[nboxes * horizon]
   unsigned long long* d_ticket = nullptr;
@@ -84,6 +85,16 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
     B.ntiles = e->ntiles[b];
     B.coef0 = (long long)b * e->horizon;
   }
+  // tensor maps of each box's two position buffers (FP32; disabled plans
+  // otherwise), read by the kernels from device memory
+  std::vector<TmaPlan> hp((size_t)2 * nb);
+  for (int b = 0; b < nb; ++b)
+    for (int k = 0; k < 2; ++k) make_tma_plan<T>(hb[b].pos[k], hb[b].nx, hb[b].ny, hb[b].nz, &hp[2 * b + k]);
+  if (!e->d_tma) U1U1_CUDA_TRY(cudaMalloc((void**)&e->d_tma, sizeof(TmaPlan) * hp.size()), "ensemble tensor maps");
+  U1U1_CUDA_TRY(cudaMemcpy(e->d_tma, hp.data(), sizeof(TmaPlan) * hp.size(), cudaMemcpyHostToDevice),
+                "tensor map copy");
+  for (int b = 0; b < nb; ++b)
+    for (int k = 0; k < 2; ++k) hb[b].tma[k] = e->d_tma + 2 * b + k;
   if (!e->d_boxes) U1U1_CUDA_TRY(cudaMalloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_boxes, hb.data(), sizeof(EnsBox<T>) * nb, cudaMemcpyHostToDevice), "box table copy");
   if (e->d_coef) return U1U1_OK;  // a re-tiling keeps the coefficient table
@@ -204,6 +215,7 @@ extern "C" void u1u1_ensemble_destroy(u1u1_ensemble* e) {
   e->schedules.clear();
   for (u1u1_lattice* h : e->boxes) u1u1_destroy(h);
   cudaFree(e->d_boxes);
+  cudaFree(e->d_tma);
   cudaFree(e->d_dyn);
   cudaFree(e->d_coef);
   cudaFree(e->d_ticket);
@@ -331,6 +343,8 @@ extern "C" int u1u1_ensemble_status(u1u1_ensemble* e, int* status, void* stream)
   int v = 0;
   U1U1_CUDA_TRY(cudaMemcpyAsync(&v, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status");
   U1U1_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+  // a wait for a tensor copy that ran out counts as a timeout too
+  if (v == 0 && tma_timeout_flag(true)) v = U1U1_ERR_TIMEOUT;
   *status = v;
   if (v != 0) e->poisoned = 1;
   return U1U1_OK;

@@ -46,16 +46,6 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // ---- tensor-memory-access (TMA) copies of the position ring ----------------
-// The tensor maps of the ten position fields of the step's input buffer
-// (box: one ring slot of one field, TX + 2 VEC columns x TY + 2 rows x one
-// plane); `enabled` is 0 when they could not be made (FP64, lattices without
-// an interior tile, no driver entry point).  Passed as a __grid_constant__
-// kernel parameter.
-struct TmaPlan {
-  CUtensorMap map[U1U1_NPOS];
-  int enabled;
-};
-
 // set when a wait for a tensor copy ran out (2 s); read by the host
 __device__ int g_tma_timeout = 0;
 
@@ -264,8 +254,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   // slot's mbarrier; tiles at the lattice's edges, whose halo wraps around,
   // use the cp.async plan.  So does the Gauss-residual variant: with tensor
   // copies it ran 15% slower (the other variants gain or break even).
-  const bool use_tma = !GAUSS && tma != nullptr && tma->enabled && x0 >= TL::VEC && x0 + TX + TL::VEC <= v.nx &&
-                       y0 >= 1 && y0 + TY + 1 <= v.ny;
+  const bool use_tma = !GAUSS && x0 >= TL::VEC && x0 + TX + TL::VEC <= v.nx && y0 >= 1 && y0 + TY + 1 <= v.ny &&
+                       tma != nullptr && tma->enabled;
   constexpr unsigned SLOT_BYTES = U1U1_NPOS * TL::ROWS * TL::RS * sizeof(T);
   unsigned phase = 0u;  // bit k: parity of slot k's next completion
   CopyPlan<T, TX, TY> cpl;
@@ -282,6 +272,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   };
   if (use_tma) {
     if (tid == 0) {
+      // order any earlier generic accesses to the ring before the copies
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 #pragma unroll
       for (int k = 0; k < 3; ++k) mbar_init(&sm.mbar[k]);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -707,19 +699,19 @@ EncodeTiledFn encode_tiled() {
 // plan stays disabled (every tile then uses cp.async) for FP64, for
 // lattices too small to have an interior tile, and when encoding fails.
 template <typename T>
-void make_tma_plan(const LatticeView<T>& v, TmaPlan* tp) {
+void make_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* tp) {
   memset(tp, 0, sizeof(*tp));
   if (sizeof(T) != 4) return;
   using TL = Tile<T, TileShape<T>::TX, TileShape<T>::TY>;
-  if (v.nx < TileShape<T>::TX + 2 * TL::VEC || v.ny < TileShape<T>::TY + 2) return;
+  if (nx < TileShape<T>::TX + 2 * TL::VEC || ny < TileShape<T>::TY + 2) return;
   const EncodeTiledFn enc = encode_tiled();
   if (!enc) return;
-  const cuuint64_t dims[3] = {(cuuint64_t)v.nx, (cuuint64_t)v.ny, (cuuint64_t)v.nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)v.nx * sizeof(T), (cuuint64_t)v.nx * v.ny * sizeof(T)};
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T)};
   const cuuint32_t box[3] = {(cuuint32_t)TL::RS, (cuuint32_t)TL::ROWS, 1u};
   const cuuint32_t estride[3] = {1u, 1u, 1u};
   for (int f = 0; f < U1U1_NPOS; ++f) {
-    if (enc(&tp->map[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<T*>(v.pin[f]), dims, strides, box, estride,
+    if (enc(&tp->map[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<T*>(pin[f]), dims, strides, box, estride,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return;
@@ -756,12 +748,19 @@ cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const Measure
   Grid g = tiled_grid<T>(v.nx, v.ny, v.nz, waves);
   dim3 grid(g.gx, g.gy, g.gz);
   TmaPlan tp;
-  make_tma_plan<T>(v, &tp);
+  make_plan<T>(v.pin, v.nx, v.ny, v.nz, &tp);
   k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz, tp);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+template <typename T>
+void make_tma_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* tp) {
+  make_plan<T>(pin, nx, ny, nz, tp);
+}
+template void make_tma_plan<float>(const float* const*, int, int, int, TmaPlan*);
+template void make_tma_plan<double>(const double* const*, int, int, int, TmaPlan*);
 
 int tma_timeout_flag(bool clear) {
   int v = 0;
@@ -825,7 +824,10 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
   v.ny = B.ny;
   v.nz = B.nz;
   MeasureOut mo{nullptr, nullptr, nullptr};
-  tile_run<T, TX, TY, MODE_WRITE, COHERENT>(smem, v, c, mo, bx, by, z0, z1, 0, nullptr);
+  // tensor copies in the per-step kernel only: in the persistent kernel,
+  // which runs many small work items per CTA, they made the 64^3 class 8%
+  // slower (30.8 against 33.4 G site-updates/s) and gained nothing overall
+  tile_run<T, TX, TY, MODE_WRITE, COHERENT>(smem, v, c, mo, bx, by, z0, z1, 0, COHERENT ? nullptr : B.tma[cur]);
 }
 
 // Persistent ensemble kernel: CTAs take work items (step k, box, tile) in

@@ -2,6 +2,7 @@
 // libu1u1.  Nothing here is part of the public interface (include/u1u1.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,6 +80,18 @@ struct Coef {
   T qG[2];          // 2 e^2 c~_{n-1}, Gauss charge factor
 };
 
+// Tensor maps of the ten position fields of one position buffer for the
+// FP32 tiled kernels' tensor copies (box: one ring slot of one field); kept
+// in a kernel parameter or, for ensembles, in device memory.  `enabled` is 0
+// when they could not be made (FP64, lattices without an interior tile, no
+// driver entry point); the kernels then fill every ring slot by cp.async.
+struct TmaPlan {
+  CUtensorMap map[U1U1_NPOS];
+  int enabled;
+};
+template <typename T>
+void make_tma_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* tp);
+
 // Raw field pointers of one lattice (positions double-buffered).
 template <typename T>
 struct LatticeView {
@@ -150,6 +163,7 @@ struct EnsBox {
   int nx, ny, nz;
   int gx, gy, lz, gz, ntiles;  // tile grid of this box
   long long coef0;             // first row of this box in the coefficient table
+  const TmaPlan* tma[2];       // tensor maps of each position buffer (device memory)
 };
 struct EnsDyn {                // device-side step index and current buffer
   long long n;

@@ -126,3 +126,27 @@ def test_ensemble_autotune_keeps_states():
     ens.run([4] * 6, mode=choice["mode"])
     for b, p in enumerate(ps):
         assert torch.equal(ens.boxes[b].state(), alone(p, 6)), b
+
+
+@pytest.mark.parametrize("mode,graph", [(U.ENS_PERSISTENT, False), (U.ENS_PERSISTENT, True),
+                                        (U.ENS_PER_STEP, True), (U.ENS_UNBATCHED, False)])
+def test_ensemble_tensor_copy_boxes(mode, graph):
+    """FP32 boxes wide and tall enough to have interior tiles, whose ring
+    slots the per-step ensemble kernel fills by tensor copies from per-box
+    tensor maps in device memory (the persistent kernel uses cp.async), next
+    to a box without interior tiles: every box equals the same box stepped
+    alone, bit for bit, in every mode and over graph replays."""
+    shapes = [(104, 32, 20), (136, 40, 12), (16, 16, 16)]
+    ps = [U.Params(nx=nx, ny=ny, nz=nz, m=0.5, beta=1.0, eta0=1.0, eta_ref=3.0, seed=2000 + b, precision=U.FP32)
+          for b, (nx, ny, nz) in enumerate(shapes)]
+    steps = [6, 9, 4]
+    reps = 2 if graph else 1
+    ens = U.Ensemble(ps)
+    for _ in range(reps):
+        ens.run(steps, mode=mode, use_graph=graph)
+    torch.cuda.synchronize()
+    assert ens.status() == 0
+    for b, p in enumerate(ps):
+        assert ens.boxes[b].n == reps * steps[b]
+        assert torch.equal(ens.boxes[b].state(), alone(p, reps * steps[b])), b
+    ens.close()
