@@ -343,6 +343,17 @@ int u1u1_get_kernel(const u1u1_lattice* h, int* kernel);
  * a caller reproduce a tuned choice without timing. */
 int u1u1_set_tile_waves(u1u1_lattice* h, int waves);
 
+/* Failure-detection test hook for the single-lattice tiled kernels' bounded
+ * waits on their tensor copies into shared memory (process-wide; launches
+ * enqueued afterwards see it).
+ * enable = 1 makes every ring slot expect 16 bytes more than its copies
+ * deliver, so every such wait runs out after limit_ns (the kernel finishes
+ * on the delivered data and the next synchronising call returns TIMEOUT);
+ * enable = 0 restores normal copies.  limit_ns (>= 1000) is the wait limit
+ * from then on; the default is 2 s.  No GPU fault or hang is involved.
+ * Errors: INVALID_ARG. */
+int u1u1_inject_copy_timeout(int enable, int64_t limit_ns);
+
 /* ---- ensembles of independent boxes ---------------------------------------- */
 
 /* How u1u1_ensemble_run schedules the boxes' steps. */

@@ -343,6 +343,12 @@ extern "C" int u1u1_set_tile_waves(u1u1_lattice* h, int waves) {
   return U1U1_OK;
 }
 
+extern "C" int u1u1_inject_copy_timeout(int enable, int64_t limit_ns) {
+  if (limit_ns < 1000) return fail(U1U1_ERR_INVALID_ARG, "wait limit must be >= 1000 ns");
+  tma_inject_timeout(enable, (long long)limit_ns);
+  return U1U1_OK;
+}
+
 extern "C" int u1u1_get_kernel(const u1u1_lattice* h, int* kernel) {
   if (!h || !kernel) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
   *kernel = h->kernel;

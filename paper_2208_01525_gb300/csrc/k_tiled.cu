@@ -46,7 +46,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // ---- tensor-memory-access (TMA) copies of the position ring ----------------
-// set when a wait for a tensor copy ran out (2 s); read by the host
+// set when a wait for a tensor copy ran out; read by the host
 __device__ int g_tma_timeout = 0;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -70,19 +70,29 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned pa
       : "memory");
   return ok != 0;
 }
-// Wait for phase `parity` of m to complete, for at most 2 s; past that the
-// global flag is set and the caller carries on (every thread still reaches
-// every barrier, and the host reports the timeout).
-__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* m, unsigned parity) {
-  if (mbar_try_wait(m, parity)) return;
+// Wait for phase `parity` of m to complete, for at most `limit` ns (2 s);
+// true when it did.  Past the limit the global flag is set for the host and
+// the CTA's flag is set, after which the CTA's later waits give up at once
+// (they still return, so every thread reaches every barrier) and the
+// thread that issues the copies issues no more (re-arming a slot whose phase
+// never completed would be an arrival too many); the CTA finishes on stale
+// data.  A timed-out wait has given the slot's copies the whole limit to
+// land before the CTA can exit.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity, volatile int* cta_fail,
+                                                  long long limit) {
+  if (mbar_try_wait(m, parity)) return true;
+  if (*cta_fail) return false;
   const long long t0 = gtimer_ns();
   while (!mbar_try_wait(m, parity)) {
-    if (gtimer_ns() - t0 > 2000000000LL) {
+    if (gtimer_ns() - t0 > limit) {
       atomicExch(&g_tma_timeout, 1);
-      return;
+      *cta_fail = 1;
+      return false;
     }
   }
+  return true;
 }
+
 // tensor copy of the box at (x, y, z) of `map` into shared memory at dst,
 // completing on m
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
@@ -146,8 +156,10 @@ struct Smem {
   // detection step and 4 ms per diagnostics pass at 1024^3.
   static constexpr bool ACC = MEAS && sizeof(T) == 4;
   static constexpr int NACC = acc_slot(NSUM, GAUSS);
-  // completion of the tensor copies into each ring slot (interior tiles)
+  // completion of the tensor copies into each ring slot (interior tiles),
+  // and whether a wait for them gave up
   unsigned long long mbar[3];
+  int tma_fail;
 };
 
 // Planes a thread sums in plain FP32 before its partials join the warp's
@@ -261,19 +273,21 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   CopyPlan<T, TX, TY> cpl;
   auto zoff = [&](int z) { return (long long)wrapm(z, v.nz) * plane; };
   auto tma_issue = [&](int slot, int z) {  // thread 0 only
-    mbar_expect_tx(&sm.mbar[slot], SLOT_BYTES);
+    mbar_expect_tx(&sm.mbar[slot], SLOT_BYTES + tma->extra_bytes);
 #pragma unroll
     for (int f = 0; f < U1U1_NPOS; ++f)
       tma_load_3d(&sm.pos[slot][f][0], &tma->map[f], x0 - TL::VEC, y0 - 1, wrapm(z, v.nz), &sm.mbar[slot]);
   };
+  bool copies_ok = true;  // every wait of this thread completed
   auto tma_wait = [&](int slot) {
-    mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u);
+    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, tma->limit_ns) && copies_ok;
     phase ^= 1u << slot;
   };
   if (use_tma) {
     if (tid == 0) {
       // order any earlier generic accesses to the ring before the copies
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      sm.tma_fail = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) mbar_init(&sm.mbar[k]);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -341,7 +355,7 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
     __syncthreads();
     if (z + 2 <= z1) {
       if (use_tma) {
-        if (tid == 0) {
+        if (tid == 0 && copies_ok) {
           // the slot's last reads were generic loads: order them before the
           // tensor copy's writes
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -698,9 +712,16 @@ EncodeTiledFn encode_tiled() {
 // a 3D view (x, y, z) of each field, box = one ring slot of one field.  The
 // plan stays disabled (every tile then uses cp.async) for FP64, for
 // lattices too small to have an interior tile, and when encoding fails.
+// bytes each ring slot of the single-lattice kernels expects on top of what
+// its copies deliver (0, or 16 while the timeout test hook is on), and the
+// limit of a wait for them; both travel in the kernel parameter
+unsigned g_inject_extra_bytes = 0u;
+long long g_wait_limit_ns = 2000000000LL;
+
 template <typename T>
 void make_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* tp) {
   memset(tp, 0, sizeof(*tp));
+  tp->limit_ns = 2000000000LL;
   if (sizeof(T) != 4) return;
   using TL = Tile<T, TileShape<T>::TX, TileShape<T>::TY>;
   if (nx < TileShape<T>::TX + 2 * TL::VEC || ny < TileShape<T>::TY + 2) return;
@@ -749,6 +770,8 @@ cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const Measure
   dim3 grid(g.gx, g.gy, g.gz);
   TmaPlan tp;
   make_plan<T>(v.pin, v.nx, v.ny, v.nz, &tp);
+  tp.extra_bytes = g_inject_extra_bytes;
+  tp.limit_ns = g_wait_limit_ns;
   k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz, tp);
   return cudaGetLastError();
 }
@@ -761,6 +784,12 @@ void make_tma_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPla
 }
 template void make_tma_plan<float>(const float* const*, int, int, int, TmaPlan*);
 template void make_tma_plan<double>(const double* const*, int, int, int, TmaPlan*);
+
+int tma_inject_timeout(int enable, long long limit_ns) {
+  g_inject_extra_bytes = enable ? 16u : 0u;
+  g_wait_limit_ns = limit_ns;
+  return 0;
+}
 
 int tma_timeout_flag(bool clear) {
   int v = 0;

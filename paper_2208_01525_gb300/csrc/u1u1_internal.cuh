@@ -88,6 +88,8 @@ struct Coef {
 struct TmaPlan {
   CUtensorMap map[U1U1_NPOS];
   int enabled;
+  unsigned extra_bytes;  // failure-detection test hook: 0 in normal runs
+  long long limit_ns;    // limit of a wait for a slot's copies (2 s)
 };
 template <typename T>
 void make_tma_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* tp);
@@ -139,6 +141,10 @@ constexpr int TILE_WAVES_DEFAULT = 32;
 // out of time (the kernel then finished on stale data); `clear` resets it.
 // Reading it synchronises the device.
 int tma_timeout_flag(bool clear);
+// Test hook: make every tensor-copy wait of the single-lattice kernels run
+// out (enable) after limit_ns, or restore normal copies; the limit applies to
+// launches enqueued from then on either way.
+int tma_inject_timeout(int enable, long long limit_ns);
 int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves = TILE_WAVES_DEFAULT);
 // block partials a tiled measuring launch writes (with or without windings)
 int tiled_measure_blocks(int nx, int ny, int nz, int sizeof_t, int waves, bool windings);

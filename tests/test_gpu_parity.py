@@ -130,6 +130,33 @@ def test_fp32_tensor_copy_tiles_match_oracle():
     assert abs(d["energy"] - od["energy"]) <= 1e-4 * abs(od["energy"])
 
 
+def test_copy_wait_timeout_is_reported():
+    """The tiled kernels' waits for their tensor copies are bounded: with the
+    test hook making every slot expect more bytes than its copies deliver,
+    the waits run out after 50 ms, the step finishes, and the next
+    synchronising call reports TIMEOUT (once).  With the hook off, the same
+    box steps normally again and matches the oracle."""
+    p = U.Params(nx=136, ny=40, nz=24, m=0.5, beta=1.0, eta0=1.0, eta_ref=65.0, seed=12, precision=U.FP32)
+    lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+    U.check(U.lib().u1u1_inject_copy_timeout(1, 50_000_000))
+    try:
+        lat.step(2)
+        with pytest.raises(U.U1U1Error) as ei:
+            lat.read_records()
+        assert ei.value.code == -5 and "tensor copy" in str(ei.value)  # TIMEOUT
+    finally:
+        U.check(U.lib().u1u1_inject_copy_timeout(0, 2_000_000_000))
+    lat.read_records()  # reported once
+    lat.close()
+    lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+    lat.step(6)
+    assert lat.read_records()[1] == 0
+    ref = O.init(to_oracle(p))
+    O.step(to_oracle(p), ref, 0, 6)
+    err = field_maxrel(host_state(lat), ref)
+    assert err.max() <= 1e-5, err
+
+
 @pytest.mark.parametrize("prec", [U.FP32, U.FP64])
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_windings_bit_exact_on_snapshot(prec, kernel):
