@@ -224,7 +224,10 @@ __device__ __forceinline__ T ld_mom(const T* p) {
 
 // One tile column (tile (bx, by), planes [z0, z1)) of a step or measuring
 // pass; `bid` indexes the block partial of a measuring pass.
-template <typename T, int TX, int TY, int MODE, bool COHERENT>
+// HOOKS: the plan's test-hook fields are read (single-lattice kernels, whose
+// plan is a kernel parameter); ensemble kernels, whose plans live in device
+// memory, use the exact slot size and the 2 s limit instead.
+template <typename T, int TX, int TY, int MODE, bool COHERENT, bool HOOKS = true>
 __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeView<T>& v, const Coef<T>& c,
                                          const MeasureOut& mo, int bx, int by, int z0, int z1, int bid,
                                          const TmaPlan* tma) {
@@ -269,18 +272,20 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   const bool use_tma = !GAUSS && x0 >= TL::VEC && x0 + TX + TL::VEC <= v.nx && y0 >= 1 && y0 + TY + 1 <= v.ny &&
                        tma != nullptr && tma->enabled;
   constexpr unsigned SLOT_BYTES = U1U1_NPOS * TL::ROWS * TL::RS * sizeof(T);
+  const unsigned slot_expect = (HOOKS && use_tma) ? SLOT_BYTES + tma->extra_bytes : SLOT_BYTES;
+  const long long wait_limit = (HOOKS && use_tma) ? tma->limit_ns : 2000000000LL;
   unsigned phase = 0u;  // bit k: parity of slot k's next completion
   CopyPlan<T, TX, TY> cpl;
   auto zoff = [&](int z) { return (long long)wrapm(z, v.nz) * plane; };
   auto tma_issue = [&](int slot, int z) {  // thread 0 only
-    mbar_expect_tx(&sm.mbar[slot], SLOT_BYTES + tma->extra_bytes);
+    mbar_expect_tx(&sm.mbar[slot], slot_expect);
 #pragma unroll
     for (int f = 0; f < U1U1_NPOS; ++f)
       tma_load_3d(&sm.pos[slot][f][0], &tma->map[f], x0 - TL::VEC, y0 - 1, wrapm(z, v.nz), &sm.mbar[slot]);
   };
   bool copies_ok = true;  // every wait of this thread completed
   auto tma_wait = [&](int slot) {
-    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, tma->limit_ns) && copies_ok;
+    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, wait_limit) && copies_ok;
     phase ^= 1u << slot;
   };
   if (use_tma) {
@@ -856,7 +861,7 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
   // tensor copies in the per-step kernel only: in the persistent kernel,
   // which runs many small work items per CTA, they made the 64^3 class 8%
   // slower (30.8 against 33.4 G site-updates/s) and gained nothing overall
-  tile_run<T, TX, TY, MODE_WRITE, COHERENT>(smem, v, c, mo, bx, by, z0, z1, 0, COHERENT ? nullptr : B.tma[cur]);
+  tile_run<T, TX, TY, MODE_WRITE, COHERENT, false>(smem, v, c, mo, bx, by, z0, z1, 0, COHERENT ? nullptr : B.tma[cur]);
 }
 
 // Persistent ensemble kernel: CTAs take work items (step k, box, tile) in
