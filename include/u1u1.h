@@ -361,7 +361,7 @@ int u1u1_inject_copy_timeout(int enable, int64_t limit_ns);
 #define U1U1_ENS_PER_STEP 1   /* one launch per step covering all boxes still running */
 #define U1U1_ENS_UNBATCHED 2  /* one launch per box per step, box after box (reference loop) */
 
-/* Create an ensemble of nboxes independent lattices (SURVEY-style batched
+/* Create an ensemble of nboxes independent lattices (batched independent
  * realisations, e.g. uneven box sizes, eras, beta and seeds): per_box[b] and
  * buffers[b] are as for u1u1_init_lattice, every box gets its random-phase
  * initial conditions on `stream`, and all boxes share one precision.
