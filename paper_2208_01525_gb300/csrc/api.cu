@@ -604,8 +604,8 @@ static void to_diag(const u1u1_params* p, const RawRecord& r, u1u1_diag* d) {
 
 // After a synchronisation: a tiled kernel whose wait for a tensor copy into
 // shared memory ran out of time finished on stale data; report it once.
-static int check_tma_timeout() {
-  if (tma_timeout_flag(true))
+static int check_tma_timeout(cudaStream_t st) {
+  if (tma_timeout_flag(true, st))
     return fail(U1U1_ERR_TIMEOUT, "a tiled kernel's wait for a tensor copy into shared memory ran out (2 s); "
                                   "the fields written since may be wrong");
   return U1U1_OK;
@@ -616,7 +616,7 @@ static int read_scratch(u1u1_lattice* h, RawRecord* r, cudaStream_t st) {
                 "record copy");
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
   *r = h->host_rec[0];
-  return check_tma_timeout();
+  return check_tma_timeout(st);
 }
 
 extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
@@ -736,7 +736,7 @@ extern "C" int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag
     U1U1_CUDA_TRY(cudaMemcpyAsync(h->host_rec, h->ring, sizeof(RawRecord) * (take - run1),
                                   cudaMemcpyDeviceToHost, st), "record ring copy");
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
-  if (int rc = check_tma_timeout()) return rc;
+  if (int rc = check_tma_timeout(st)) return rc;
   for (int64_t k = 0; k < take; ++k) {
     const RawRecord& r = h->host_rec[(h->rec_read + k) % RING_CAP];
     if (s_out) to_strings(&h->p, r, &s_out[k]);

@@ -344,7 +344,7 @@ extern "C" int u1u1_ensemble_status(u1u1_ensemble* e, int* status, void* stream)
   U1U1_CUDA_TRY(cudaMemcpyAsync(&v, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status");
   U1U1_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
   // a wait for a tensor copy that ran out counts as a timeout too
-  if (v == 0 && tma_timeout_flag(true)) v = U1U1_ERR_TIMEOUT;
+  if (v == 0 && tma_timeout_flag(true, (cudaStream_t)stream)) v = U1U1_ERR_TIMEOUT;
   *status = v;
   if (v != 0) e->poisoned = 1;
   return U1U1_OK;

@@ -796,15 +796,21 @@ int tma_inject_timeout(int enable, long long limit_ns) {
   return 0;
 }
 
-int tma_timeout_flag(bool clear) {
+int tma_timeout_flag(bool clear, cudaStream_t st) {
+  // read (and clear) the flag in the order of stream st, so that no other
+  // stream is waited for; nothing is allocated (the allocation-free
+  // detection entry point calls this too)
   int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_tma_timeout, sizeof(int)) != cudaSuccess) {
+  if (cudaMemcpyFromSymbolAsync(&v, g_tma_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   if (v && clear) {
-    const int z = 0;
-    cudaMemcpyToSymbol(g_tma_timeout, &z, sizeof(int));
+    const int zero = 0;
+    if (cudaMemcpyToSymbolAsync(g_tma_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      cudaGetLastError();
   }
   return v;
 }

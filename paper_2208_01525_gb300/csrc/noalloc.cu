@@ -96,7 +96,7 @@ int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int
   RawRecord r;
   U1U1_CUDA_TRY(cudaMemcpyAsync(&r, rec, sizeof(RawRecord), cudaMemcpyDeviceToHost, st), "record copy");
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
-  if (tma_timeout_flag(true))
+  if (tma_timeout_flag(true, st))
     return fail(U1U1_ERR_TIMEOUT, "a tiled kernel's wait for a tensor copy into shared memory ran out (2 s)");
   to_strings(p, r, out);
   return U1U1_OK;

@@ -139,8 +139,8 @@ cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, c
 constexpr int TILE_WAVES_DEFAULT = 32;
 // Nonzero when a tiled kernel's wait for a tensor copy into shared memory ran
 // out of time (the kernel then finished on stale data); `clear` resets it.
-// Reading it synchronises the device.
-int tma_timeout_flag(bool clear);
+// Read in the order of stream `st`, which it synchronises.
+int tma_timeout_flag(bool clear, cudaStream_t st);
 // Test hook: make every tensor-copy wait of the single-lattice kernels run
 // out (enable) after limit_ns, or restore normal copies; the limit applies to
 // launches enqueued from then on either way.
