@@ -95,10 +95,10 @@ template <> __device__ __forceinline__ double cut_frac<double>() { return 0.4999
 // field at either end: then d and k are NaN and the test below fails; a
 // plaquette with such an edge gets W = 0).
 template <typename T>
-__device__ __forceinline__ T edge_k(T a_h, T a_t, T theta, bool* cut) {
+__device__ __forceinline__ T edge_k(T a_h, T a_t, T theta, unsigned* cut) {
   const T t = ((a_h - a_t) - theta) * Consts<T>::inv_two_pi();
   const T k = rint_t<T>(t);
-  *cut = !(fabs(t - k) <= cut_frac<T>());
+  *cut = (fabs(t - k) <= cut_frac<T>()) ? 0u : 1u;
   return k;
 }
 
@@ -174,7 +174,7 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
       // own edges 0 and 1 of this plane
       const T ax = __shfl_down_sync(0xffffffffu, al[s], 1);
       const T ay = sm.al[z % 3][s][ty];
-      bool c0, c1;
+      unsigned c0, c1;
       const T k0 = edge_k<T>(ax, al[s], dx * A[s][0], &c0);
       const T k1 = edge_k<T>(ay, al[s], dx * A[s][1], &c1);
 
@@ -185,7 +185,7 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
         const int W0 = round_int<T>(P01[s] + eb.k0[s][ty]);  // NaN (flagged) -> 0
         const int W1 = round_int<T>(P02[s] + k0);
         const int W2 = round_int<T>(P12[s] - eb.k2[s][ty] + k1);
-        const unsigned ckm = pc[s] | (cy & 1u) | (c0 ? 2u : 0u) | ((c1 || (cy & 4u)) ? 4u : 0u);
+        const unsigned ckm = pc[s] | (cy & 1u) | (c0 << 1) | ((c1 | (cy >> 2)) << 2);
         const int a0 = abs(W0), a1 = abs(W1), a2 = abs(W2);
         unsigned byte = (unsigned)min(a0, 3) | ((unsigned)min(a1, 3) << FACE_SHIFT(1)) |
                         ((unsigned)min(a2, 3) << FACE_SHIFT(2));
@@ -206,20 +206,20 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
       if (last) continue;
 
       // own edge 2; publish edges 0 and 2 for the row below
-      bool c2;
+      unsigned c2;
       const T k2 = edge_k<T>(aln[s], al[s], dx * A[s][2], &c2);
       ec.k0[s][t] = k0;
       ec.k2[s][t] = k2;
-      ec.cut[s][t] = (uint8_t)((c0 ? 1u : 0u) | (c2 ? 4u : 0u));
+      ec.cut[s][t] = (uint8_t)(c0 | (c2 << 2));
       // edges 1 and 2 of x + x by shuffle
-      const unsigned cb = (c1 ? 1u : 0u) | (c2 ? 2u : 0u);
+      const unsigned cb = c1 | (c2 << 1);
       const T k1x = __shfl_down_sync(0xffffffffu, k1, 1);
       const T k2x = __shfl_down_sync(0xffffffffu, k2, 1);
       const unsigned cx = __shfl_down_sync(0xffffffffu, cb, 1);
       P01[s] = -(k0 + k1x - k1);  // + k_0 of the row above
       P02[s] = -(k0 + k2x - k2);  // + k_0 of the plane above
       P12[s] = -(k1 - k2);        // - k_2 of the row above + k_1 of the plane above
-      pc[s] = ((c0 || (cx & 1u) || c1) ? 1u : 0u) | ((c0 || (cx & 2u) || c2) ? 2u : 0u) | ((c1 || c2) ? 4u : 0u);
+      pc[s] = (c0 | (cx & 1u) | c1) | ((c0 | (cx >> 1) | c2) << 1) | ((c1 | c2) << 2);
       al[s] = aln[s];
 #pragma unroll
       for (int i = 0; i < 3; ++i) A[s][i] = An[s][i];
