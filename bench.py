@@ -433,6 +433,9 @@ def run_ours(args):
                "d2h_bytes_per_step": state_bytes / args.steps + rec_bytes,
                "what": "upload state from pinned host, K periods each followed by a record read, "
                        "download state",
+               "transfer": ("SM copy kernel through the mapped host address"
+                            if all(U.host_span_mapped(t.data_ptr(), t.numel() * t.element_size()) for t in host)
+                            else "copy engines"),
                "upload_s": t1 - t0, "periods_s": t2 - t1, "download_s": t3 - t2}
         del host
 

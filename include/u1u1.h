@@ -299,11 +299,22 @@ int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag* d_out, in
 
 /* Copy the whole state between the handle's device buffers and 20 host
  * arrays (field order POS then MOM; each u1u1_field_bytes long; pinned
- * memory recommended).  Upload writes the current position buffer.  Both
- * are asynchronous on `stream`; the host arrays must stay valid until the
- * stream reaches them. */
+ * memory recommended).  Upload writes the current position buffer.  Arrays
+ * for which u1u1_host_span_mapped reports 1 are copied by one kernel on the
+ * SMs through their mapped device address (faster than the copy engines
+ * over the CPU-GPU link); the others by one copy-engine transfer each.
+ * Both calls are asynchronous on `stream`; the host arrays must stay valid
+ * until the stream reaches them.  Errors: INVALID_ARG (NULL handle, table
+ * or entry), CUDA. */
 int u1u1_upload_state(u1u1_lattice* h, const void* const host[U1U1_NFIELDS], void* stream);
 int u1u1_download_state(const u1u1_lattice* h, void* const host[U1U1_NFIELDS], void* stream);
+
+/* *mapped = 1 when the host span [host, host + bytes) is page-locked host
+ * memory mapped into the device's address space, 16-byte aligned, a whole
+ * number of 16-byte words long and inside one allocation, so that state
+ * transfers through it run on the SMs; 0 otherwise (copy engines).
+ * Synchronous, no device work.  Errors: INVALID_ARG (NULL pointer). */
+int u1u1_host_span_mapped(const void* host, size_t bytes, int* mapped);
 
 /* Checkpoint / resume: write or read the parameters, step index and all 20
  * fields to or from a file; resuming continues bit for bit.  Synchronous.

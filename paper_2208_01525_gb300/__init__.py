@@ -76,6 +76,14 @@ def coefficients(p: Params, n: int) -> dict:
     return dict(eta=out[0], a=out[1], c=out[2], delta=out[3], omega=out[4], ctilde=out[5])
 
 
+def host_span_mapped(ptr: int, nbytes: int) -> bool:
+    """Whether state transfers through the host span run on the SMs
+    (page-locked, mapped, 16-byte aligned, inside one allocation)."""
+    v = ctypes.c_int()
+    check(lib().u1u1_host_span_mapped(ctypes.c_void_p(ptr), int(nbytes), ctypes.byref(v)))
+    return bool(v.value)
+
+
 def check_params(p: Params) -> None:
     check(lib().u1u1_check_params(ctypes.byref(p.c())))
 
@@ -266,7 +274,8 @@ class Lattice:
 
     # -- host transfer and checkpoints --
     def upload(self, host_fields, stream=None):
-        """Enqueue host -> device copies of 20 host tensors (pinned recommended)."""
+        """Enqueue host -> device copies of 20 host tensors (pinned recommended:
+        pinned, 16-byte aligned tensors are copied by the SMs)."""
         arr = (ctypes.c_void_p * NFIELDS)(*[t.data_ptr() for t in host_fields])
         check(lib().u1u1_upload_state(self._h, arr, _stream_ptr(stream)))
 

@@ -120,6 +120,7 @@ PROTOTYPES = {
                                          _P(ctypes.c_int64), _vp]),
     "u1u1_upload_state": (ctypes.c_int, [_vp, _P(_vp), _vp]),
     "u1u1_download_state": (ctypes.c_int, [_vp, _P(_vp), _vp]),
+    "u1u1_host_span_mapped": (ctypes.c_int, [_vp, ctypes.c_size_t, _P(ctypes.c_int)]),
     "u1u1_save": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "u1u1_load": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp]),
     "u1u1_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),

@@ -1,7 +1,9 @@
 // C ABI of libu1u1 (include/u1u1.h): parameter handling, lattice handles,
 // the step loop, detection and diagnostics orchestration, record ring,
 // host epilogue of Sec. III.A (Eqs. 31-37) and checkpoint I/O.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -12,6 +14,7 @@
 
 #include "../../include/u1u1.h"
 #include "host_internal.h"
+#include "state_copy.cuh"
 #include "u1u1_internal.cuh"
 
 using namespace u1u1;
@@ -752,27 +755,98 @@ extern "C" int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag
 // state transfer and checkpoints
 // ---------------------------------------------------------------------------
 
-extern "C" int u1u1_upload_state(u1u1_lattice* h, const void* const host[U1U1_NFIELDS], void* stream) {
-  if (!h || !host) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
-  size_t bytes = h->V * h->esize;
-  cudaStream_t st = (cudaStream_t)stream;
+// Host spans that the SMs copy directly: page-locked host memory mapped into
+// the device's address space, 16-byte aligned, a whole number of 16-byte
+// words, and lying inside one allocation (so no access can leave it).  On
+// the GB300's CPU-GPU link such copies ran at 193 GB/s device to host and
+// 211 GB/s host to device over twenty 4 GiB buffers, against 91-136 and
+// 148-152 GB/s for the copy engines; every other host pointer (pageable
+// memory, odd offsets) goes through the copy engines.
+namespace {
+using PointerGetAttributeFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+
+PointerGetAttributeFn pointer_get_attribute() {
+  static const PointerGetAttributeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (PointerGetAttributeFn) nullptr;
+    }
+    return reinterpret_cast<PointerGetAttributeFn>(p);
+  }();
+  return fn;
+}
+
+bool mapped_host_span(const void* p, size_t bytes, void** dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer || bytes == 0) return false;
+  const uintptr_t d = (uintptr_t)at.devicePointer;
+  if ((d | (uintptr_t)bytes) & 15u) return false;
+  const PointerGetAttributeFn get = pointer_get_attribute();
+  if (!get) return false;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)d) != CUDA_SUCCESS ||
+      get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)d) != CUDA_SUCCESS)
+    return false;
+  if (d < (uintptr_t)start || d - (uintptr_t)start > size || bytes > size - (d - (uintptr_t)start)) return false;
+  *dev = at.devicePointer;
+  return true;
+}
+
+// fields whose host span qualifies go to one SM copy launch, the rest to
+// one copy-engine transfer each
+int transfer_state(const u1u1_lattice* h, void* const dev[U1U1_NFIELDS], const void* const host[U1U1_NFIELDS],
+                   bool upload, cudaStream_t st) {
+  const size_t bytes = h->V * h->esize;
+  XferTable t{};
   for (int f = 0; f < U1U1_NFIELDS; ++f) {
     if (!host[f]) return fail(U1U1_ERR_INVALID_ARG, "host[%d] is NULL", f);
-    void* dst = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
-    U1U1_CUDA_TRY(cudaMemcpyAsync(dst, host[f], bytes, cudaMemcpyHostToDevice, st), "state upload");
+    void* hd = nullptr;
+    if (mapped_host_span(host[f], bytes, &hd)) {
+      t.src[t.m] = upload ? hd : dev[f];
+      t.dst[t.m] = upload ? dev[f] : hd;
+      ++t.m;
+    } else if (upload) {
+      U1U1_CUDA_TRY(cudaMemcpyAsync(dev[f], host[f], bytes, cudaMemcpyHostToDevice, st), "state upload");
+    } else {
+      U1U1_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(host[f]), dev[f], bytes, cudaMemcpyDeviceToHost, st),
+                    "state download");
+    }
   }
+  U1U1_CUDA_TRY(launch_state_copy(t, (long long)(bytes / 16), st), upload ? "state upload" : "state download");
   return U1U1_OK;
+}
+
+void state_fields(const u1u1_lattice* h, void* dev[U1U1_NFIELDS]) {
+  for (int f = 0; f < U1U1_NFIELDS; ++f) dev[f] = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
+}
+}  // namespace
+
+extern "C" int u1u1_upload_state(u1u1_lattice* h, const void* const host[U1U1_NFIELDS], void* stream) {
+  if (!h || !host) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  void* dev[U1U1_NFIELDS];
+  state_fields(h, dev);
+  return transfer_state(h, dev, host, true, (cudaStream_t)stream);
 }
 
 extern "C" int u1u1_download_state(const u1u1_lattice* h, void* const host[U1U1_NFIELDS], void* stream) {
   if (!h || !host) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
-  size_t bytes = h->V * h->esize;
-  cudaStream_t st = (cudaStream_t)stream;
-  for (int f = 0; f < U1U1_NFIELDS; ++f) {
-    if (!host[f]) return fail(U1U1_ERR_INVALID_ARG, "host[%d] is NULL", f);
-    const void* src = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
-    U1U1_CUDA_TRY(cudaMemcpyAsync(host[f], src, bytes, cudaMemcpyDeviceToHost, st), "state download");
-  }
+  void* dev[U1U1_NFIELDS];
+  state_fields(h, dev);
+  return transfer_state(h, dev, host, false, (cudaStream_t)stream);
+}
+
+extern "C" int u1u1_host_span_mapped(const void* host, size_t bytes, int* mapped) {
+  if (!host || !mapped) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  void* dev = nullptr;
+  *mapped = mapped_host_span(host, bytes, &dev) ? 1 : 0;
   return U1U1_OK;
 }
 

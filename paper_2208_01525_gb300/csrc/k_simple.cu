@@ -10,6 +10,7 @@
 
 #include "reduce.cuh"
 #include "site_math.cuh"
+#include "state_copy.cuh"
 #include "u1u1_internal.cuh"
 
 namespace u1u1 {
@@ -287,7 +288,23 @@ __global__ void k_edge_phase(const float* __restrict__ re, const float* __restri
     out[i] = edge_phase<float>(re[i], im[i]);
 }
 
+// One launch moves every field of the table; 16-byte words, grid-stride.
+__global__ void __launch_bounds__(256) k_state_copy(const __grid_constant__ XferTable t, long long n16) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int f = 0; f < t.m; ++f) {
+    const uint4* __restrict__ src = static_cast<const uint4*>(t.src[f]);
+    uint4* __restrict__ dst = static_cast<uint4*>(t.dst[f]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_state_copy(const XferTable& t, long long n16, cudaStream_t st) {
+  if (t.m <= 0 || n16 <= 0) return cudaSuccess;
+  k_state_copy<<<152 * 8, 256, 0, st>>>(t, n16);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_edge_phase(const float* re, const float* im, float* out, long long n, cudaStream_t st) {
   k_edge_phase<<<152 * 4, 256, 0, st>>>(re, im, out, n);

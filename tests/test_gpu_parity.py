@@ -395,6 +395,7 @@ def test_full_size_sampled_sites(n, prec):
             pytest.skip("needs ~140 GB of free device memory")
     p = radiation(n, 2560 if n == 1024 else 640, precision=prec, seed=4)
     lat = U.Lattice(p)
+    lat.autotune()  # the benchmark's launch configuration: kernel and z-chunking by timing
     lat.step(20)
     sites = synth.site_sample(p.shape, 192, seed=n)
     pt = patches(lat.fields(), p.shape, sites, radius=2)
@@ -427,6 +428,35 @@ def test_full_size_sampled_sites(n, prec):
     assert res["n_p"] == int(Wg[0].abs().sum(dtype=torch.int64).item())
 
 
+def test_wave_targets_agree_bit_exact():
+    """Every z-chunking the autotuner may choose gives the same fields bit for
+    bit, since each site's update does not depend on where its z-chunk
+    starts.  On a 1024 x 1024 x 300 box the wave targets 8 .. 256 cut z into
+    chunks of 300, 150, 75, 38 (ragged last chunk of 34) and 32 (ragged last
+    chunk of 12) planes, so chunk prologues and their carries fall on
+    different planes; 1024-wide rows put most tiles on tensor copies."""
+    free = torch.cuda.mem_get_info()[0]
+    if free < 100e9:
+        pytest.skip("needs ~90 GB of free device memory")
+    p = radiation((1024, 1024, 300), 320, precision=U.FP32, seed=21)
+    ref = None
+    for w in (8, 16, 32, 64, 128, 256):
+        lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+        lat.set_tile_waves(w)
+        lat.step(4)
+        got = [t.clone() for t in lat.fields()]
+        lat.close()
+        del lat
+        if ref is None:
+            ref = got
+            continue
+        for f, (a, b) in enumerate(zip(got, ref)):
+            assert torch.equal(a, b), (w, f)
+        del got
+    del ref
+    torch.cuda.empty_cache()
+
+
 def test_checkpoint_resume_bit_exact(tmp_path):
     p = radiation(24, 50, precision=U.FP32, seed=12)
     a = U.Lattice(p)
@@ -441,16 +471,52 @@ def test_checkpoint_resume_bit_exact(tmp_path):
     assert torch.equal(a.state(), b.state())
 
 
-def test_upload_download_roundtrip():
-    p = U.Params(nx=16, ny=8, nz=8, precision=U.FP64)
+@pytest.mark.parametrize("shape,prec", [((16, 8, 8), U.FP64), ((16, 8, 8), U.FP32), ((12, 6, 5), U.FP32)])
+def test_upload_download_roundtrip(shape, prec):
+    """State transfers: pinned, 16-byte aligned host tensors are copied by
+    the SM kernel through their mapped address (a field is a whole number of
+    16-byte words since nx is a multiple of 4); pageable tensors and pinned
+    views at an 8-byte offset by the copy engines.  Every mix of the two
+    lands bit for bit on the device and comes back unchanged."""
+    p = U.Params(nx=shape[0], ny=shape[1], nz=shape[2], precision=prec)
+    dt = torch.float64 if prec == U.FP64 else torch.float32
+    V, nb = p.nsites, p.nsites * (8 if prec == U.FP64 else 4)
     lat = U.Lattice(p)
-    st = torch.from_numpy(synth.random_state(p.shape, seed=1)).reshape(20, -1)
-    host_in = [st[f].contiguous().pin_memory() for f in range(20)]
-    lat.upload(host_in)
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-    lat.download(host_out)
-    torch.cuda.synchronize()
-    assert all(torch.equal(a, b) for a, b in zip(host_in, host_out))
+    st = torch.from_numpy(synth.random_state(p.shape, seed=1)).reshape(20, -1).to(dt)
+    pinned = [st[f].contiguous().pin_memory() for f in range(20)]
+    assert all(U.host_span_mapped(t.data_ptr(), nb) for t in pinned)
+    pageable = [st[f].clone() for f in range(20)]
+    assert not any(U.host_span_mapped(t.data_ptr(), nb) for t in pageable)
+    block = torch.empty(V + 2, dtype=dt).pin_memory()
+    assert not U.host_span_mapped(block.data_ptr(), 8)  # not a whole 16-byte word
+    assert not U.host_span_mapped(block.data_ptr(), 1 << 40)  # beyond the allocation
+    odd = block.view(torch.uint8)[8:8 + nb].view(dt)  # pinned, 8-byte offset
+    odd.copy_(st[3])
+    assert not U.host_span_mapped(odd.data_ptr(), nb)
+
+    def expect_device():
+        torch.cuda.synchronize()
+        got = lat.fields()
+        for f in range(20):
+            assert torch.equal(got[f].cpu(), st[f]), f
+
+    lat.upload(pinned)
+    expect_device()
+    mixed = [pinned[f] if f % 2 == 0 else pageable[f] for f in range(20)]
+    mixed[3] = odd
+    lat.upload(mixed)
+    expect_device()
+    outs = {
+        "pinned": [torch.empty(V, dtype=dt).pin_memory() for _ in range(20)],
+        "pageable": [torch.empty(V, dtype=dt) for _ in range(20)],
+    }
+    outs["mixed"] = [outs["pinned"][f] if f % 2 else outs["pageable"][f] for f in range(20)]
+    for name, out in outs.items():
+        for t in out:
+            t.fill_(float("nan"))
+        lat.download(out)
+        torch.cuda.synchronize()
+        assert all(torch.equal(out[f], st[f]) for f in range(20)), name
 
 
 def test_vacuum_special_values():
