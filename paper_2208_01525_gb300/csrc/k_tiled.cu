@@ -628,10 +628,16 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   cp_async_wait0();
 
   if (MEAS) {
-    ThreadAcc ta;
-#pragma unroll
-    for (int k = 0; k < NSUM; ++k)
-      ta.s[k] = ((tid & 31) == 0) ? (double)sm.wsum[tid >> 5][k] - (double)sm.wcmp[tid >> 5][k] : 0.0;
+    // The block's partial: the warps' compensated sums are already in
+    // shared memory, so only the extremes (in the working precision) and
+    // the counts (32-bit, like each thread's own: a warp adds 32 of them) are
+    // reduced across each warp; then one thread per quantity merges the
+    // warps in a fixed order, the sums by Neumaier in FP64.  Nothing
+    // per-thread goes through GB300's narrow FP64 pipe, so the cost of a
+    // block's epilogue no longer grows the detection step when z-chunks
+    // are short and blocks many.
+    constexpr int NW = TL::NT / 32;
+    const int lane = tid & 31, warp = tid >> 5;
     // |phi| from the extremes of |phi|^2 (-inf: no site of this block)
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -640,12 +646,49 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
       if (mx[kx] != -INFINITY) mx[kx] = sqrt(mx[kx]);
     }
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) ta.mx[k] = (double)mx[k];
+    for (int k = 0; k < NMAX; ++k) {
 #pragma unroll
-    for (int k = 0; k < NCNT; ++k) ta.cnt[k] = cnt[k];
+      for (int o = 16; o > 0; o >>= 1) mx[k] = fmax(mx[k], __shfl_down_sync(0xffffffffu, mx[k], o));
+    }
+#pragma unroll
+    for (int k = 0; k < NCNT; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const int u = __shfl_down_sync(0xffffffffu, cnt[k], o);
+        cnt[k] = k == C_MAXW ? max(cnt[k], u) : cnt[k] + u;
+      }
+    }
+    struct EpiSmem {
+      double mx[NW][NMAX];
+      long long cnt[NW][NCNT];
+    };
+    static_assert(sizeof(EpiSmem) <= sizeof(sm.pos), "epilogue scratch must fit in the position ring");
+    __syncthreads();  // the ring is no longer read; every warp's sums are final
+    EpiSmem& es = *reinterpret_cast<EpiSmem*>(&sm.pos[0][0][0]);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NMAX; ++k) es.mx[warp][k] = (double)mx[k];
+#pragma unroll
+      for (int k = 0; k < NCNT; ++k) es.cnt[warp][k] = cnt[k];
+    }
     __syncthreads();
-    ReduceSmem<TL::NT / 32>& rs = *reinterpret_cast<ReduceSmem<TL::NT / 32>*>(smem_raw);
-    block_reduce<TL::NT / 32>(ta, rs, mo.partial + bid);
+    BlockPartial* out = mo.partial + bid;
+    if (tid < NSUM) {
+      double sum = 0.0, comp = 0.0;
+      for (int w = 0; w < NW; ++w) neumaier_add(sum, comp, (double)sm.wsum[w][tid] - (double)sm.wcmp[w][tid]);
+      out->sum[tid] = sum;
+      out->comp[tid] = comp;
+    } else if (tid < NSUM + NMAX) {
+      const int k = tid - NSUM;
+      double m = -INFINITY;
+      for (int w = 0; w < NW; ++w) m = fmax(m, es.mx[w][k]);
+      out->mx[k] = m;
+    } else if (tid < NSUM + NMAX + NCNT) {
+      const int k = tid - NSUM - NMAX;
+      long long n = 0;
+      for (int w = 0; w < NW; ++w) n = k == C_MAXW ? max(n, es.cnt[w][k]) : n + es.cnt[w][k];
+      out->cnt[k] = n;
+    }
   }
 }
 
