@@ -1,6 +1,6 @@
 """Host-side logic of bench.py, without a GPU: the whole-job figures of a
-multi-rank run (world size 2 over gloo on 127.0.0.1), the clock summary and
-the hash-keyed DRAM traffic record."""
+multi-rank run (world size 2 over gloo on 127.0.0.1), the clock summary,
+the hash-keyed DRAM traffic record and the reference arm's JSON line."""
 import os
 import socket
 import sys
@@ -99,3 +99,39 @@ def test_launch_count_per_detection_period():
     assert bench.measure_partials(1024, True) == 16384 + 34 * 147 * 2
     assert bench.launches_per_period(64, 16, True) == 20
     assert bench.launches_per_period(64, 16, False) == 19
+
+
+def _run_bench(args, env_extra=None):
+    import subprocess
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=300)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`--impl reference` times the FP64 oracle on the host cores (one step =
+    one detection period of the sample) and prints one JSON line with the
+    benchmark's metric and unit, `impl`, a `cpu_baseline` describing the run
+    and an `e2e` with no host-device bytes."""
+    import json
+    r = _run_bench(["--impl", "reference", "--ref-n", "16", "--steps", "2", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "site-updates/s"
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert abs(d["value"] - 2 * 16 * 16 ** 3 / (2 * d["ms_per_step"] * 1e-3)) <= 1e-6 * d["value"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "16^3" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs and prints the reference arm."""
+    r = _run_bench(["--impl", "reference", "--ref-n", "16", "--steps", "1", "--warmup", "1"], {"RANK": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
