@@ -38,10 +38,15 @@ if ROOT not in sys.path:
 METRIC = "site-updates/s & % HBM roofline, FP32 vs FP64, U(1)xU(1) step at 1024^3"
 BYTES_PER_SITE = {"fp32": 160, "fp64": 320}  # read 20 + write 20 words
 # FP64 step: 126 DFMA + 60 DADD + 77 DMUL per site (ncu thread-instruction
-# counts of one launch at 256^3) = 389 FP64 operations; nominal FP64 rate of
-# the GB300 (non-tensor) 1.25 TFLOP/s
+# counts of one launch at 256^3) = 389 FP64 operations; its ceiling is the
+# FP64 rate measured in the same run by the library's FMA probe (nominal
+# GB300 non-tensor FP64: 1.25 TFLOP/s, used only if the probe fails)
 FP64_FLOPS_PER_SITE = 389
-FP64_PEAK_TFLOPS = 1.25
+FP64_NOMINAL_TFLOPS = 1.25
+# standalone string detection: the windings kernel reads the ten position
+# fields (40 B/site in FP32) and writes 2 face bytes per site, the cell pass
+# reads those back and writes 0.25 B/site of masks
+DETECT_BYTES_PER_SITE = {"fp32": 40 + 2 + 2 + 0.25, "fp64": 80 + 2 + 2 + 0.25}
 
 
 def peaks():
@@ -382,8 +387,8 @@ def run_ours(args):
 
     # standalone passes on the current state (no step): the diagnostics pass
     # (all sums and the Gauss residual; reads positions and momenta, 80 B/site
-    # in FP32) and string detection (sums, windings, cells, overlap); each
-    # call ends with its record copied to the host
+    # in FP32) and string detection (windings of the positions, cells,
+    # overlap); each call ends with its record copied to the host
     passes = None
     if args.passes:
         passes = {}
@@ -403,6 +408,9 @@ def run_ours(args):
         rd = BYTES_PER_SITE[tag] // 2 * V  # the pass reads the 20 words of every site once
         passes["diagnostics"]["hbm_frac"] = rd / (passes["diagnostics"]["ms"] * 1e-3) / 1e9 / peak
         passes["diagnostics"]["bytes_per_site"] = BYTES_PER_SITE[tag] // 2
+        db = DETECT_BYTES_PER_SITE[tag]
+        passes["detect_strings"]["hbm_frac"] = db * V / (passes["detect_strings"]["ms"] * 1e-3) / 1e9 / peak
+        passes["detect_strings"]["bytes_per_site"] = db
 
     # end-to-end through the public API with host buffers
     e2e = None
@@ -444,6 +452,41 @@ def run_ours(args):
     gc.collect()
     torch.cuda.empty_cache()
 
+    # the core-growth case of the same box (beta = -1, unit width at the
+    # start: a = 1 at eta0), same kernel choice, a few detection periods
+    beta_m1 = None
+    if args.beta_m1_steps > 0:
+        pb = U.Params.cube(n, m=0.5, beta=-1.0, eta0=1.0, eta_ref=1.0, seed=2024 + rank, precision=prec)
+        latb = U.Lattice(pb, device=dev, kernel=kernel_used)
+        if kernel_used == U.KERNEL_TILED:
+            latb.set_tile_waves(waves_used)
+        for _ in range(args.warmup):
+            latb.step(de, detect_every=de)
+        torch.cuda.synchronize()
+        latb.read_records()
+        evb = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.beta_m1_steps)]
+        for k in range(args.beta_m1_steps):
+            evb[k][0].record(stream)
+            latb.step(1, detect_every=de)
+            evb[k][1].record(stream)
+            latb.step(de - 1, detect_every=de)
+            evb[k][2].record(stream)
+        torch.cuda.synchronize()
+        tb = sum(e[0].elapsed_time(e[2]) for e in evb) / args.beta_m1_steps
+        pl = sum(e[1].elapsed_time(e[2]) for e in evb) / (args.beta_m1_steps * (de - 1))
+        recb, _ = latb.read_records()
+        beta_m1 = {"beta": -1.0, "lattice": n, "periods": args.beta_m1_steps, "ms_per_period": tb,
+                   "value": de * V / (tb * 1e-3), "unit": "site-updates/s",
+                   "detect_ms_per_period": sum(e[0].elapsed_time(e[1]) for e in evb) / args.beta_m1_steps,
+                   "plain_ms_per_launch": pl,
+                   "hbm_frac": BYTES_PER_SITE[tag] * V / (pl * 1e-3) / 1e9 / peak,
+                   "last_record": None if not recb else {"n": recb[-1][0]["n"], "xi_w": recb[-1][0]["xi_w"],
+                                                          "f_total": recb[-1][0]["f_total"]}}
+        latb.close()
+        del latb
+        gc.collect()
+        torch.cuda.empty_cache()
+
     # FP64 step throughput (same box when it fits)
     fp64 = None
     if args.fp64_n > 0 and prec == U.FP32:
@@ -455,6 +498,11 @@ def run_ours(args):
         if free <= need:
             fp64 = {"lattice": n64, "skipped": f"needs {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free"}
         else:
+            # the FP64 ceiling measured on this device (FMA probe, no setting changed)
+            try:
+                fp64_peak, fp64_kind = U.fp64_fma_rate(), "measured (FP64 FMA probe)"
+            except U.U1U1Error:
+                fp64_peak, fp64_kind = FP64_NOMINAL_TFLOPS, "nominal"
             lat64 = U.Lattice(p64, device=dev, kernel=args.kernel)
             lat64.step(2)
             torch.cuda.synchronize()
@@ -466,14 +514,14 @@ def run_ours(args):
             t64 = a.elapsed_time(b) / args.fp64_steps
             # the FP64 step is bound by GB300's FP64 arithmetic, not by HBM:
             # FP64_FLOPS_PER_SITE from ncu instruction counts (DFMA x 2 + DADD
-            # + DMUL per site) against the nominal FP64 rate
+            # + DMUL per site) against the FP64 rate measured above
             tflops = FP64_FLOPS_PER_SITE * p64.nsites / (t64 * 1e-3) / 1e12
             fp64 = {"lattice": n64, "value": p64.nsites / (t64 * 1e-3), "unit": "site-updates/s",
                     "ms_per_step": t64,
                     "hbm_frac": BYTES_PER_SITE["fp64"] * p64.nsites / (t64 * 1e-3) / 1e9 / peak,
-                    "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                                 "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
-                                 "peak_kind": "nominal", "flops_per_site": FP64_FLOPS_PER_SITE},
+                    "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak,
+                                 "unit": "TFLOP/s (FP64)", "frac": tflops / fp64_peak,
+                                 "peak_kind": fp64_kind, "flops_per_site": FP64_FLOPS_PER_SITE},
                     "steps": args.fp64_steps}
             lat64.close()
             del lat64
@@ -513,6 +561,7 @@ def run_ours(args):
             "gpu_launches": args.steps * launches_per_period(n, de, kernel_used != U.KERNEL_SIMPLE),
             "e2e": e2e,
             "fp64": fp64,
+            "beta_m1": beta_m1,
             "ensemble": ens,
             "cpu_baseline": cpu,
             "records_lost": lost,
@@ -537,7 +586,9 @@ def main():
     ap.add_argument("--detect-every", type=int, default=16)
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--fp64-n", type=int, default=1024)
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--beta-m1-steps", type=int, default=5,
+                    help="detection periods timed on the beta = -1 (core growth) box; 0 skips it")
     ap.add_argument("--cpu-n", type=int, default=128)
     ap.add_argument("--ref-n", type=int, default=96)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

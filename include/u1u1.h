@@ -231,8 +231,17 @@ int u1u1_current(const u1u1_lattice* h, int64_t* n, int* current);
  * (Sec. III.A), the fast cell overlap (Sec. III.B, tolerance set by
  * u1u1_set_overlap_tol, default 1) and the diagnostic sums (Eqs. 33, 36-37,
  * without the Gauss-law fields); the result is appended to the handle's
- * record ring (read with u1u1_read_records).  Asynchronous; safe to capture
- * in a CUDA graph.  Errors: INVALID_ARG, CUDA. */
+ * record ring (read with u1u1_read_records).  Asynchronous on `stream`.
+ * Each enqueued launch carries the values of the step it was enqueued for:
+ * the coefficients of step n (Eqs. 12, 19, 22), the position buffer it reads
+ * and writes, and (detection steps) the record-ring slot.  The call may be
+ * recorded by stream capture, but a replay of such a graph repeats exactly
+ * the captured launches with those captured values: it neither advances the
+ * handle's step index nor re-evaluates the coefficients, and with an odd
+ * nsteps it reads the position buffer the capture started from while the
+ * momenta advance in place.  For replayed steps use the ensemble API, whose
+ * graphs read coefficients and buffers from device tables.
+ * Errors: INVALID_ARG, CUDA. */
 int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* stream);
 
 /* Diffusive cooling (Sec. III, Eqs. 27-30): nsteps >= 0 forward-Euler steps
@@ -256,14 +265,18 @@ int u1u1_set_params(u1u1_lattice* h, const u1u1_params* p, int64_t n);
  * used by fused detection steps. */
 int u1u1_set_overlap_tol(u1u1_lattice* h, int tol);
 
-/* Fast string detection on the current state without stepping (Sec. III.A-B).
+/* Fast string detection on the current state without stepping (Sec. III.A-B):
+ * the plaquette windings of the current positions, the cells, the overlap
+ * and the counts (the momenta are not read).
  * Optional device outputs (NULL to skip): cell_p, cell_q (uint8 per site:
  * sum over the cell's six faces of |W|, each |W| counted up to 3; any
  * alignment, 16-byte aligned arrays take the vectorised pass),
  * windings (int8, 6 arrays of nx*ny*nz: sector-major, plane (x,y), (x,z),
  * (y,z), the plaquette anchored at each site).  *out is filled on the host
  * (synchronises `stream`).  Errors: INVALID_ARG, CUDA, TIMEOUT (a tiled
- * kernel's bounded wait for its shared-memory tensor copies ran out). */
+ * step kernel of this handle had a bounded wait for its shared-memory tensor
+ * copies run out since the handle's last check; each handle keeps its own
+ * status, so a timeout is reported only by the handle whose launch it hit). */
 int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
                         int8_t* windings, u1u1_strings* out, void* stream);
 
@@ -292,8 +305,9 @@ int u1u1_diagnostics(u1u1_lattice* h, u1u1_diag* out, void* stream);
  * first, into s_out[] and d_out[] (either may be NULL); *count receives the
  * number copied and *lost (may be NULL) the number overwritten in the
  * device ring (capacity 1024) before they were read.  Synchronises `stream`.
- * Errors: INVALID_ARG, CUDA, TIMEOUT (a step kernel's bounded wait for its
- * shared-memory tensor copies ran out since the last check). */
+ * Errors: INVALID_ARG, CUDA, TIMEOUT (a step kernel of this handle had a
+ * bounded wait for its shared-memory tensor copies run out since the
+ * handle's last check). */
 int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag* d_out, int max, int* count,
                       int64_t* lost, void* stream);
 
@@ -359,7 +373,8 @@ int u1u1_set_tile_waves(u1u1_lattice* h, int waves);
  * enqueued afterwards see it).
  * enable = 1 makes every ring slot expect 16 bytes more than its copies
  * deliver, so every such wait runs out after limit_ns (the kernel finishes
- * on the delivered data and the next synchronising call returns TIMEOUT);
+ * on the delivered data and the next synchronising call of the handle that
+ * launched it returns TIMEOUT);
  * enable = 0 restores normal copies.  limit_ns (>= 1000) is the wait limit
  * from then on; the default is 2 s.  No GPU fault or hang is involved.
  * Errors: INVALID_ARG. */
@@ -442,14 +457,16 @@ void u1u1_ensemble_destroy(u1u1_ensemble* e);
  * addition: the paper has no counterpart.
  * Arguments: p, the lattice parameters; fields, the 20 device field arrays
  * of the state (U1U1_POS_* then U1U1_MOM_* order, layout as for a lattice,
- * 256-byte aligned), read only; n, the step index the record reports;
+ * 256-byte aligned; only the ten position fields are read); n, the step
+ * index the record reports;
  * overlap_tol, 0 or 1; *out, filled on the host.  Synchronises `stream`.
  * Limits: at most U1U1_NOALLOC_MAX_SITES sites, and the scratch the shape
  * needs must fit the array (every cubic box up to 256^3 does); larger
  * requests return U1U1_ERR_INVALID_ARG with the byte count in the message.
  * Set-up: the first call on a device, with that device current, looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one array, which keeps
+ * before any stream capture.  The lookup is repeated only when the device's
+ * context has changed since (e.g. after cudaDeviceReset).  All calls share the one array, which keeps
  * the last call's contents: calls that overlap on the GPU (several streams
  * or threads) race and must be serialised by the caller.
  * Errors: INVALID_ARG, NOT_SUPPORTED (device index >= 64), CUDA. */
@@ -457,6 +474,16 @@ int u1u1_detect_strings_noalloc(const u1u1_params* p, const void* const fields[U
                                 int overlap_tol, u1u1_strings* out, void* stream);
 
 /* ---- check entry points ---------------------------------------------------- */
+
+/* Measured FP64 arithmetic rate of the current device, in TFLOP/s (two
+ * operations per fused multiply-add): every thread of a full-occupancy grid
+ * runs eight independent chains of dependent FP64 FMAs, timed with CUDA
+ * events on `stream` over runs of at least 50 ms (best of several).  The
+ * ceiling of the FP64 step, which is bound by the FP64 pipe rather than by
+ * HBM (Sec. III, Eqs. 17-26 in double precision); a measurement helper with
+ * no counterpart in the paper.  Changes no device setting and allocates no
+ * device memory.  Synchronises `stream`.  Errors: INVALID_ARG, CUDA. */
+int u1u1_fp64_fma_rate(double* tflops, void* stream);
 
 /* Evaluate, on n device values theta, the FP32 routine the kernels use for
  * the link variable U = exp(-i theta) (sin and cos of theta: reduction by

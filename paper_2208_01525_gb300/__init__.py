@@ -84,6 +84,13 @@ def host_span_mapped(ptr: int, nbytes: int) -> bool:
     return bool(v.value)
 
 
+def fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 fused-multiply-add rate of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    check(lib().u1u1_fp64_fma_rate(ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
+
+
 def check_params(p: Params) -> None:
     check(lib().u1u1_check_params(ctypes.byref(p.c())))
 

@@ -213,7 +213,9 @@ void u1u1::lattice_free_scratch(u1u1_lattice* h) {
   cudaFree(h->cpartials);
   cudaFree(h->ring);
   cudaFree(h->scratch_rec);
+  cudaFree(h->tma_status);
   cudaFreeHost(h->host_rec);
+  cudaFreeHost(h->host_status);
 }
 
 int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out) {
@@ -250,6 +252,9 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ring, sizeof(RawRecord) * RING_CAP);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->scratch_rec, sizeof(RawRecord));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_rec, sizeof(RawRecord) * RING_CAP);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->tma_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->tma_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_status, sizeof(int));
   if (e != cudaSuccess) {
     lattice_free_scratch(h);
     free(h);
@@ -383,7 +388,7 @@ template <typename T>
 static cudaError_t run_kernel(u1u1_lattice* h, int mode, const MeasureOut& mo, cudaStream_t st) {
   LatticeView<T> v = view<T>(h);
   Coef<T> c = make_coef<T>(&h->p, h->n);
-  if (use_tiled(h)) return launch_tiled<T>(mode, v, c, mo, st, launch_waves(h, mode));
+  if (use_tiled(h)) return launch_tiled<T>(mode, v, c, mo, st, launch_waves(h, mode), h->tma_status);
   return launch_simple<T>(mode, v, c, mo, st);
 }
 
@@ -397,6 +402,31 @@ static int measure_blocks(const u1u1_lattice* h, bool windings) {
 
 static cudaError_t dispatch(u1u1_lattice* h, int mode, const MeasureOut& mo, cudaStream_t st) {
   return h->esize == 8 ? run_kernel<double>(h, mode, mo, st) : run_kernel<float>(h, mode, mo, st);
+}
+
+// Windings, face bytes and counts of the current positions for a
+// standalone detection (Sec. III.A): on the tiled path the windings kernel
+// alone, which reads the ten position fields once and neither the momenta
+// nor any step arithmetic; the simple kernel family takes its own windings
+// in a measuring pass.  Returns the number of block partials written.
+template <typename T>
+static cudaError_t windings_t(u1u1_lattice* h, int8_t* windings, cudaStream_t st) {
+  PosView<T> pv;
+  for (int f = 0; f < U1U1_NPOS; ++f) pv.pos[f] = (const T*)h->pos[h->cur][f];
+  pv.nx = h->p.nx;
+  pv.ny = h->p.ny;
+  pv.nz = h->p.nz;
+  return launch_windings<T>(pv, (T)h->p.dx, h->partials, h->faces, windings, st);
+}
+
+static cudaError_t strings_pass(u1u1_lattice* h, int8_t* windings, cudaStream_t st, int* nblocks) {
+  if (!use_tiled(h)) {
+    *nblocks = simple_grid_blocks();
+    MeasureOut mo{h->partials, h->faces, windings};
+    return dispatch(h, MODE_MEASURE, mo, st);
+  }
+  *nblocks = wind_grid_blocks(h->p.nx, h->p.ny, h->p.nz);
+  return h->esize == 8 ? windings_t<double>(h, windings, st) : windings_t<float>(h, windings, st);
 }
 
 extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* stream) {
@@ -466,7 +496,7 @@ static cudaError_t cool_t(u1u1_lattice* h, double dt, int nsteps, cudaStream_t s
   const MeasureOut mo{nullptr, nullptr, nullptr};
   for (int k = 0; k < nsteps; ++k) {
     LatticeView<T> v = view<T>(h);
-    cudaError_t e = use_tiled(h) ? launch_tiled<T>(MODE_WRITE, v, c, mo, st, h->tile_waves)
+    cudaError_t e = use_tiled(h) ? launch_tiled<T>(MODE_WRITE, v, c, mo, st, h->tile_waves, h->tma_status)
                                  : launch_simple<T>(MODE_WRITE, v, c, mo, st);
     if (e != cudaSuccess) return e;
     h->cur ^= 1;
@@ -605,13 +635,19 @@ static void to_diag(const u1u1_params* p, const RawRecord& r, u1u1_diag* d) {
   d->nan_count = r.cnt[C_NAN];
 }
 
-// After a synchronisation: a tiled kernel whose wait for a tensor copy into
-// shared memory ran out of time finished on stale data; report it once.
-static int check_tma_timeout(cudaStream_t st) {
-  if (tma_timeout_flag(true, st))
-    return fail(U1U1_ERR_TIMEOUT, "a tiled kernel's wait for a tensor copy into shared memory ran out (2 s); "
-                                  "the fields written since may be wrong");
-  return U1U1_OK;
+// A tiled kernel of this handle whose wait for a tensor copy into shared
+// memory ran out of time finished on stale data and set the handle's status
+// word; read it in the order of `st` (which this synchronises) and report
+// it once.  Other handles' words are not touched.
+static int check_tma_timeout(u1u1_lattice* h, cudaStream_t st) {
+  U1U1_CUDA_TRY(cudaMemcpyAsync(h->host_status, h->tma_status, sizeof(int), cudaMemcpyDeviceToHost, st),
+                "status copy");
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  if (*h->host_status == 0) return U1U1_OK;
+  U1U1_CUDA_TRY(cudaMemsetAsync(h->tma_status, 0, sizeof(int), st), "status reset");
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  return fail(U1U1_ERR_TIMEOUT, "a tiled kernel's wait for a tensor copy into shared memory ran out (2 s); "
+                                "the fields written since may be wrong");
 }
 
 static int read_scratch(u1u1_lattice* h, RawRecord* r, cudaStream_t st) {
@@ -619,7 +655,7 @@ static int read_scratch(u1u1_lattice* h, RawRecord* r, cudaStream_t st) {
                 "record copy");
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
   *r = h->host_rec[0];
-  return check_tma_timeout(st);
+  return check_tma_timeout(h, st);
 }
 
 extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
@@ -628,14 +664,14 @@ extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* ce
   if (overlap_tol < 0 || overlap_tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
   if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  MeasureOut mo{h->partials, h->faces, windings};
-  cudaError_t e = dispatch(h, MODE_MEASURE, mo, st);
-  if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
+  int nblocks = 0;
+  cudaError_t e = strings_pass(h, windings, st, &nblocks);
+  if (e != cudaSuccess) return cuda_fail(e, "windings kernel");
   e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, cell_p, cell_q, h->masks, h->cpartials, st,
                    nullptr, h->ge4);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
-  e = launch_finalize(h->partials, measure_blocks(h, true), h->cpartials, h->ncpartials, h->scratch_rec,
-                      (long long)h->n, 1, 0, 1, overlap_tol, st, h->ge4);
+  e = launch_finalize(h->partials, nblocks, h->cpartials, h->ncpartials, h->scratch_rec, (long long)h->n, 0, 0, 1,
+                      overlap_tol, st, h->ge4);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   RawRecord r;
   int rc = read_scratch(h, &r, st);
@@ -670,9 +706,9 @@ extern "C" int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells,
                   cudaGetErrorString(e));
     }
   }
-  MeasureOut mo{h->partials, h->faces, nullptr};
-  cudaError_t e = dispatch(h, MODE_MEASURE, mo, st);
-  if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
+  int nblocks = 0;
+  cudaError_t e = strings_pass(h, nullptr, st, &nblocks);
+  if (e != cudaSuccess) return cuda_fail(e, "windings kernel");
   e = launch_cells(h->faces, h->p.nx, h->p.ny, h->p.nz, overlap_tol, nullptr, nullptr, h->masks, h->cpartials, st,
                    h->mpq);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
@@ -739,7 +775,7 @@ extern "C" int u1u1_read_records(u1u1_lattice* h, u1u1_strings* s_out, u1u1_diag
     U1U1_CUDA_TRY(cudaMemcpyAsync(h->host_rec, h->ring, sizeof(RawRecord) * (take - run1),
                                   cudaMemcpyDeviceToHost, st), "record ring copy");
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
-  if (int rc = check_tma_timeout(st)) return rc;
+  if (int rc = check_tma_timeout(h, st)) return rc;
   for (int64_t k = 0; k < take; ++k) {
     const RawRecord& r = h->host_rec[(h->rec_read + k) % RING_CAP];
     if (s_out) to_strings(&h->p, r, &s_out[k]);

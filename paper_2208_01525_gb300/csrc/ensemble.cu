@@ -53,7 +53,7 @@ struct u1u1_ensemble {
   void* d_coef = nullptr;   // Coef<T>[nboxes * horizon]
   unsigned long long* d_ticket = nullptr;
   unsigned* d_done = nullptr;
-  int* d_err = nullptr;
+  int* d_err = nullptr;      // [0]: persistent-kernel error, [1]: tensor-copy timeout of the per-step kernel
   std::vector<int> ntiles;
   // host view of the device step indices after every enqueued run
   std::vector<long long> shadow_n;
@@ -89,7 +89,10 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
   // otherwise), read by the kernels from device memory
   std::vector<TmaPlan> hp((size_t)2 * nb);
   for (int b = 0; b < nb; ++b)
-    for (int k = 0; k < 2; ++k) make_tma_plan<T>(hb[b].pos[k], hb[b].nx, hb[b].ny, hb[b].nz, &hp[2 * b + k]);
+    for (int k = 0; k < 2; ++k) {
+      make_tma_plan<T>(hb[b].pos[k], hb[b].nx, hb[b].ny, hb[b].nz, &hp[2 * b + k]);
+      hp[2 * b + k].status = e->d_err + 1;  // a copy timeout is this ensemble's, reported by its status
+    }
   if (!e->d_tma) U1U1_CUDA_TRY(cudaMalloc((void**)&e->d_tma, sizeof(TmaPlan) * hp.size()), "ensemble tensor maps");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_tma, hp.data(), sizeof(TmaPlan) * hp.size(), cudaMemcpyHostToDevice),
                 "tensor map copy");
@@ -251,15 +254,17 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
     h->kernel = U1U1_KERNEL_TILED;
     e->boxes.push_back(h);
   }
-  int rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
+  int rc = U1U1_OK;
   cudaError_t err = cudaSuccess;
+  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_err, 2 * sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(e->d_err, 0, 2 * sizeof(int));
+  if (err != cudaSuccess) rc = cuda_fail(err, "ensemble allocation");
+  if (!rc) rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
   if (!rc) {
     if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_dyn, sizeof(EnsDyn) * nboxes);
     if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_ticket, sizeof(unsigned long long));
     if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_done, sizeof(unsigned) * nboxes);
-    if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_err, sizeof(int));
     if (err == cudaSuccess) err = cudaMemset(e->d_dyn, 0, sizeof(EnsDyn) * nboxes);
-    if (err == cudaSuccess) err = cudaMemset(e->d_err, 0, sizeof(int));
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->capture_stream, cudaStreamNonBlocking);
     if (err != cudaSuccess) rc = cuda_fail(err, "ensemble allocation");
   }
@@ -340,11 +345,11 @@ extern "C" int u1u1_ensemble_lattice(u1u1_ensemble* e, int box, u1u1_lattice** h
 
 extern "C" int u1u1_ensemble_status(u1u1_ensemble* e, int* status, void* stream) {
   if (!e || !status) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
-  int v = 0;
-  U1U1_CUDA_TRY(cudaMemcpyAsync(&v, e->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status");
+  int w[2] = {0, 0};
+  U1U1_CUDA_TRY(cudaMemcpyAsync(w, e->d_err, sizeof(w), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status");
   U1U1_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
   // a wait for a tensor copy that ran out counts as a timeout too
-  if (v == 0 && tma_timeout_flag(true, (cudaStream_t)stream)) v = U1U1_ERR_TIMEOUT;
+  const int v = w[0] != 0 ? w[0] : w[1];
   *status = v;
   if (v != 0) e->poisoned = 1;
   return U1U1_OK;

@@ -62,6 +62,8 @@ struct u1u1_lattice {
   u1u1::SegCounts* seg_counts;
   RawRecord* ring;
   RawRecord* scratch_rec;
+  int* tma_status;      // device word: U1U1_ERR_TIMEOUT after a tensor-copy wait ran out
+  int* host_status;     // pinned copy of it, read after a synchronisation
   RawRecord* host_rec;  // pinned, RING_CAP entries
   int64_t rec_written;
   int64_t rec_read;

@@ -46,9 +46,6 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // ---- tensor-memory-access (TMA) copies of the position ring ----------------
-// set when a wait for a tensor copy ran out; read by the host
-__device__ int g_tma_timeout = 0;
-
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ long long gtimer_ns() {
   unsigned long long t;
@@ -71,21 +68,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned pa
   return ok != 0;
 }
 // Wait for phase `parity` of m to complete, for at most `limit` ns (2 s);
-// true when it did.  Past the limit the global flag is set for the host and
-// the CTA's flag is set, after which the CTA's later waits give up at once
+// true when it did.  Past the limit the launching handle's status word is
+// set to U1U1_ERR_TIMEOUT for the host and the CTA's flag is set, after which
+// the CTA's later waits give up at once
 // (they still return, so every thread reaches every barrier) and the
 // thread that issues the copies issues no more (re-arming a slot whose phase
 // never completed would be an arrival too many); the CTA finishes on stale
 // data.  A timed-out wait has given the slot's copies the whole limit to
 // land before the CTA can exit.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity, volatile int* cta_fail,
-                                                  long long limit) {
+                                                  long long limit, int* status) {
   if (mbar_try_wait(m, parity)) return true;
   if (*cta_fail) return false;
   const long long t0 = gtimer_ns();
   while (!mbar_try_wait(m, parity)) {
     if (gtimer_ns() - t0 > limit) {
-      atomicExch(&g_tma_timeout, 1);
+      if (status) atomicExch(status, U1U1_ERR_TIMEOUT);
       *cta_fail = 1;
       return false;
     }
@@ -285,7 +283,8 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   };
   bool copies_ok = true;  // every wait of this thread completed
   auto tma_wait = [&](int slot) {
-    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, wait_limit) && copies_ok;
+    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, wait_limit, tma->status) &&
+                copies_ok;
     phase ^= 1u << slot;
   };
   if (use_tma) {
@@ -790,7 +789,7 @@ void make_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* t
 
 template <typename T, int MODE>
 cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo, cudaStream_t st,
-                        int waves) {
+                        int waves, int* status) {
   constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
   constexpr bool MEAS = (MODE & MODE_MEASURE) != 0;
   constexpr bool GAUSS = (MODE & MODE_GAUSS) != 0;
@@ -820,6 +819,7 @@ cudaError_t launch_mode(const LatticeView<T>& v, const Coef<T>& c, const Measure
   make_plan<T>(v.pin, v.nx, v.ny, v.nz, &tp);
   tp.extra_bytes = g_inject_extra_bytes;
   tp.limit_ns = g_wait_limit_ns;
+  tp.status = status;
   k_tiled<T, TX, TY, MODE><<<grid, TX * TY, bytes, st>>>(v, c, mo, g.lz, tp);
   return cudaGetLastError();
 }
@@ -837,25 +837,6 @@ int tma_inject_timeout(int enable, long long limit_ns) {
   g_inject_extra_bytes = enable ? 16u : 0u;
   g_wait_limit_ns = limit_ns;
   return 0;
-}
-
-int tma_timeout_flag(bool clear, cudaStream_t st) {
-  // read (and clear) the flag in the order of stream st, so that no other
-  // stream is waited for; nothing is allocated (the allocation-free
-  // detection entry point calls this too)
-  int v = 0;
-  if (cudaMemcpyFromSymbolAsync(&v, g_tma_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  if (v && clear) {
-    const int zero = 0;
-    if (cudaMemcpyToSymbolAsync(g_tma_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      cudaGetLastError();
-  }
-  return v;
 }
 
 int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves) {
@@ -1077,19 +1058,20 @@ template cudaError_t launch_ens_step<double>(const EnsBox<double>*, const EnsDyn
 
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
-                         cudaStream_t st, int waves) {
+                         cudaStream_t st, int waves, int* status) {
+  if (!status) return cudaErrorInvalidValue;  // a copy timeout must reach its caller
   cudaError_t e;
   switch (mode) {
     case MODE_WRITE:
-      return launch_mode<T, MODE_WRITE>(v, c, mo, st, waves);
+      return launch_mode<T, MODE_WRITE>(v, c, mo, st, waves, status);
     case MODE_WRITE | MODE_MEASURE:
-      e = launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st, waves);
+      e = launch_mode<T, MODE_WRITE | MODE_MEASURE>(v, c, mo, st, waves, status);
       break;
     case MODE_MEASURE:
-      e = launch_mode<T, MODE_MEASURE>(v, c, mo, st, waves);
+      e = launch_mode<T, MODE_MEASURE>(v, c, mo, st, waves, status);
       break;
     case MODE_MEASURE | MODE_GAUSS:
-      e = launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st, waves);
+      e = launch_mode<T, MODE_MEASURE | MODE_GAUSS>(v, c, mo, st, waves, status);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -1111,8 +1093,8 @@ int tiled_measure_blocks(int nx, int ny, int nz, int sizeof_t, int waves, bool w
 }
 
 template cudaError_t launch_tiled<float>(int, const LatticeView<float>&, const Coef<float>&, const MeasureOut&,
-                                         cudaStream_t, int);
+                                         cudaStream_t, int, int*);
 template cudaError_t launch_tiled<double>(int, const LatticeView<double>&, const Coef<double>&,
-                                          const MeasureOut&, cudaStream_t, int);
+                                          const MeasureOut&, cudaStream_t, int, int*);
 
 }  // namespace u1u1

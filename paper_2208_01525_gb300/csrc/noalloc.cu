@@ -1,10 +1,11 @@
 // String detection for callers that cannot allocate device memory.
 //
-// u1u1_detect_strings_noalloc runs the same measuring kernel, cell pass and
+// u1u1_detect_strings_noalloc runs the same windings kernel, cell pass and
 // finalize as u1u1_detect_strings, but without a lattice handle: its scratch
 // (per-site winding bytes, packed cell masks, block partials, the census
 // counters and the result record) is carved out of one file-scope static device array, so the call
 // itself never calls cudaMalloc, cudaFree or any allocating routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -26,22 +27,59 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 void* g_scratch_addr[MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[MAX_DEVICES] = {};  // context the address belongs to
 std::mutex g_scratch_mu;
 
 size_t round_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// device address of the scratch array on the current device (set up on the
-// first call per device)
+// Unique id of the calling thread's current context, 0 when there is none
+// (or the driver entry points are unavailable).  Neither query allocates.
+unsigned long long current_context_id() {
+  using GetCurrentFn = CUresult (*)(CUcontext*);
+  using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+  static const GetCurrentFn get_current = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (GetCurrentFn) nullptr;
+    }
+    return reinterpret_cast<GetCurrentFn>(p);
+  }();
+  static const GetIdFn get_id = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (GetIdFn) nullptr;
+    }
+    return reinterpret_cast<GetIdFn>(p);
+  }();
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device.  Set up on
+// the first call per device, with that device current; looked up again
+// only when the device's context has changed since (after a
+// cudaDeviceReset the module may be loaded at another address).
 int scratch_address(void** out) {
   int dev = 0;
   U1U1_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev < 0 || dev >= MAX_DEVICES) return fail(U1U1_ERR_NOT_SUPPORTED, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
     g_scratch_addr[dev] = ptr;
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_addr[dev];
   return U1U1_OK;
@@ -51,7 +89,7 @@ template <typename T>
 int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int64_t n, int tol, unsigned char* base,
                u1u1_strings* out, cudaStream_t st) {
   const size_t V = (size_t)p->nx * p->ny * p->nz;
-  const int nblocks = tiled_measure_blocks(p->nx, p->ny, p->nz, (int)sizeof(T), TILE_WAVES_DEFAULT, true);
+  const int nblocks = wind_grid_blocks(p->nx, p->ny, p->nz);
   const int ncblocks = cells_grid_blocks();
   // carve the scratch: face bytes, cell masks, block partials, cell partials,
   // census counters, record
@@ -76,28 +114,21 @@ int run_detect(const u1u1_params* p, const void* const fields[U1U1_NFIELDS], int
   // cell pass clears the census counters with a memset), so nothing needs
   // clearing here
 
-  LatticeView<T> v;
-  for (int f = 0; f < U1U1_NPOS; ++f) {
-    v.pin[f] = (const T*)fields[f];
-    v.pout[f] = (T*)fields[f];  // a measuring pass writes no field
-  }
-  for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = (T*)fields[U1U1_NPOS + f];
+  // the windings read only the ten position fields
+  PosView<T> v;
+  for (int f = 0; f < U1U1_NPOS; ++f) v.pos[f] = (const T*)fields[f];
   v.nx = p->nx;
   v.ny = p->ny;
   v.nz = p->nz;
-  const Coef<T> c = make_coef<T>(p, n);
-  MeasureOut mo{part, faces, nullptr};
-  cudaError_t e = launch_tiled<T>(MODE_MEASURE, v, c, mo, st);
-  if (e != cudaSuccess) return cuda_fail(e, "detect kernel");
+  cudaError_t e = launch_windings<T>(v, (T)p->dx, part, faces, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e, "windings kernel");
   e = launch_cells(faces, p->nx, p->ny, p->nz, tol, nullptr, nullptr, masks, cpart, st, nullptr, ge4);
   if (e != cudaSuccess) return cuda_fail(e, "cell overlap kernel");
-  e = launch_finalize(part, nblocks, cpart, ncblocks, rec, (long long)n, 1, 0, 1, tol, st, ge4);
+  e = launch_finalize(part, nblocks, cpart, ncblocks, rec, (long long)n, 0, 0, 1, tol, st, ge4);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   RawRecord r;
   U1U1_CUDA_TRY(cudaMemcpyAsync(&r, rec, sizeof(RawRecord), cudaMemcpyDeviceToHost, st), "record copy");
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
-  if (tma_timeout_flag(true, st))
-    return fail(U1U1_ERR_TIMEOUT, "a tiled kernel's wait for a tensor copy into shared memory ran out (2 s)");
   to_strings(p, r, out);
   return U1U1_OK;
 }

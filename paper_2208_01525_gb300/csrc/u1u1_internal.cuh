@@ -90,6 +90,8 @@ struct TmaPlan {
   int enabled;
   unsigned extra_bytes;  // failure-detection test hook: 0 in normal runs
   long long limit_ns;    // limit of a wait for a slot's copies (2 s)
+  int* status;           // device word of the launching handle (or ensemble):
+                         // set to U1U1_ERR_TIMEOUT when a wait ran out
 };
 template <typename T>
 void make_tma_plan(const T* const pin[U1U1_NPOS], int nx, int ny, int nz, TmaPlan* tp);
@@ -137,10 +139,6 @@ cudaError_t launch_simple(int mode, const LatticeView<T>& v, const Coef<T>& c, c
 // A measuring launch (MODE_MEASURE) with mo.faces set also runs the windings
 // kernel on v.pin, whose block partials follow the step kernel's.
 constexpr int TILE_WAVES_DEFAULT = 32;
-// Nonzero when a tiled kernel's wait for a tensor copy into shared memory ran
-// out of time (the kernel then finished on stale data); `clear` resets it.
-// Read in the order of stream `st`, which it synchronises.
-int tma_timeout_flag(bool clear, cudaStream_t st);
 // Test hook: make every tensor-copy wait of the single-lattice kernels run
 // out (enable) after limit_ns, or restore normal copies; the limit applies to
 // launches enqueued from then on either way.
@@ -148,9 +146,12 @@ int tma_inject_timeout(int enable, long long limit_ns);
 int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves = TILE_WAVES_DEFAULT);
 // block partials a tiled measuring launch writes (with or without windings)
 int tiled_measure_blocks(int nx, int ny, int nz, int sizeof_t, int waves, bool windings);
+// status: the caller's device status word, which a kernel whose wait for a
+// tensor copy into shared memory ran out sets to U1U1_ERR_TIMEOUT (the kernel
+// then finishes on stale data); required.
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,
-                         cudaStream_t st, int waves = TILE_WAVES_DEFAULT);
+                         cudaStream_t st, int waves, int* status);
 
 // Windings kernel (k_wind.cu): face bytes, optional int8 windings and one
 // block partial (counts only) per block.

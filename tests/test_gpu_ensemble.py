@@ -1,26 +1,36 @@
 """Batched ensembles of independent boxes of uneven size: every box advanced
-in an ensemble run equals the same box advanced alone by the single-lattice
-tiled kernel, bit for bit, in all three scheduling modes and through CUDA
-graph replays; the persistent kernel's bounded dependency wait turns an
-unreachable wait into a reported timeout."""
+in an ensemble run matches the FP64 oracle stepped from the same initial
+conditions (FP64 within 1e-10, FP32 within the field max-rel 1e-5) and equals
+the same box advanced alone by the single-lattice tiled kernel, bit for bit,
+in all three scheduling modes and through CUDA graph replays; the persistent
+kernel's bounded dependency wait turns an unreachable wait into a reported
+timeout."""
 import numpy as np
 import pytest
 
+import oracle as O
 import paper_2208_01525_gb300 as U
+from gpu_helpers import field_maxrel, host_state, to_oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def box_params(prec=U.FP32):
-    """Uneven boxes, eras, beta and seeds (ragged tiles in x, y and z)."""
+# unequal sector couplings (Sec. VI) for the odd boxes of the oracle test
+UNEQUAL = dict(lambda_p=2.0, lambda_q=1.62, e_p=1.0, e_q=0.9, sigma_p=1.0, sigma_q=0.8, kappa=0.5)
+
+
+def box_params(prec=U.FP32, unequal_odd=False):
+    """Uneven boxes, eras, beta and seeds (ragged tiles in x, y and z);
+    with unequal_odd, the odd boxes take unequal sector couplings."""
     shapes = [(16, 16, 16), (24, 20, 12), (32, 8, 40), (8, 12, 4), (40, 24, 33), (12, 12, 12)]
     out = []
     for b, (nx, ny, nz) in enumerate(shapes):
         m = (0.5, 2.0 / 3.0)[b % 2]
         beta = (1.0, 0.0, -1.0)[b % 3]
+        kw = UNEQUAL if unequal_odd and b % 2 else {}
         out.append(U.Params(nx=nx, ny=ny, nz=nz, m=m, beta=beta, eta0=1.0,
-                            eta_ref=3.0 if beta > 0 else 1.0, seed=1000 + b, precision=prec))
+                            eta_ref=3.0 if beta > 0 else 1.0, seed=1000 + b, precision=prec, **kw))
     return out
 
 
@@ -41,6 +51,34 @@ def test_ensemble_matches_single_boxes(mode, prec):
     for b, p in enumerate(ps):
         assert ens.boxes[b].n == steps[b]
         assert torch.equal(ens.boxes[b].state(), alone(p, steps[b])), b
+    ens.close()
+
+
+@pytest.mark.parametrize("mode,graph", [(U.ENS_PERSISTENT, False), (U.ENS_PERSISTENT, True),
+                                        (U.ENS_PER_STEP, False), (U.ENS_PER_STEP, True),
+                                        (U.ENS_UNBATCHED, False)])
+@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-10), (U.FP32, 1e-5)])
+def test_ensemble_boxes_match_oracle(mode, graph, prec, tol):
+    """Every box of an ensemble run against the FP64 oracle stepped from the
+    box's own initial conditions (per-box seed, era, beta, couplings, size):
+    FP64 within 1e-10, FP32 within the field max-rel 1e-5.  Half the boxes
+    carry unequal sector couplings; graph runs are captured once and
+    replayed, so each box takes twice its step count."""
+    ps = box_params(prec, unequal_odd=True)
+    steps = [10, 7, 9, 0, 5, 8]
+    reps = 2 if graph else 1
+    ens = U.Ensemble(ps)
+    for _ in range(reps):
+        ens.run(steps, mode=mode, use_graph=graph)
+    torch.cuda.synchronize()
+    assert ens.status() == 0
+    for b, p in enumerate(ps):
+        assert ens.boxes[b].n == reps * steps[b]
+        op = to_oracle(p)
+        ref = O.init(op)
+        O.step(op, ref, 0, reps * steps[b])
+        err = field_maxrel(host_state(ens.boxes[b]), ref)
+        assert err.max() <= tol, (b, err)
     ens.close()
 
 

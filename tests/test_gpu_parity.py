@@ -21,6 +21,12 @@ torch = pytest.importorskip("torch")
 
 KERNELS = [U.KERNEL_SIMPLE, U.KERNEL_AUTO]
 
+# Unequal sector couplings (the unequal-tension case of Sec. VI): every
+# per-sector coefficient of the step and of the diagnostics differs between
+# p and q, so a p/q mix-up in any kernel changes the result.
+UNEQUAL = dict(lambda_p=2.0, lambda_q=1.62, e_p=1.0, e_q=0.9, sigma_p=1.0, sigma_q=0.8, kappa=0.5)
+COUPLINGS = {"equal": {}, "unequal": UNEQUAL}
+
 
 def radiation(n, nsteps, **kw):
     """The 64^3-style configuration: dx 0.5, deta 0.1, radiation, beta = 1,
@@ -45,10 +51,12 @@ def test_initial_conditions_match_oracle(prec):
     assert other == 0.0
 
 
+@pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_fp64_matches_oracle_full_run(kernel):
-    """64^3, 160 steps to eta = 17 (radiation, beta = 1), FP64 vs oracle."""
-    p = radiation(64, 160, precision=U.FP64, seed=1)
+def test_fp64_matches_oracle_full_run(kernel, couplings):
+    """64^3, 160 steps to eta = 17 (radiation, beta = 1), FP64 vs oracle,
+    with equal couplings and with every per-sector coupling different."""
+    p = radiation(64, 160, precision=U.FP64, seed=1, **COUPLINGS[couplings])
     lat = U.Lattice(p, kernel=kernel)
     lat.step(160)
     ref = O.init(to_oracle(p))
@@ -73,12 +81,32 @@ def test_fp64_ragged_boxes_all_eras(kernel, shape, cfg):
     assert err.max() < 1e-11, err
 
 
+@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-11), (U.FP32, 1e-5)])
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("cfg", [dict(m=2.0 / 3.0, beta=0.0), dict(m=0.5, beta=-1.0, eta_ref=1.0),
+                                 dict(m=0.0, beta=1.0)])
+def test_unequal_couplings_ragged_boxes(prec, tol, kernel, cfg):
+    """Unequal couplings in both sectors on a ragged box from a rough state
+    (momenta and links of every sign), in every era: FP64 within 1e-11 and
+    FP32 within the field max-rel 1e-5 of the oracle after 12 steps."""
+    p = radiation((36, 20, 12), 12, precision=prec, seed=5, **cfg, **UNEQUAL)
+    lat = U.Lattice(p, kernel=kernel)
+    st0 = synth.random_state(p.shape, seed=19, a_amp=1.0, mom_amp=0.5)
+    lat.set_state(st0, n=3)
+    lat.step(12)
+    ref = st0.copy()
+    O.step(to_oracle(p), ref, 3, 12)
+    err = field_maxrel(host_state(lat), ref)
+    assert err.max() <= tol, err
+
+
+@pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("cfg", [dict(m=0.5, beta=1.0), dict(m=2.0 / 3.0, beta=0.0),
                                  dict(m=0.5, beta=-1.0, eta_ref=1.0)])
-def test_fp32_matches_oracle_20_steps(kernel, cfg):
+def test_fp32_matches_oracle_20_steps(kernel, cfg, couplings):
     """FP32 bulk vs FP64 oracle: field max-rel <= 1e-5 after 20 steps."""
-    p = radiation(64, 640, precision=U.FP32, seed=2, **cfg)
+    p = radiation(64, 640, precision=U.FP32, seed=2, **cfg, **COUPLINGS[couplings])
     lat = U.Lattice(p, kernel=kernel)
     lat.step(20)
     ref = O.init(to_oracle(p))
@@ -134,19 +162,29 @@ def test_copy_wait_timeout_is_reported():
     """The tiled kernels' waits for their tensor copies are bounded: with the
     test hook making every slot expect more bytes than its copies deliver,
     the waits run out after 50 ms, the step finishes, and the next
-    synchronising call reports TIMEOUT (once).  With the hook off, the same
-    box steps normally again and matches the oracle."""
+    synchronising call of the handle that launched it reports TIMEOUT
+    (once).  Another handle, synchronised in between, reports nothing: each
+    handle has its own status word.  With the hook off, the same box steps
+    normally again and matches the oracle."""
     p = U.Params(nx=136, ny=40, nz=24, m=0.5, beta=1.0, eta0=1.0, eta_ref=65.0, seed=12, precision=U.FP32)
     lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+    other = U.Lattice(p, kernel=U.KERNEL_TILED)
+    other.step(2)
     U.check(U.lib().u1u1_inject_copy_timeout(1, 50_000_000))
     try:
         lat.step(2)
+        torch.cuda.synchronize()
+        # the untouched handle synchronises first and sees no timeout
+        assert other.read_records() == ([], 0)
+        other.detect_strings()
+        other.diagnostics()
         with pytest.raises(U.U1U1Error) as ei:
             lat.read_records()
         assert ei.value.code == -5 and "tensor copy" in str(ei.value)  # TIMEOUT
     finally:
         U.check(U.lib().u1u1_inject_copy_timeout(0, 2_000_000_000))
     lat.read_records()  # reported once
+    other.close()
     lat.close()
     lat = U.Lattice(p, kernel=U.KERNEL_TILED)
     lat.step(6)
@@ -157,10 +195,11 @@ def test_copy_wait_timeout_is_reported():
     assert err.max() <= 1e-5, err
 
 
+@pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("prec", [U.FP32, U.FP64])
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_windings_bit_exact_on_snapshot(prec, kernel):
-    p = radiation(64, 640, precision=prec, seed=3)
+def test_windings_bit_exact_on_snapshot(prec, kernel, couplings):
+    p = radiation(64, 640, precision=prec, seed=3, **COUPLINGS[couplings])
     lat = U.Lattice(p, kernel=kernel)
     lat.step(30)
     res, ores, nflag = _windings_compare(p, lat)
@@ -296,10 +335,11 @@ def test_planted_vortices_detected():
         assert int(r0["cells"][0].sum().item()) == 2 * 4 * nz
 
 
+@pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-10), (U.FP32, 2e-5)])
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_diagnostics_match_oracle(prec, tol, kernel):
-    p = radiation((32, 24, 16), 100, precision=prec, seed=6)
+def test_diagnostics_match_oracle(prec, tol, kernel, couplings):
+    p = radiation((32, 24, 16), 100, precision=prec, seed=6, **COUPLINGS[couplings])
     lat = U.Lattice(p, kernel=kernel)
     lat.step(25)
     d = lat.diagnostics()
@@ -313,6 +353,8 @@ def test_diagnostics_match_oracle(prec, tol, kernel):
         if k.startswith("r"):
             s = max(abs(od["rl_den"]), abs(od["rl_num"]), abs(ref))
         assert abs(d[k] - ref) <= tol * s, (k, d[k], ref)
+    for k in ("lag_p", "lag_q"):
+        assert abs(d[k] - od[k]) <= tol * p.dx ** 3 * scale, (k, d[k], od[k])
     for k in ("xi_l", "xi_l_p", "xi_l_q", "v2_l", "v2_pq"):
         if math.isnan(od[k]):  # xi_L is undefined while the Lagrangian sum is positive
             assert math.isnan(d[k]), k
@@ -340,11 +382,12 @@ def test_gauss_law_preserved(prec):
             assert d["gauss_max_" + sec] < bound, (lat.n, sec, d["gauss_max_" + sec])
 
 
+@pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_fused_detection_equals_standalone(kernel):
+def test_fused_detection_equals_standalone(kernel, couplings):
     """A step fused with detection records exactly what the standalone
     detection and diagnostics report on the same input state."""
-    p = radiation(40, 400, precision=U.FP32, seed=10)
+    p = radiation(40, 400, precision=U.FP32, seed=10, **COUPLINGS[couplings])
     a = U.Lattice(p, kernel=kernel)
     b = U.Lattice(p, kernel=kernel)
     a.step(16)

@@ -1,0 +1,109 @@
+"""Precision of the FP32 path, stated per result (Sec. III.A, Eqs. 31-37).
+
+Two claims are checked here:
+
+* After a full run of the 64^3 configuration (160 steps to eta = 17,
+  radiation, beta = 1) the FP32 GPU path still reports every diagnostic and
+  every string estimator within 1e-3 of the FP64 oracle run from the same
+  initial conditions (measured: within 2e-6), and the FP64 GPU path within
+  1e-10.
+* The FP32 global sums are summed, not just computed, accurately: on one
+  full-size 512^3 snapshot, loaded once into an FP32 lattice and, widened
+  exactly, into an FP64 lattice, every sum of the FP32 measuring pass agrees
+  with the FP64 pass within 1e-6 relative (the sign-changing Lagrangian and
+  the potential, which cancel, relative to the energy scale), and the string
+  counts differ by no more than the plaquettes flagged within 1e-4 of the
+  branch cut.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2208_01525_gb300 as U
+from gpu_helpers import field_maxrel, host_state, to_oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# every diagnostic of Eqs. 33, 36-37 and the lattice sums behind them
+DIAG = ("energy", "lag", "kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q", "pot", "vint",
+        "lag_p", "lag_q", "xi_l", "xi_l_p", "xi_l_q", "R_l", "v2_l", "R_pq", "v2_pq")
+# the string-length estimators of Eqs. 31-35
+STRINGS = ("L_p", "L_q", "L_pq", "xi_p", "xi_q", "xi_pq", "xi_w", "f_total", "f_p")
+
+
+def rel(a, b):
+    if math.isnan(b):
+        return 0.0 if math.isnan(a) else math.inf
+    if math.isinf(b):
+        return 0.0 if a == b else math.inf
+    return abs(a - b) / abs(b) if b != 0 else abs(a)
+
+
+@pytest.mark.parametrize("prec,tol", [(U.FP32, 1e-3), (U.FP64, 1e-10)])
+def test_full_run_diagnostics_against_oracle(prec, tol):
+    """64^3, dx 0.5, deta 0.1, radiation, beta = 1, kappa 0.9, 160 steps:
+    diagnostics and string estimators every 40 steps and after the full
+    run, against the oracle on its own FP64 trajectory."""
+    p = U.Params.cube(64, m=0.5, beta=1.0, eta0=1.0, eta_ref=17.0, seed=1, precision=prec)
+    op = to_oracle(p)
+    lat = U.Lattice(p)
+    ref = O.init(op)
+    for n in (40, 80, 120, 160):
+        lat.step(40)
+        O.step(op, ref, n - 40, 40)
+    err = field_maxrel(host_state(lat), ref)
+    assert err.max() <= (1e-4 if prec == U.FP32 else 1e-10), err  # measured 4.4e-6 in FP32
+    d = lat.diagnostics()
+    od = O.diagnostics(op, ref, 160)
+    for k in DIAG:
+        assert rel(d[k], od[k]) <= tol, (k, d[k], od[k])
+    s = lat.detect_strings(tol=1)
+    os_ = O.strings(op, ref, tol=1)
+    for k in STRINGS:
+        assert rel(s[k], os_[k]) <= tol, (k, s[k], os_[k])
+    for k in ("n_p", "n_q", "n_pq_cell"):
+        assert abs(s[k] - os_[k]) <= tol * os_[k] + max(s["n_flagged"], os_["n_flagged"]), k
+
+
+def test_fp32_sums_match_fp64_summation_512():
+    """The same 512^3 snapshot (40 FP32 steps of the radiation beta = 1
+    network from random phases) in an FP32 and, widened exactly, in an FP64
+    lattice: the FP32 measuring pass's compensated sums against the FP64
+    pass's over 134 M sites."""
+    free = torch.cuda.mem_get_info()[0]
+    if free < 60e9:
+        pytest.skip("needs ~50 GB of free device memory")
+    kw = dict(m=0.5, beta=1.0, eta0=1.0, eta_ref=129.0, seed=3)
+    p32 = U.Params.cube(512, precision=U.FP32, **kw)
+    p64 = U.Params.cube(512, precision=U.FP64, **kw)
+    a = U.Lattice(p32)
+    a.step(40)
+    b = U.Lattice(p64, init=False)
+    b.set_state(a.state().double(), n=40)
+    torch.cuda.empty_cache()
+    da, db = a.diagnostics(), b.diagnostics()
+    sa, sb = a.detect_strings(tol=1), b.detect_strings(tol=1)
+    scale = abs(db["energy"])
+    for k in ("energy", "kin_p", "kin_q", "grad_p", "grad_q", "el_p", "el_q", "mag_p", "mag_q", "vint",
+              "charge_sum_p", "charge_sum_q", "rl_num", "rl_den", "rpq_num", "rpq_den"):
+        assert abs(da[k] - db[k]) <= 1e-6 * abs(db[k]), (k, da[k], db[k])
+    for k in ("lag", "lag_p", "lag_q", "pot", "pot_p", "pot_q"):
+        assert abs(da[k] - db[k]) <= 1e-6 * scale, (k, da[k], db[k])
+    for k in ("R_l", "v2_l", "R_pq", "v2_pq", "xi_l_p", "xi_l_q"):
+        assert rel(da[k], db[k]) <= 1e-6, (k, da[k], db[k])
+    for k in ("phi_min_p", "phi_max_p", "phi_min_q", "phi_max_q"):
+        assert abs(da[k] - db[k]) <= 1e-6 * abs(db[k]), k
+    # the Gauss residual is a rounding-level quantity: bounded, not compared
+    for sec in "pq":
+        assert da["gauss_max_" + sec] <= 1e-4 and db["gauss_max_" + sec] <= 1e-4
+    flagged = max(sa["n_flagged"], sb["n_flagged"])
+    assert 0 < flagged < 1e-3 * sb["n_p"]
+    for k in ("n_p", "n_q", "n_pq_plaq", "nonzero_p", "nonzero_q"):
+        assert abs(sa[k] - sb[k]) <= flagged, (k, sa[k], sb[k])
+    for k in ("n_pq_cell", "n_pq_cell_q"):  # a flagged plaquette touches two cells, each 27 neighbourhoods
+        assert abs(sa[k] - sb[k]) <= 54 * flagged, (k, sa[k], sb[k])
+    for k in ("xi_p", "xi_q", "xi_pq", "xi_w", "f_total", "f_p"):
+        assert rel(sa[k], sb[k]) <= 1e-5, (k, sa[k], sb[k])

@@ -50,10 +50,33 @@ def test_noalloc_detection_matches_handle_twice(prec):
     for tol in (1, 0):
         ref = lat.detect_strings(tol=tol)
         first = noalloc(lat, tol)
+        # the second call must not touch the device memory pool: neither the
+        # driver's free-memory figure nor PyTorch's allocator may move
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        stats0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
         second = noalloc(lat, tol)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == stats0
         assert ref["n_p"] > 0
         assert same(first, ref), (first, ref)
         assert same(second, ref), (second, ref)
+
+
+def test_noalloc_rejects_oversized_scratch():
+    """A lattice under the site limit whose scratch does not fit the static
+    array (4 x 2048 x 2048: face bytes plus one cell-mask word per row) is
+    refused before any launch, with the byte count in the message."""
+    p = U.Params(nx=4, ny=2048, nz=2048)
+    assert p.nsites <= 16777216
+    dummy = torch.empty(64, device="cuda")
+    fields = (ctypes.c_void_p * 20)(*([dummy.data_ptr()] * 20))
+    out = _abi.CStrings()
+    rc = U.lib().u1u1_detect_strings_noalloc(ctypes.byref(p.c()), fields, 0, 1, ctypes.byref(out), None)
+    assert rc == -1  # INVALID_ARG
+    msg = U.lib().u1u1_last_error().decode()
+    assert "bytes of scratch" in msg and str(48 << 20) in msg, msg
 
 
 def test_noalloc_rejects_oversized_lattice():
