@@ -136,10 +136,11 @@ def launches_per_period(n, de, tiled):
     return de + (1 if tiled else 0) + 2 + 1 + stage
 
 
-def workload_params(U, n, precision, beta=1.0, seed=2024):
-    # 2560 steps to eta = 257 for the 1024^3 box; a = 1 at the end of the run
-    return U.Params.cube(n, m=0.5, beta=beta, eta0=1.0, eta_ref=1.0 + 0.1 * 2560, seed=seed,
-                         precision=precision)
+def workload_params(U, n, precision, beta=1.0, seed=2024, nz=0):
+    # 2560 steps to eta = 257 for the 1024^3 box; a = 1 at the end of the run.
+    # nz > 0: an n x n x nz slab of the same workload (small profiling cases)
+    return U.Params(nx=n, ny=n, nz=nz if nz > 0 else n, m=0.5, beta=beta, eta0=1.0, eta_ref=1.0 + 0.1 * 2560,
+                    seed=seed, precision=precision)
 
 
 class ClockSampler:
@@ -289,6 +290,31 @@ def ensemble_bench(U, torch, dev):
         out[name] = {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": status}
     out["speedup_vs_unbatched"] = out["persistent_graph"]["site_updates_per_s"] / \
         out["unbatched"]["site_updates_per_s"]
+    # the same runs with detection every 16 steps inside the run (windings,
+    # cells, overlap and diagnostic sums of every box, records in each box's
+    # ring); batched modes detect all boxes of a run step in one launch per pass
+    det = {"detect_every": 16}
+    for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True),
+                              ("per_step_graph", U.ENS_PER_STEP, True),
+                              ("unbatched", U.ENS_UNBATCHED, False)):
+        ens = U.Ensemble(ps, device=dev, horizon=2048)
+        ens.run(steps, mode=mode, use_graph=graph, detect_every=16)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.run(steps, mode=mode, use_graph=graph, detect_every=16)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        status = ens.status()
+        nrec = sum(len(bx.read_records(max_records=1024)[0]) for bx in ens.boxes)
+        ens.close()
+        del ens
+        torch.cuda.empty_cache()
+        det[name] = {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": status, "records": nrec}
+    det["speedup_vs_unbatched"] = det["persistent_graph"]["site_updates_per_s"] / \
+        det["unbatched"]["site_updates_per_s"]
+    out["with_detection"] = det
     # the small-box class alone (16 x 64^3), where per-box launches cannot fill the GPU
     small = [p for p, n in zip(ps, sizes) if n == 64]
     ssteps = [s_ for s_, n in zip(steps, sizes) if n == 64]
@@ -332,7 +358,7 @@ def run_ours(args):
     prec = U.FP64 if args.precision == "fp64" else U.FP32
     tag = "fp64" if prec == U.FP64 else "fp32"
     # independent realisations per rank (replicas: the path has no exchange step)
-    p = workload_params(U, n, prec, seed=2024 + rank)
+    p = workload_params(U, n, prec, seed=2024 + rank, nz=args.nz)
     lat = U.Lattice(p, device=dev, kernel=args.kernel)
     tune = None
     if args.waves > 0:
@@ -539,12 +565,13 @@ def run_ours(args):
                          f"{args.cpu_n}^3, {dt:.1f} s"}
 
     if rank == 0:
+        box = f"{n}^3" if args.nz <= 0 else f"{n}x{n}x{args.nz} slab"
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if tag == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"U(1)xU(1) {n}^3 leapfrog, radiation era, beta=1, detection every {de} "
+            "config": {"workload": f"U(1)xU(1) {box} leapfrog, radiation era, beta=1, detection every {de} "
                                    f"steps (one step = {de} leapfrog steps)",
                        "lattice": n, "dx": 0.5, "deta": 0.1, "detect_every": de,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
@@ -582,6 +609,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--nz", type=int, default=0, help="planes of an n x n x nz slab (default: a cube)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--detect-every", type=int, default=16)
     ap.add_argument("--kernel", type=int, default=0)

@@ -397,18 +397,31 @@ int u1u1_inject_copy_timeout(int enable, int64_t limit_ns);
 int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, const u1u1_buffers* buffers, int horizon,
                          void* stream, u1u1_ensemble** out);
 
-/* Advance box b by steps[b] >= 0 plain leapfrog steps (Eqs. 17-26), all
- * boxes together, scheduled by `mode`.  In U1U1_ENS_PERSISTENT mode one
- * launch of about as many CTAs as fit on the GPU takes (box, step, tile)
- * work items from an ordered ticket counter; an item of step k of a box waits
- * until every item of step k-1 of that box is done (bounded wait: after the
- * limit set by u1u1_ensemble_set_wait_limit the kernel records
- * U1U1_ERR_TIMEOUT, read with u1u1_ensemble_status, and returns).  With
- * use_graph != 0 the work of this (steps, mode) pair is captured once into a
- * CUDA graph and replayed on later calls with the same pair.  Asynchronous
- * on `stream`.  Errors: INVALID_ARG, STATE (step horizon reached, or an
- * earlier run timed out), CUDA. */
-int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int mode, int use_graph, void* stream);
+/* Advance box b by steps[b] >= 0 leapfrog steps (Eqs. 17-26), all boxes
+ * together, scheduled by `mode`.  With detect_every > 0, each step of a box
+ * whose input index n satisfies n % detect_every == 0 is fused with the
+ * detection of that input state, exactly as u1u1_step does for one lattice
+ * (windings, cells, fast overlap with the tolerance of the box's handle as
+ * set when the run is enqueued, and the diagnostic sums of Sec. III.A), and
+ * the record is appended to the box's record ring, read with
+ * u1u1_read_records on the box's handle (u1u1_ensemble_lattice); the
+ * records equal those of the box stepped alone with u1u1_step.  In the
+ * batched modes the detection steps of all boxes at one run step go through
+ * one launch of each pass (measuring step, windings, cells, overlap,
+ * finalize).  In U1U1_ENS_PERSISTENT mode one launch of about as many CTAs
+ * as fit on the GPU takes (box, step, tile) work items from an ordered
+ * ticket counter -- one such launch per stretch of plain steps between
+ * detection steps; an item of step k of a box waits until every item of
+ * step k-1 of that box is done (bounded wait: after the limit set by
+ * u1u1_ensemble_set_wait_limit the kernel records U1U1_ERR_TIMEOUT, read
+ * with u1u1_ensemble_status, and returns).  With use_graph != 0 the work of
+ * this (steps, detect_every, mode) combination, and of each box's step index
+ * modulo detect_every, is captured once into a CUDA graph and replayed on
+ * later calls with the same combination (coefficients, buffers and record
+ * slots come from device tables).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, STATE (step horizon reached, or an earlier run timed
+ * out), CUDA. */
+int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int detect_every, int mode, int use_graph, void* stream);
 
 /* Borrow the handle of box b (for detection, diagnostics, state transfer);
  * it stays owned by the ensemble and valid until u1u1_ensemble_destroy. */

@@ -344,9 +344,12 @@ class Ensemble:
             pos, mom = fields[b]
             self.boxes.append(Lattice(p, device=device, _borrow=(pos, mom, hb, self)))
 
-    def run(self, steps, mode: int = ENS_PERSISTENT, use_graph: bool = False, stream=None):
+    def run(self, steps, mode: int = ENS_PERSISTENT, use_graph: bool = False, detect_every: int = 0, stream=None):
+        """Advance box b by steps[b]; with detect_every > 0 the detection records
+        go to each box's ring (``boxes[b].read_records()``)."""
         arr = (ctypes.c_int * len(self.params))(*[int(s) for s in steps])
-        check(lib().u1u1_ensemble_run(self._h, arr, int(mode), int(bool(use_graph)), _stream_ptr(stream)))
+        check(lib().u1u1_ensemble_run(self._h, arr, int(detect_every), int(mode), int(bool(use_graph)),
+                                      _stream_ptr(stream)))
 
     def autotune(self, probe_steps: int = 4, stream=None) -> dict:
         """Pick the work-item z-chunk and schedule by timing (states unchanged)."""

@@ -133,7 +133,7 @@ PROTOTYPES = {
     "u1u1_eval_edge_phase": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),
     "u1u1_fp64_fma_rate": (ctypes.c_int, [_P(ctypes.c_double), _vp]),
     "u1u1_ensemble_create": (ctypes.c_int, [_P(CParams), ctypes.c_int, _P(CBuffers), ctypes.c_int, _vp, _P(_vp)]),
-    "u1u1_ensemble_run": (ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_int, ctypes.c_int, _vp]),
+    "u1u1_ensemble_run": (ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     "u1u1_ensemble_lattice": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp)]),
     "u1u1_ensemble_status": (ctypes.c_int, [_vp, _P(ctypes.c_int), _vp]),
     "u1u1_ensemble_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),

@@ -40,6 +40,46 @@ struct Schedule {
   }
 };
 
+// One detection step k of a run: the boxes detecting at k and the prefix
+// sums of their work items in each batched pass (offsets into the plan's
+// device arrays).
+struct DetGroup {
+  int k = 0;
+  int nlist = 0;
+  size_t list = 0;                      // ints: box indices
+  size_t pm = 0, pw = 0, pc = 0, po = 0;  // long longs: nlist + 1 prefix sums each
+  long long m_items = 0, w_items = 0, c_items = 0, o_items = 0;
+  bool stage = false;                   // some box has more partials than one finalize CTA takes
+};
+// A launch of plain steps: its schedule view (order, prefix tables) and,
+// for persistent segments, each box's first run step.
+struct PlainLaunch {
+  int k = 0;               // per-step mode: the run step
+  size_t order = 0, steps = 0, kstart = 0;  // ints
+  size_t prefix = 0, step_off = 0;          // long longs
+  int nboxes = 0, smax = 0;
+  long long total = 0;     // items (persistent: all steps of the segment)
+  long long items = 0;     // per-step mode: items of step k
+};
+
+// Device plan of a run with detection every `de` steps: per-step plain
+// launches and detection groups (per-step mode), persistent segments between
+// the detection steps and the same groups (persistent mode).
+struct DetPlan {
+  std::vector<DetGroup> groups;
+  std::vector<PlainLaunch> per_step;   // one per run step
+  std::vector<PlainLaunch> segments;   // groups.size() + 1 persistent segments
+  int* d_int = nullptr;
+  long long* d_ll = nullptr;
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  ~DetPlan() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+    cudaFree(d_int);
+    cudaFree(d_ll);
+  }
+};
+
 }  // namespace
 
 struct u1u1_ensemble {
@@ -64,6 +104,12 @@ struct u1u1_ensemble {
   int item_lz = ENS_LZ;  // z-chunk of a work item (tuning knob)
   std::map<std::vector<int>, std::unique_ptr<Schedule>> schedules;
   cudaStream_t capture_stream = nullptr;
+  // detection inside runs: per-box resources and plans keyed by
+  // (steps, detect_every, each box's step index modulo detect_every)
+  EnsDet* d_det = nullptr;
+  std::vector<EnsDet> hdet;
+  std::vector<long long> shadow_rec;
+  std::map<std::vector<int>, std::unique_ptr<DetPlan>> det_plans;
 };
 
 namespace {
@@ -81,6 +127,7 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
     B.nx = h->p.nx;
     B.ny = h->p.ny;
     B.nz = h->p.nz;
+    B.dx = (T)h->p.dx;
     e->ntiles[b] = ens_tile_grid(B.nx, B.ny, B.nz, &B.gx, &B.gy, &B.lz, &B.gz, e->item_lz);
     B.ntiles = e->ntiles[b];
     B.coef0 = (long long)b * e->horizon;
@@ -100,6 +147,33 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
     for (int k = 0; k < 2; ++k) hb[b].tma[k] = e->d_tma + 2 * b + k;
   if (!e->d_boxes) U1U1_CUDA_TRY(cudaMalloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_boxes, hb.data(), sizeof(EnsBox<T>) * nb, cudaMemcpyHostToDevice), "box table copy");
+  // detection resources: each box's own handle scratch, and the grids of a
+  // single lattice's measuring and windings passes of its shape
+  e->hdet.assign(nb, EnsDet{});
+  for (int b = 0; b < nb; ++b) {
+    u1u1_lattice* h = e->boxes[b];
+    EnsDet& D = e->hdet[b];
+    D.part = h->partials;
+    D.faces = h->faces;
+    D.masks = h->masks;
+    D.counts = h->cpartials;
+    D.ge4 = h->ge4;
+    D.ring = h->ring;
+    tiled_grid_dims(h->p.nx, h->p.ny, h->p.nz, (int)sizeof(T), TILE_WAVES_DEFAULT, &D.mgx, &D.mgy, &D.mgz, &D.mlz);
+    wind_grid_dims(h->p.nx, h->p.ny, h->p.nz, &D.wtx, &D.wty, &D.wtz, &D.wlz);
+    D.nmeas = D.mgx * D.mgy * D.mgz;
+    D.nwind = D.wtx * D.wty * D.wtz;
+    D.words = (h->p.nx + 31) / 32;
+    D.tol = h->overlap_tol;
+    D.nx = h->p.nx;
+    D.ny = h->p.ny;
+    D.nz = h->p.nz;
+    if (D.nmeas + D.nwind > h->npartials)
+      return fail(U1U1_ERR_STATE, "box %d: detection partials exceed the handle's buffer", b);
+  }
+  if (!e->d_det) U1U1_CUDA_TRY(cudaMalloc((void**)&e->d_det, sizeof(EnsDet) * nb), "detection table");
+  U1U1_CUDA_TRY(cudaMemcpy(e->d_det, e->hdet.data(), sizeof(EnsDet) * nb, cudaMemcpyHostToDevice),
+                "detection table copy");
   if (e->d_coef) return U1U1_OK;  // a re-tiling keeps the coefficient table
   // per-step coefficients of every box up to the horizon
   std::vector<Coef<T>> hc((size_t)nb * e->horizon);
@@ -157,9 +231,10 @@ int make_schedule(u1u1_ensemble* e, const std::vector<int>& steps, Schedule** ou
   return U1U1_OK;
 }
 
-// Enqueue the device work of one run (no host bookkeeping).
+// Enqueue the device work of one run without detection, or the unbatched
+// loop with it (no host bookkeeping).
 template <typename T>
-int enqueue_run(u1u1_ensemble* e, Schedule* s, int mode, cudaStream_t st) {
+int enqueue_run(u1u1_ensemble* e, Schedule* s, int mode, int de, cudaStream_t st) {
   const EnsBox<T>* boxes = (const EnsBox<T>*)e->d_boxes;
   const Coef<T>* coef = (const Coef<T>*)e->d_coef;
   cudaError_t err = cudaSuccess;
@@ -167,8 +242,8 @@ int enqueue_run(u1u1_ensemble* e, Schedule* s, int mode, cudaStream_t st) {
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), st), "ticket reset");
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->nboxes, st), "counter reset");
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_err, 0, sizeof(int), st), "status reset");
-    err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, s->sc, e->d_ticket, e->d_done, e->d_err, e->wait_limit_ns,
-                                   e->inject, st);
+    err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, s->sc, nullptr, e->d_ticket, e->d_done, e->d_err,
+                                   e->wait_limit_ns, e->inject, st);
     if (err != cudaSuccess) return cuda_fail(err, "persistent ensemble kernel");
   } else if (mode == U1U1_ENS_PER_STEP) {
     for (int k = 0; k < s->sc.smax; ++k) {
@@ -178,17 +253,220 @@ int enqueue_run(u1u1_ensemble* e, Schedule* s, int mode, cudaStream_t st) {
   } else {
     // the per-box handles advance their own host bookkeeping here
     for (int b = 0; b < e->nboxes; ++b) {
-      const int rc = u1u1_step(e->boxes[b], s->steps[b], 0, st);
+      const int rc = u1u1_step(e->boxes[b], s->steps[b], de, st);
       if (rc) return rc;
     }
   }
-  err = launch_ens_advance(e->d_dyn, s->d_steps, e->nboxes, st);
+  err = launch_ens_advance(e->d_dyn, s->d_steps, e->nboxes, de, st);
   if (err != cudaSuccess) return cuda_fail(err, "ensemble advance kernel");
   return U1U1_OK;
 }
 
-int enqueue(u1u1_ensemble* e, Schedule* s, int mode, cudaStream_t st) {
-  return e->precision == U1U1_FP64 ? enqueue_run<double>(e, s, mode, st) : enqueue_run<float>(e, s, mode, st);
+int enqueue(u1u1_ensemble* e, Schedule* s, int mode, int de, cudaStream_t st) {
+  return e->precision == U1U1_FP64 ? enqueue_run<double>(e, s, mode, de, st)
+                                   : enqueue_run<float>(e, s, mode, de, st);
+}
+
+// box b, at step index n0 when the run starts, detects at run step k
+bool detects(long long n0, int k, int steps, int de) { return de > 0 && k < steps && (n0 + k) % de == 0; }
+
+// Plan of a run with detection every de steps (host tables, then one upload).
+int make_det_plan(u1u1_ensemble* e, const std::vector<int>& steps, int de, DetPlan** out) {
+  const int nb = e->nboxes;
+  std::vector<int> key(steps);
+  key.push_back(de);
+  std::vector<long long> n0(nb);
+  for (int b = 0; b < nb; ++b) {
+    n0[b] = e->boxes[b]->n;
+    key.push_back((int)(n0[b] % de));
+  }
+  auto it = e->det_plans.find(key);
+  if (it != e->det_plans.end()) {
+    *out = it->second.get();
+    return U1U1_OK;
+  }
+  std::unique_ptr<DetPlan> P(new DetPlan());
+  std::vector<int> ints;
+  std::vector<long long> lls;
+  auto push_ints = [&](const std::vector<int>& v) {
+    const size_t off = ints.size();
+    ints.insert(ints.end(), v.begin(), v.end());
+    if (v.empty()) ints.push_back(0);  // keep every view's offset valid
+    return off;
+  };
+  auto push_prefix = [&](const std::vector<long long>& c) {
+    const size_t off = lls.size();
+    lls.push_back(0);
+    for (long long v : c) lls.push_back(lls.back() + v);
+    return off;
+  };
+  int smax = 0;
+  for (int b = 0; b < nb; ++b) smax = std::max(smax, steps[b]);
+  // detection groups
+  for (int k = 0; k < smax; ++k) {
+    std::vector<int> list;
+    for (int b = 0; b < nb; ++b)
+      if (detects(n0[b], k, steps[b], de)) list.push_back(b);
+    if (list.empty()) continue;
+    DetGroup g;
+    g.k = k;
+    g.nlist = (int)list.size();
+    g.list = push_ints(list);
+    std::vector<long long> m, w, c, o;
+    for (int b : list) {
+      const EnsDet& D = e->hdet[b];
+      const long long words = (long long)D.words * D.ny * D.nz;
+      m.push_back(D.nmeas);
+      w.push_back(D.nwind);
+      c.push_back(words);
+      o.push_back((words + 31) / 32);
+      g.m_items += D.nmeas;
+      g.w_items += D.nwind;
+      g.c_items += words;
+      g.o_items += (words + 31) / 32;
+      if (D.nmeas + D.nwind > FIN_STAGE_MIN) g.stage = true;
+    }
+    g.pm = push_prefix(m);
+    g.pw = push_prefix(w);
+    g.pc = push_prefix(c);
+    g.po = push_prefix(o);
+    P->groups.push_back(g);
+  }
+  // per-step mode: the plain steps of each run step
+  for (int k = 0; k < smax; ++k) {
+    std::vector<int> plain;
+    std::vector<long long> tiles;
+    for (int b = 0; b < nb; ++b)
+      if (k < steps[b] && !detects(n0[b], k, steps[b], de)) {
+        plain.push_back(b);
+        tiles.push_back(e->ntiles[b]);
+      }
+    PlainLaunch L;
+    L.k = k;
+    L.nboxes = (int)plain.size();
+    L.order = push_ints(plain);
+    L.prefix = push_prefix(tiles);
+    for (long long t : tiles) L.items += t;
+    P->per_step.push_back(L);
+  }
+  // persistent mode: segments of plain steps between detection steps; the
+  // boxes that detect at a step start the next segment one step later
+  const int ng = (int)P->groups.size();
+  for (int j = 0; j <= ng; ++j) {
+    std::vector<int> cnt(nb), kst(nb);
+    for (int b = 0; b < nb; ++b) {
+      const int g0 = j == 0 ? 0 : P->groups[j - 1].k;
+      const int start = j == 0 ? 0 : g0 + (detects(n0[b], g0, steps[b], de) ? 1 : 0);
+      const int end = std::min(j < ng ? P->groups[j].k : steps[b], steps[b]);
+      cnt[b] = std::max(0, end - start);
+      kst[b] = start;
+    }
+    std::vector<int> order(nb);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
+    std::vector<long long> tiles(nb);
+    for (int i = 0; i < nb; ++i) tiles[i] = e->ntiles[order[i]];
+    const int sm = nb ? cnt[order[0]] : 0;
+    std::vector<long long> per(sm, 0);
+    int active = nb;
+    for (int k = 0; k < sm; ++k) {
+      while (active > 0 && cnt[order[active - 1]] <= k) --active;
+      for (int i = 0; i < active; ++i) per[k] += e->ntiles[order[i]];
+    }
+    PlainLaunch L;
+    L.order = push_ints(order);
+    L.steps = push_ints(cnt);
+    L.kstart = push_ints(kst);
+    L.prefix = push_prefix(tiles);
+    L.step_off = push_prefix(per);
+    L.nboxes = nb;
+    L.smax = sm;
+    for (long long v : per) L.total += v;
+    P->segments.push_back(L);
+  }
+  U1U1_CUDA_TRY(cudaMalloc((void**)&P->d_int, sizeof(int) * std::max<size_t>(ints.size(), 1)), "detection plan");
+  U1U1_CUDA_TRY(cudaMalloc((void**)&P->d_ll, sizeof(long long) * std::max<size_t>(lls.size(), 1)), "detection plan");
+  U1U1_CUDA_TRY(cudaMemcpy(P->d_int, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice), "plan copy");
+  U1U1_CUDA_TRY(cudaMemcpy(P->d_ll, lls.data(), sizeof(long long) * lls.size(), cudaMemcpyHostToDevice), "plan copy");
+  *out = P.get();
+  e->det_plans[key] = std::move(P);
+  return U1U1_OK;
+}
+
+EnsSched view(const DetPlan* P, const PlainLaunch& L) {
+  EnsSched sc{};
+  sc.order = P->d_int + L.order;
+  sc.steps = P->d_int + L.steps;
+  sc.box_prefix = P->d_ll + L.prefix;
+  sc.step_off = P->d_ll + L.step_off;
+  sc.nboxes = L.nboxes;
+  sc.smax = L.smax;
+  sc.total = L.total;
+  return sc;
+}
+
+// the batched detection of one group: measuring step, windings, cells and
+// overlap, finalize into each box's record ring
+template <typename T>
+int enqueue_group(u1u1_ensemble* e, const DetPlan* P, const DetGroup& g, int de, cudaStream_t st) {
+  const EnsBox<T>* boxes = (const EnsBox<T>*)e->d_boxes;
+  const Coef<T>* coef = (const Coef<T>*)e->d_coef;
+  const int* list = P->d_int + g.list;
+  cudaError_t err = launch_ens_measure<T>(boxes, e->d_det, e->d_dyn, coef, list, P->d_ll + g.pm, g.nlist, g.m_items,
+                                          g.k, st);
+  if (err != cudaSuccess) return cuda_fail(err, "ensemble measuring step");
+  err = launch_ens_windings<T>(boxes, e->d_det, e->d_dyn, list, P->d_ll + g.pw, g.nlist, g.w_items, g.k, st);
+  if (err != cudaSuccess) return cuda_fail(err, "ensemble windings");
+  err = launch_ens_cells(e->d_det, list, P->d_ll + g.pc, P->d_ll + g.po, g.nlist, g.c_items, g.o_items, st);
+  if (err != cudaSuccess) return cuda_fail(err, "ensemble cells and overlap");
+  err = launch_ens_finalize(e->d_det, e->d_dyn, list, g.nlist, g.k, de, g.stage, st);
+  if (err != cudaSuccess) return cuda_fail(err, "ensemble finalize");
+  return U1U1_OK;
+}
+
+// Enqueue the device work of one batched run with detection.
+template <typename T>
+int enqueue_det_run(u1u1_ensemble* e, Schedule* s, DetPlan* P, int mode, int de, cudaStream_t st) {
+  const EnsBox<T>* boxes = (const EnsBox<T>*)e->d_boxes;
+  const Coef<T>* coef = (const Coef<T>*)e->d_coef;
+  cudaError_t err = cudaSuccess;
+  if (mode == U1U1_ENS_PERSISTENT) {
+    U1U1_CUDA_TRY(cudaMemsetAsync(e->d_err, 0, sizeof(int), st), "status reset");
+    for (size_t j = 0; j < P->segments.size(); ++j) {
+      const PlainLaunch& L = P->segments[j];
+      if (L.total > 0) {
+        U1U1_CUDA_TRY(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), st), "ticket reset");
+        U1U1_CUDA_TRY(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->nboxes, st), "counter reset");
+        err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, view(P, L), P->d_int + L.kstart, e->d_ticket,
+                                       e->d_done, e->d_err, e->wait_limit_ns, e->inject, st);
+        if (err != cudaSuccess) return cuda_fail(err, "persistent ensemble kernel");
+      }
+      if (j < P->groups.size()) {
+        const int rc = enqueue_group<T>(e, P, P->groups[j], de, st);
+        if (rc) return rc;
+      }
+    }
+  } else {
+    size_t gi = 0;
+    for (const PlainLaunch& L : P->per_step) {
+      if (L.items > 0) {
+        err = launch_ens_step<T>(boxes, e->d_dyn, coef, view(P, L), L.k, L.items, st);
+        if (err != cudaSuccess) return cuda_fail(err, "ensemble step kernel");
+      }
+      if (gi < P->groups.size() && P->groups[gi].k == L.k) {
+        const int rc = enqueue_group<T>(e, P, P->groups[gi++], de, st);
+        if (rc) return rc;
+      }
+    }
+  }
+  err = launch_ens_advance(e->d_dyn, s->d_steps, e->nboxes, de, st);
+  if (err != cudaSuccess) return cuda_fail(err, "ensemble advance kernel");
+  return U1U1_OK;
+}
+
+int enqueue_det(u1u1_ensemble* e, Schedule* s, DetPlan* P, int mode, int de, cudaStream_t st) {
+  return e->precision == U1U1_FP64 ? enqueue_det_run<double>(e, s, P, mode, de, st)
+                                   : enqueue_det_run<float>(e, s, P, mode, de, st);
 }
 
 // bring the device step table in line with the per-box handles (a box may
@@ -196,15 +474,19 @@ int enqueue(u1u1_ensemble* e, Schedule* s, int mode, cudaStream_t st) {
 int sync_dyn(u1u1_ensemble* e, cudaStream_t st) {
   bool stale = false;
   for (int b = 0; b < e->nboxes; ++b)
-    if (e->boxes[b]->n != e->shadow_n[b] || e->boxes[b]->cur != e->shadow_cur[b]) stale = true;
+    if (e->boxes[b]->n != e->shadow_n[b] || e->boxes[b]->cur != e->shadow_cur[b] ||
+        e->boxes[b]->rec_written != e->shadow_rec[b])
+      stale = true;
   if (!stale) return U1U1_OK;
   std::vector<EnsDyn> hd(e->nboxes);
   for (int b = 0; b < e->nboxes; ++b) {
     hd[b].n = e->boxes[b]->n;
+    hd[b].rec = e->boxes[b]->rec_written;
     hd[b].cur = e->boxes[b]->cur;
     hd[b].pad = 0;
     e->shadow_n[b] = hd[b].n;
     e->shadow_cur[b] = hd[b].cur;
+    e->shadow_rec[b] = hd[b].rec;
   }
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_dyn, hd.data(), sizeof(EnsDyn) * e->nboxes, cudaMemcpyHostToDevice), "step table");
@@ -216,6 +498,7 @@ int sync_dyn(u1u1_ensemble* e, cudaStream_t st) {
 extern "C" void u1u1_ensemble_destroy(u1u1_ensemble* e) {
   if (!e) return;
   e->schedules.clear();
+  e->det_plans.clear();
   for (u1u1_lattice* h : e->boxes) u1u1_destroy(h);
   cudaFree(e->d_boxes);
   cudaFree(e->d_tma);
@@ -224,6 +507,7 @@ extern "C" void u1u1_ensemble_destroy(u1u1_ensemble* e) {
   cudaFree(e->d_ticket);
   cudaFree(e->d_done);
   cudaFree(e->d_err);
+  cudaFree(e->d_det);
   if (e->capture_stream) cudaStreamDestroy(e->capture_stream);
   delete e;
 }
@@ -244,6 +528,7 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
   e->ntiles.assign(nboxes, 0);
   e->shadow_n.assign(nboxes, 0);
   e->shadow_cur.assign(nboxes, 0);
+  e->shadow_rec.assign(nboxes, 0);
   for (int b = 0; b < nboxes; ++b) {
     u1u1_lattice* h = nullptr;
     int rc = u1u1_init_lattice(&per_box[b], &buffers[b], stream, &h);
@@ -276,9 +561,12 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
   return U1U1_OK;
 }
 
-extern "C" int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int mode, int use_graph, void* stream) {
+extern "C" int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int detect_every, int mode, int use_graph,
+                                 void* stream) {
   if (!e || !steps) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
   if (mode < U1U1_ENS_PERSISTENT || mode > U1U1_ENS_UNBATCHED) return fail(U1U1_ERR_INVALID_ARG, "unknown mode %d", mode);
+  if (detect_every < 0) return fail(U1U1_ERR_INVALID_ARG, "detect_every must be >= 0");
+  const int de = detect_every;
   if (e->poisoned) return fail(U1U1_ERR_STATE, "an earlier persistent run timed out; the ensemble state is incomplete");
   std::vector<int> sv(steps, steps + e->nboxes);
   for (int b = 0; b < e->nboxes; ++b) {
@@ -293,21 +581,41 @@ extern "C" int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int mode, i
     return fail(U1U1_ERR_NOT_SUPPORTED,
                 "the unbatched loop bakes each box's buffers and coefficients into its launches; run it without a graph");
   cudaStream_t st = (cudaStream_t)stream;
+  if (de > 0) {
+    // the overlap tolerance of each box's handle, as set when the run is enqueued
+    bool changed = false;
+    for (int b = 0; b < e->nboxes; ++b)
+      if (e->hdet[b].tol != e->boxes[b]->overlap_tol) {
+        e->hdet[b].tol = e->boxes[b]->overlap_tol;
+        changed = true;
+      }
+    if (changed) {
+      U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+      U1U1_CUDA_TRY(cudaMemcpy(e->d_det, e->hdet.data(), sizeof(EnsDet) * e->nboxes, cudaMemcpyHostToDevice),
+                    "detection table copy");
+    }
+  }
   int rc = sync_dyn(e, st);
   if (rc) return rc;
   Schedule* s = nullptr;
   rc = make_schedule(e, sv, &s);
   if (rc) return rc;
+  DetPlan* P = nullptr;
+  if (de > 0 && mode != U1U1_ENS_UNBATCHED) {
+    rc = make_det_plan(e, sv, de, &P);
+    if (rc) return rc;
+  }
+  auto run_on = [&](cudaStream_t q) { return P ? enqueue_det(e, s, P, mode, de, q) : enqueue(e, s, mode, de, q); };
   if (!use_graph) {
-    rc = enqueue(e, s, mode, st);
+    rc = run_on(st);
     if (rc) return rc;
   } else {
-    cudaGraphExec_t& g = s->graph[mode];
+    cudaGraphExec_t& g = P ? P->graph[mode] : s->graph[mode];
     if (!g) {
       // capture on a private stream so the caller's stream may be the legacy one
       cudaGraph_t graph = nullptr;
       U1U1_CUDA_TRY(cudaStreamBeginCapture(e->capture_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-      int crc = enqueue(e, s, mode, e->capture_stream);
+      int crc = run_on(e->capture_stream);
       cudaError_t ce = cudaStreamEndCapture(e->capture_stream, &graph);
       if (crc) {
         if (graph) cudaGraphDestroy(graph);
@@ -325,13 +633,19 @@ extern "C" int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int mode, i
   }
   if (mode != U1U1_ENS_UNBATCHED) {
     for (int b = 0; b < e->nboxes; ++b) {
-      e->boxes[b]->n += sv[b];
-      e->boxes[b]->cur ^= (sv[b] & 1);
+      u1u1_lattice* h = e->boxes[b];
+      if (de > 0) {  // records appended to the box's ring by the batched detection
+        const long long k1 = (de - h->n % de) % de;
+        if (sv[b] > k1) h->rec_written += (sv[b] - 1 - k1) / de + 1;
+      }
+      h->n += sv[b];
+      h->cur ^= (sv[b] & 1);
     }
   }
   for (int b = 0; b < e->nboxes; ++b) {
     e->shadow_n[b] = e->boxes[b]->n;
     e->shadow_cur[b] = e->boxes[b]->cur;
+    e->shadow_rec[b] = e->boxes[b]->rec_written;
   }
   return U1U1_OK;
 }
@@ -365,6 +679,7 @@ extern "C" int u1u1_ensemble_set_wait_limit(u1u1_ensemble* e, int64_t ns) {
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
+  e->det_plans.clear();
   return U1U1_OK;
 }
 
@@ -377,6 +692,7 @@ extern "C" int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enabl
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
+  e->det_plans.clear();
   return U1U1_OK;
 }
 
@@ -441,6 +757,7 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
     if (rc) break;
     e->item_lz = lz;
     e->schedules.clear();
+    e->det_plans.clear();
     rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
     for (int mode : modes) {
       if (rc) break;
@@ -449,7 +766,7 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
         rc = restore();
         if (rc) break;
         cudaEventRecord(ev0, st);
-        rc = u1u1_ensemble_run(e, steps.data(), mode, 0, stream);
+        rc = u1u1_ensemble_run(e, steps.data(), 0, mode, 0, stream);
         cudaEventRecord(ev1, st);
         if (rc) break;
         if (cudaEventSynchronize(ev1) != cudaSuccess) {
@@ -477,9 +794,10 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
   if (!rc) rc = rrc;
   e->item_lz = rc ? lz0 : best_lz;
   e->schedules.clear();
+  e->det_plans.clear();
   const int brc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
   // re-sync the device step table with the restored host bookkeeping
-  for (int b = 0; b < nb; ++b) e->shadow_n[b] = -1;
+  for (int b = 0; b < nb; ++b) e->shadow_n[b] = -1;  // forces the upload (records included)
   const int src = sync_dyn(e, st);
   if (rc) return rc;
   if (brc) return brc;

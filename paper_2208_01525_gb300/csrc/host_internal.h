@@ -12,7 +12,6 @@
 
 namespace u1u1 {
 
-constexpr int RING_CAP = 1024;  // detection records kept on the device
 
 extern thread_local std::string g_last_error;
 int fail(int code, const char* fmt, ...);

@@ -318,12 +318,12 @@ __device__ __forceinline__ void merge_pair(double& s, double& c, double s2, doub
 // First stage: CTA j merges the contiguous slice j of the partials into
 // mid[j].  Warp w takes the quantities w, w + 8, ...; its lanes run over the
 // slice with a stride of 32 and merge their results in a fixed shuffle tree.
-__global__ void __launch_bounds__(FIN_THREADS)
-k_fin_stage(const BlockPartial* __restrict__ part, int nb, BlockPartial* __restrict__ mid) {
-  const int per = (nb + gridDim.x - 1) / gridDim.x;
-  const int b0 = blockIdx.x * per, b1 = min(nb, b0 + per);
+__device__ __forceinline__ void fin_stage_body(const BlockPartial* __restrict__ part, int nb,
+                                               BlockPartial* __restrict__ mid, int j, int nj) {
+  const int per = (nb + nj - 1) / nj;
+  const int b0 = j * per, b1 = min(nb, b0 + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  BlockPartial* out = mid + blockIdx.x;
+  BlockPartial* out = mid + j;
   constexpr int NQ = NSUM + NMAX + NCNT;
   for (int q = warp; q < NQ; q += FIN_THREADS / 32) {
     if (q < NSUM) {
@@ -360,9 +360,15 @@ k_fin_stage(const BlockPartial* __restrict__ part, int nb, BlockPartial* __restr
 }
 
 __global__ void __launch_bounds__(FIN_THREADS)
-k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __restrict__ cpart, int ncb,
-           RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol,
-           const unsigned long long* __restrict__ ge4) {
+k_fin_stage(const BlockPartial* __restrict__ part, int nb, BlockPartial* __restrict__ mid) {
+  fin_stage_body(part, nb, mid, blockIdx.x, gridDim.x);
+}
+
+// Second (or only) stage: one CTA merges nb partials in a fixed tree.
+__device__ __forceinline__ void finalize_body(const BlockPartial* __restrict__ part, int nb,
+                                              const CellPartial* __restrict__ cpart, int ncb, RawRecord* rec,
+                                              long long n, int has_diag, int has_gauss, int has_strings, int tol,
+                                              const unsigned long long* __restrict__ ge4) {
   __shared__ double ss[FIN_THREADS], sc[FIN_THREADS];
   __shared__ long long sl[FIN_THREADS];
   const int t = threadIdx.x;
@@ -429,6 +435,133 @@ k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __r
   }
 }
 
+__global__ void __launch_bounds__(FIN_THREADS)
+k_finalize(const BlockPartial* __restrict__ part, int nb, const CellPartial* __restrict__ cpart, int ncb,
+           RawRecord* rec, long long n, int has_diag, int has_gauss, int has_strings, int tol,
+           const unsigned long long* __restrict__ ge4) {
+  finalize_body(part, nb, cpart, ncb, rec, n, has_diag, has_gauss, has_strings, tol, ge4);
+}
+
+// ---- batched detection of ensemble boxes -----------------------------------
+// The boxes of list[0..nlist) detect at the same run step.  Their cell values
+// and overlap counts are integers, so the batched passes (bytewise cell
+// values, one mask word per warp; 32 mask words per warp for the overlap,
+// counts added atomically per box) give exactly the single-lattice counts.
+
+constexpr int ENS_CELL_THREADS = 256;
+constexpr int ENS_CELL_BLOCKS = 152 * 8;
+
+__global__ void __launch_bounds__(ENS_CELL_THREADS)
+k_ens_cellbits(const EnsDet* __restrict__ det, const int* __restrict__ list, const long long* __restrict__ pre,
+               int nlist, long long items) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < items; u += nwarps) {
+    const int si = ens_list_index(pre, nlist, u);
+    const EnsDet& D = det[list[si]];
+    const long long lu = u - pre[si];
+    const int nx = D.nx, ny = D.ny, nz = D.nz, words = D.words;
+    const long long V = (long long)nx * ny * nz;
+    const long long nw = (long long)words * ny * nz;
+    const int w = (int)(lu % words);
+    const long long row = lu / words;
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    const int x = w * 32 + lane;
+    int c[2] = {0, 0};
+    if (x < nx) {
+      const long long i = row * nx + x;
+      const long long ix = row * nx + (x + 1 == nx ? 0 : x + 1);
+      const long long iy = ((long long)z * ny + (y + 1 == ny ? 0 : y + 1)) * nx + x;
+      const long long iz = ((long long)(z + 1 == nz ? 0 : z + 1) * ny + y) * nx + x;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const uint8_t* f = D.faces + s * V;
+        c[s] = face_w(f, i, 0) + face_w(f, iz, 0) + face_w(f, i, 1) + face_w(f, iy, 1) + face_w(f, i, 2) +
+               face_w(f, ix, 2);
+      }
+    }
+    const uint32_t bp = __ballot_sync(0xffffffffu, c[0] > 0);
+    const uint32_t bq = __ballot_sync(0xffffffffu, c[1] > 0);
+    const int g0 = __popc(__ballot_sync(0xffffffffu, c[0] >= 4));
+    const int g1 = __popc(__ballot_sync(0xffffffffu, c[1] >= 4));
+    if (lane == 0) {
+      D.masks[row * words + w] = bp;
+      D.masks[nw + row * words + w] = bq;
+      if (g0) atomicAdd(&D.ge4[0], (unsigned long long)g0);
+      if (g1) atomicAdd(&D.ge4[1], (unsigned long long)g1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(ENS_CELL_THREADS)
+k_ens_overlap(const EnsDet* __restrict__ det, const int* __restrict__ list, const long long* __restrict__ pre,
+              int nlist, long long items) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < items; u += nwarps) {
+    const int si = ens_list_index(pre, nlist, u);
+    const EnsDet& D = det[list[si]];
+    const int nx = D.nx, ny = D.ny, nz = D.nz, words = D.words;
+    const long long nw = (long long)words * ny * nz;
+    const uint32_t* mp = D.masks;
+    const uint32_t* mq = D.masks + nw;
+    const long long idx = (u - pre[si]) * 32 + lane;
+    long long cp = 0, cq = 0;
+    if (idx < nw) {
+      const int w = (int)(idx % words);
+      const long long row = idx / words;
+      const int y = (int)(row % ny), z = (int)(row / ny);
+      const uint32_t p = mp[idx], q = mq[idx];
+      if (D.tol == 0) {
+        cp = cq = __popc(p & q);
+      } else if ((p | q) != 0) {
+        uint32_t dq = 0, dp = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+          const int zz = z + dz < 0 ? nz - 1 : (z + dz >= nz ? 0 : z + dz);
+          for (int dy = -1; dy <= 1; ++dy) {
+            const int yy = y + dy < 0 ? ny - 1 : (y + dy >= ny ? 0 : y + dy);
+            const long long rb = ((long long)zz * ny + yy) * words;
+            if (p) dq |= xdilate(mq, rb, w, words, nx);
+            if (q) dp |= xdilate(mp, rb, w, words, nx);
+          }
+        }
+        cp = __popc(p & dq);
+        cq = __popc(q & dp);
+      }
+    }
+    cp = warp_sum_ll(cp);
+    cq = warp_sum_ll(cq);
+    if (lane == 0) {
+      if (cp) atomicAdd((unsigned long long*)&D.counts->pq[0], (unsigned long long)cp);
+      if (cq) atomicAdd((unsigned long long*)&D.counts->pq[1], (unsigned long long)cq);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(FIN_THREADS)
+k_ens_fin_stage(const EnsDet* __restrict__ det, const int* __restrict__ list) {
+  const EnsDet& D = det[list[blockIdx.y]];
+  const int nb = D.nmeas + D.nwind;
+  if (nb <= FIN_STAGE_MIN) return;
+  fin_stage_body(D.part, nb, D.part + nb, blockIdx.x, gridDim.x);
+}
+
+// One CTA per box: the record of run step k goes to the box's ring slot
+// rec + (number of the box's detections before k in this run).
+__global__ void __launch_bounds__(FIN_THREADS)
+k_ens_finalize(const EnsDet* __restrict__ det, const EnsDyn* __restrict__ dyn, const int* __restrict__ list, int k,
+               int de, int ring_cap) {
+  const int b = list[blockIdx.x];
+  const EnsDet& D = det[b];
+  const int nb = D.nmeas + D.nwind;
+  const bool staged = nb > FIN_STAGE_MIN;
+  const long long n0 = dyn[b].n;
+  const long long k1 = (de - n0 % de) % de;
+  const long long slot = (dyn[b].rec + (k - k1) / de) % ring_cap;
+  finalize_body(staged ? D.part + nb : D.part, staged ? FIN_STAGE_BLOCKS : nb, D.counts, 1, D.ring + slot, n0 + k,
+                1, 0, 1, D.tol, D.ge4);
+}
+
 }  // namespace
 
 int cells_grid_blocks() { return OVL_BLOCKS; }
@@ -462,6 +595,28 @@ cudaError_t launch_cells(const uint8_t* faces, int nx, int ny, int nz, int tol, 
     k_overlap_row32<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, ny, nz, tol, part, mpq);
   else
     k_overlap<<<OVL_BLOCKS, OVL_THREADS, 0, st>>>(mp, mq, nx, ny, nz, words, tol, part, mpq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_cells(const EnsDet* det, const int* list, const long long* pre_c, const long long* pre_o,
+                             int nlist, long long items_c, long long items_o, cudaStream_t st) {
+  if (items_c <= 0) return cudaSuccess;
+  k_ens_cellbits<<<ENS_CELL_BLOCKS, ENS_CELL_THREADS, 0, st>>>(det, list, pre_c, nlist, items_c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ens_overlap<<<ENS_CELL_BLOCKS, ENS_CELL_THREADS, 0, st>>>(det, list, pre_o, nlist, items_o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_finalize(const EnsDet* det, const EnsDyn* dyn, const int* list, int nlist, int k, int de,
+                                bool stage, cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  if (stage) {
+    k_ens_fin_stage<<<dim3(FIN_STAGE_BLOCKS, nlist), FIN_THREADS, 0, st>>>(det, list);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_ens_finalize<<<nlist, FIN_THREADS, 0, st>>>(det, dyn, list, k, de, RING_CAP);
   return cudaGetLastError();
 }
 

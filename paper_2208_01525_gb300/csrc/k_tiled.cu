@@ -844,6 +844,14 @@ int tiled_grid_blocks(int nx, int ny, int nz, int sizeof_t, int waves) {
   return g.gx * g.gy * g.gz;
 }
 
+void tiled_grid_dims(int nx, int ny, int nz, int sizeof_t, int waves, int* gx, int* gy, int* gz, int* lz) {
+  Grid g = sizeof_t == 8 ? tiled_grid<double>(nx, ny, nz, waves) : tiled_grid<float>(nx, ny, nz, waves);
+  *gx = g.gx;
+  *gy = g.gy;
+  *gz = g.gz;
+  *lz = g.lz;
+}
+
 // ---------------------------------------------------------------------------
 // Ensemble kernels: many independent boxes in one launch.
 // ---------------------------------------------------------------------------
@@ -903,7 +911,8 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
-                 EnsSched sc, unsigned long long* ticket, unsigned* done, int* err, long long limit_ns, int inject) {
+                 EnsSched sc, const int* __restrict__ kstart, unsigned long long* ticket, unsigned* done, int* err,
+                 long long limit_ns, int inject) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   __shared__ long long s_t;
@@ -938,6 +947,7 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
           }
           __threadfence();
         }
+        if (kstart) k += kstart[box];  // the run step of this item
         if (go) cs = coef[boxes[box].coef0 + dyn[box].n + k];
       }
       s_go = go;
@@ -972,9 +982,59 @@ k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, 
   ens_run_item<T, false>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si]);
 }
 
-__global__ void k_ens_advance(EnsDyn* dyn, const int* steps, int nboxes) {
+// Measuring step k (a step fused with the diagnostic sums) of the boxes in
+// list[0..nlist), one CTA per tile of any of them, in the tile grid and
+// partial slots of a single lattice's measuring launch.  The CTA of a box's
+// first tile also clears the box's overlap and census counters for the
+// passes that follow in stream order.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
+k_ens_measure(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ det, const EnsDyn* __restrict__ dyn,
+              const Coef<T>* __restrict__ coef, const int* __restrict__ list, const long long* __restrict__ pre,
+              int nlist, int k) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ Coef<T> cs;
+  const long long r = blockIdx.x;
+  const int si = ens_list_index(pre, nlist, r);
+  const int b = list[si];
+  const long long t = r - pre[si];
+  const EnsBox<T>& B = boxes[b];
+  const EnsDet& D = det[b];
+  if (threadIdx.x == 0) cs = coef[B.coef0 + dyn[b].n + k];
+  if (t == 0 && threadIdx.x < 2) {
+    D.counts->pq[threadIdx.x] = 0;
+    D.ge4[threadIdx.x] = 0ull;
+  }
+  __syncthreads();
+  const int cur = (dyn[b].cur + k) & 1;
+  const int bx = (int)(t % D.mgx), by = (int)((t / D.mgx) % D.mgy), bz = (int)(t / ((long long)D.mgx * D.mgy));
+  const int z0 = bz * D.mlz, z1 = min(z0 + D.mlz, B.nz);
+  LatticeView<T> v;
+#pragma unroll
+  for (int f = 0; f < U1U1_NPOS; ++f) {
+    v.pin[f] = B.pos[cur][f];
+    v.pout[f] = B.pos[cur ^ 1][f];
+  }
+#pragma unroll
+  for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = B.mom[f];
+  v.nx = B.nx;
+  v.ny = B.ny;
+  v.nz = B.nz;
+  MeasureOut mo{D.part, nullptr, nullptr};
+  tile_run<T, TileShape<T>::TX, TileShape<T>::TY, MODE_WRITE | MODE_MEASURE, false, false>(smem_raw, v, cs, mo, bx, by,
+                                                                                         z0, z1, (int)t, B.tma[cur]);
+}
+
+// After a run: advance each box's step index, buffer parity and count of
+// records written (the steps n0 <= n < n0 + steps with n % de == 0).
+__global__ void k_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < nboxes) {
+    if (de > 0) {
+      const long long n0 = dyn[b].n;
+      const long long k1 = (de - n0 % de) % de;  // first detection step of the run
+      if (steps[b] > k1) dyn[b].rec += (steps[b] - 1 - k1) / de + 1;
+    }
     dyn[b].n += steps[b];
     dyn[b].cur ^= (steps[b] & 1);
   }
@@ -1012,8 +1072,8 @@ int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, in
 
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
-                                  unsigned long long* ticket, unsigned* done, int* err, long long limit_ns,
-                                  int inject, cudaStream_t st) {
+                                  const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
+                                  long long limit_ns, int inject, cudaStream_t st) {
   const size_t bytes = ens_smem_bytes<T>();
   cudaError_t e = set_smem_attr(k_ens_persistent<T>, bytes);
   if (e != cudaSuccess) return e;
@@ -1025,7 +1085,20 @@ cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, con
   long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
   if (grid > sc.total) grid = sc.total;
   if (grid < 1) return cudaSuccess;
-  k_ens_persistent<T><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, ticket, done, err, limit_ns, inject);
+  k_ens_persistent<T><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
+                                                          inject);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ens_measure(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const Coef<T>* coef,
+                               const int* list, const long long* pre, int nlist, long long items, int k,
+                               cudaStream_t st) {
+  const size_t bytes = sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, true, false>);
+  cudaError_t e = set_smem_attr(k_ens_measure<T>, bytes);
+  if (e != cudaSuccess) return e;
+  if (items <= 0) return cudaSuccess;
+  k_ens_measure<T><<<(unsigned)items, 256, bytes, st>>>(boxes, det, dyn, coef, list, pre, nlist, k);
   return cudaGetLastError();
 }
 
@@ -1040,17 +1113,22 @@ cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coe
   return cudaGetLastError();
 }
 
-cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, cudaStream_t st) {
-  k_ens_advance<<<(nboxes + 127) / 128, 128, 0, st>>>(dyn, steps, nboxes);
+cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de, cudaStream_t st) {
+  k_ens_advance<<<(nboxes + 127) / 128, 128, 0, st>>>(dyn, steps, nboxes, de);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_ens_persistent<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*,
-                                                  const EnsSched&, unsigned long long*, unsigned*, int*, long long,
-                                                  int, cudaStream_t);
+                                                  const EnsSched&, const int*, unsigned long long*, unsigned*, int*,
+                                                  long long, int, cudaStream_t);
 template cudaError_t launch_ens_persistent<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,
-                                                   const EnsSched&, unsigned long long*, unsigned*, int*, long long,
-                                                   int, cudaStream_t);
+                                                   const EnsSched&, const int*, unsigned long long*, unsigned*, int*,
+                                                   long long, int, cudaStream_t);
+template cudaError_t launch_ens_measure<float>(const EnsBox<float>*, const EnsDet*, const EnsDyn*, const Coef<float>*,
+                                               const int*, const long long*, int, long long, int, cudaStream_t);
+template cudaError_t launch_ens_measure<double>(const EnsBox<double>*, const EnsDet*, const EnsDyn*,
+                                                const Coef<double>*, const int*, const long long*, int, long long, int,
+                                                cudaStream_t);
 template cudaError_t launch_ens_step<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*, const EnsSched&,
                                             int, long long, cudaStream_t);
 template cudaError_t launch_ens_step<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,

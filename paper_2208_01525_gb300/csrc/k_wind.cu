@@ -102,14 +102,16 @@ __device__ __forceinline__ T edge_k(T a_h, T a_t, T theta, unsigned* cut) {
   return k;
 }
 
+// One window column (tile (bx, by), planes [bz lz, bz lz + lz)) of the
+// windings pass; its counts go to the block partial *p.
 template <typename T>
-__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 3)
-k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_t* windings) {
+__device__ __forceinline__ void windings_tile(const PosView<T>& v, T dx, int lz, int bx, int by, int bz,
+                                              BlockPartial* p, uint8_t* faces, int8_t* windings) {
   __shared__ WindSmem<T> sm;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
   const int nx = v.nx, ny = v.ny, nz = v.nz;
-  const int x0 = blockIdx.x * WOX, y0 = blockIdx.y * WOY;
-  const int z0 = blockIdx.z * lz, z1 = min(z0 + lz, nz);
+  const int x0 = bx * WOX, y0 = by * WOY;
+  const int z0 = bz * lz, z1 = min(z0 + lz, nz);
   const int gx = (x0 + lane) % nx, gy = (y0 + w) % ny;
   const bool out = lane < WOX && w < WOY && x0 + lane < nx && y0 + w < ny;
   const long long plane = (long long)nx * ny;
@@ -239,7 +241,6 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
     if (lane == 0) sm.cnt[w][k] = vk;
   }
   __syncthreads();
-  BlockPartial* p = part + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (t < NSUM) {
     p->sum[t] = 0.0;
     p->comp[t] = 0.0;
@@ -251,6 +252,38 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
     for (int ww = 0; ww < WH; ++ww) acc = (k == C_MAXW) ? max(acc, (long long)sm.cnt[ww][k]) : acc + sm.cnt[ww][k];
     p->cnt[k] = acc;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 3)
+k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_t* windings) {
+  BlockPartial* p = part + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  windings_tile<T>(v, dx, lz, blockIdx.x, blockIdx.y, blockIdx.z, p, faces, windings);
+}
+
+// Windings of the boxes of an ensemble that detect at step k of a run, one
+// CTA per window column of any of them: the same windows, chunking and
+// partial slots as a single lattice's pass, on each box's input positions
+// of step k.
+template <typename T>
+__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 3)
+k_ens_windings(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ det, const EnsDyn* __restrict__ dyn,
+               const int* __restrict__ list, const long long* __restrict__ pre, int nlist, int k) {
+  const long long r = blockIdx.x;
+  const int si = ens_list_index(pre, nlist, r);
+  const int b = list[si];
+  const long long t = r - pre[si];
+  const EnsBox<T>& B = boxes[b];
+  const EnsDet& D = det[b];
+  const int bx = (int)(t % D.wtx), by = (int)((t / D.wtx) % D.wty), bz = (int)(t / ((long long)D.wtx * D.wty));
+  PosView<T> v;
+  const int par = (dyn[b].cur + k) & 1;
+#pragma unroll
+  for (int f = 0; f < U1U1_NPOS; ++f) v.pos[f] = B.pos[par][f];
+  v.nx = B.nx;
+  v.ny = B.ny;
+  v.nz = B.nz;
+  windings_tile<T>(v, B.dx, D.wlz, bx, by, bz, D.part + D.nmeas + t, D.faces, nullptr);
 }
 
 void wind_grid(int nx, int ny, int nz, dim3* grid, int* lz) {
@@ -271,6 +304,26 @@ int wind_grid_blocks(int nx, int ny, int nz) {
   wind_grid(nx, ny, nz, &g, &lz);
   return (int)(g.x * g.y * g.z);
 }
+
+void wind_grid_dims(int nx, int ny, int nz, int* tx, int* ty, int* tz, int* lz) {
+  dim3 g;
+  wind_grid(nx, ny, nz, &g, lz);
+  *tx = (int)g.x;
+  *ty = (int)g.y;
+  *tz = (int)g.z;
+}
+
+template <typename T>
+cudaError_t launch_ens_windings(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const int* list,
+                                const long long* pre, int nlist, long long items, int k, cudaStream_t st) {
+  if (items <= 0) return cudaSuccess;
+  k_ens_windings<T><<<(unsigned)items, WNT, 0, st>>>(boxes, det, dyn, list, pre, nlist, k);
+  return cudaGetLastError();
+}
+template cudaError_t launch_ens_windings<float>(const EnsBox<float>*, const EnsDet*, const EnsDyn*, const int*,
+                                                const long long*, int, long long, int, cudaStream_t);
+template cudaError_t launch_ens_windings<double>(const EnsBox<double>*, const EnsDet*, const EnsDyn*, const int*,
+                                                 const long long*, int, long long, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_windings(const PosView<T>& v, T dx, BlockPartial* part, uint8_t* faces, int8_t* windings,

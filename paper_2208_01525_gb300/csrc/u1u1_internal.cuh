@@ -10,6 +10,8 @@
 
 namespace u1u1 {
 
+constexpr int RING_CAP = 1024;  // detection records kept on the device per lattice
+
 // ---------------------------------------------------------------------------
 // Reduction record layout.  Every measuring kernel writes one partial per
 // block; a single-block finalize kernel merges them in a fixed order into a
@@ -171,12 +173,42 @@ struct EnsBox {
   int gx, gy, lz, gz, ntiles;  // tile grid of this box
   long long coef0;             // first row of this box in the coefficient table
   const TmaPlan* tma[2];       // tensor maps of each position buffer (device memory)
+  T dx;                        // lattice spacing (windings)
 };
-struct EnsDyn {                // device-side step index and current buffer
+struct EnsDyn {                // device-side step index, current buffer and records written
   long long n;
+  long long rec;
   int cur;
   int pad;
 };
+// Detection resources of one ensemble box (the scratch of its handle) and
+// the grids of its passes, which are those of a single lattice of the same
+// shape, so that a box's records equal those of the box stepped alone.
+struct EnsDet {
+  BlockPartial* part;        // measuring partials, then windings partials, then stage slots
+  uint8_t* faces;            // 2 V face bytes
+  uint32_t* masks;           // 2 x cell_mask_words pierced-cell words
+  CellPartial* counts;       // one overlap partial, accumulated atomically
+  unsigned long long* ge4;   // census counters
+  RawRecord* ring;           // the handle's record ring (RING_CAP entries)
+  int mgx, mgy, mgz, mlz;    // measuring tile grid (the default chunking)
+  int wtx, wty, wtz, wlz;    // windings window grid
+  int nmeas, nwind;          // block partials of each pass
+  int words;                 // mask words per row
+  int tol;                   // overlap tolerance
+  int nx, ny, nz;
+};
+// index of the entry of a prefix table pre[0..n] (pre[0] = 0 <= r < pre[n])
+// that holds r: the largest i < n with pre[i] <= r
+__device__ __forceinline__ int ens_list_index(const long long* pre, int n, long long r) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 struct EnsSched {              // one run's work-item order
   const int* order;            // sorted position -> box (steps descending)
   const int* steps;            // steps of each box (box index)
@@ -188,14 +220,38 @@ struct EnsSched {              // one run's work-item order
 constexpr int ENS_LZ = 32;     // default z-chunk of an ensemble work item
 
 int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, int item_lz = ENS_LZ);
+// kstart (nullable): per box, the run step its first item of this launch
+// advances (a launch covering a segment of a run between detection steps)
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
-                                  unsigned long long* ticket, unsigned* done, int* err, long long limit_ns,
-                                  int inject, cudaStream_t st);
+                                  const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
+                                  long long limit_ns, int inject, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                             int k, long long items, cudaStream_t st);
-cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, cudaStream_t st);
+// de: detection cadence of the run (0: none), for the record counters
+cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de, cudaStream_t st);
+
+// Batched detection at run step k over the boxes list[0..nlist) (every one
+// of them detects at k); pre: per-list-entry prefix sums of the launch's
+// work items.  The measuring step (writes step k and the diagnostic sums),
+// the windings of its input positions, cells and overlap, the finalize into
+// each box's record ring.
+template <typename T>
+cudaError_t launch_ens_measure(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const Coef<T>* coef,
+                               const int* list, const long long* pre, int nlist, long long items, int k,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_ens_windings(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const int* list,
+                                const long long* pre, int nlist, long long items, int k, cudaStream_t st);
+// pre_c: prefix sums of each box's mask words (the cell pass: one warp per
+// word of 32 cells), pre_o: of its groups of 32 mask words (the overlap)
+cudaError_t launch_ens_cells(const EnsDet* det, const int* list, const long long* pre_c, const long long* pre_o,
+                             int nlist, long long items_c, long long items_o, cudaStream_t st);
+cudaError_t launch_ens_finalize(const EnsDet* det, const EnsDyn* dyn, const int* list, int nlist, int k, int de,
+                                bool stage, cudaStream_t st);
+void tiled_grid_dims(int nx, int ny, int nz, int sizeof_t, int waves, int* gx, int* gy, int* gz, int* lz);
+void wind_grid_dims(int nx, int ny, int nz, int* tx, int* ty, int* tz, int* lz);
 
 // Cells and overlap from face bytes; masks holds 2 * cell_mask_words words.
 int cells_grid_blocks();

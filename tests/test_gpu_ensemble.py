@@ -188,3 +188,84 @@ def test_ensemble_tensor_copy_boxes(mode, graph):
         assert ens.boxes[b].n == reps * steps[b]
         assert torch.equal(ens.boxes[b].state(), alone(p, reps * steps[b])), b
     ens.close()
+
+
+def _same_record(a: dict, b: dict) -> bool:
+    for k, v in b.items():
+        w = a[k]
+        if isinstance(v, float) and v != v:
+            if w == w:
+                return False
+        elif w != v:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("mode,graph", [(U.ENS_PERSISTENT, False), (U.ENS_PERSISTENT, True),
+                                        (U.ENS_PER_STEP, False), (U.ENS_PER_STEP, True),
+                                        (U.ENS_UNBATCHED, False)])
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_ensemble_detection_records_equal_single_boxes(mode, graph, prec):
+    """Detection every 4 steps inside ensemble runs: each box's records (read
+    from its own handle's ring) equal, field for field, the records of the
+    same box stepped alone with fused detection (same windings and counts,
+    same diagnostic sums bit for bit), and the states stay equal.  Box 2
+    takes one step through its own handle first, so the boxes detect at
+    different run steps; graph runs are captured and replayed, and the
+    second run starts each box at another phase of the cadence."""
+    de = 4
+    ps = box_params(prec, unequal_odd=True)
+    steps = [10, 7, 9, 0, 5, 8]
+    reps = 2 if graph else 1
+    ens = U.Ensemble(ps)
+    ens.boxes[2].step(1)
+    for _ in range(reps):
+        ens.run(steps, mode=mode, use_graph=graph, detect_every=de)
+    torch.cuda.synchronize()
+    assert ens.status() == 0
+    for b, p in enumerate(ps):
+        ref = U.Lattice(p, kernel=U.KERNEL_TILED)
+        if b == 2:
+            ref.step(1)
+        for _ in range(reps):
+            ref.step(steps[b], detect_every=de)
+        want, lost_w = ref.read_records()
+        got, lost_g = ens.boxes[b].read_records()
+        assert lost_w == lost_g == 0
+        assert [r[0]["n"] for r in got] == [r[0]["n"] for r in want], b
+        for (gs, gd), (ws, wd) in zip(got, want):
+            assert _same_record(gs, ws), (b, gs["n"], gs, ws)
+            assert _same_record(gd, wd), (b, gd["n"], gd, wd)
+        assert torch.equal(ens.boxes[b].state(), ref.state()), b
+    ens.close()
+
+
+def test_ensemble_detection_overlap_tolerance_and_oracle():
+    """The overlap tolerance of each box's handle applies to its detection
+    records (tolerance 0 on box 1, 1 elsewhere), and a detected record of
+    an FP64 box equals the oracle's strings on the oracle's own state."""
+    import oracle as O
+    ps = box_params(U.FP64)
+    ens = U.Ensemble(ps)
+    U.check(U.lib().u1u1_set_overlap_tol(ens.boxes[1]._h, 0))
+    ens.run([8] * 6, mode=U.ENS_PER_STEP, detect_every=8)
+    for b, p in enumerate(ps):
+        recs, lost = ens.boxes[b].read_records()
+        assert lost == 0 and [r[0]["n"] for r in recs] == [0]
+        assert recs[0][0]["overlap_tol"] == (0 if b == 1 else 1)
+    ens.run([8] * 6, mode=U.ENS_PERSISTENT, detect_every=8)
+    op = to_oracle(ps[4])
+    ref = O.init(op)
+    O.step(op, ref, 0, 8)
+    ores = O.strings(op, ref, tol=1)
+    recs, _ = ens.boxes[4].read_records()
+    s = recs[0][0]
+    assert s["n"] == 8
+    if ores["n_flagged"] == 0:
+        for k in ("n_p", "n_q", "n_pq_plaq", "n_pq_cell", "n_pq_cell_q", "max_abs_w"):
+            assert s[k] == ores[k], (k, s[k], ores[k])
+    od = O.diagnostics(op, ref, 8)
+    d = recs[0][1]
+    for k in ("kin_p", "grad_q", "el_p", "mag_q", "pot", "vint"):
+        assert abs(d[k] - od[k]) <= 1e-10 * max(abs(od[k]), abs(od["energy"])), k
+    ens.close()
