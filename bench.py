@@ -254,11 +254,60 @@ def run_reference(args):
     return 0
 
 
+def period_rate(U, torch, p, de, periods, warmup, dev):
+    """Detection periods of de steps (the first step of each fused with
+    detection) on a fresh lattice of parameters p: site-updates/s, ms per
+    period and the last record."""
+    lat = U.Lattice(p, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lat.step(de, detect_every=de)
+    torch.cuda.synchronize()
+    lat.read_records()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(periods):
+        lat.step(de, detect_every=de)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / periods
+    recs, _ = lat.read_records()
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    last = recs[-1] if recs else None
+    return {"value": de * p.nsites / (ms * 1e-3), "unit": "site-updates/s", "ms_per_period": ms,
+            "detect_every": de, "periods": periods,
+            "last_record": None if last is None else {"n": last[0]["n"], "xi_w": last[0]["xi_w"],
+                                                      "xi_l": last[1]["xi_l"], "v2_l": last[1]["v2_l"]}}
+
+
+def config_legs(U, torch, dev, warmup):
+    """The smaller configurations of the workload set, each a few timed
+    detection periods: 256^3 radiation beta = 1 with detection every 10
+    steps in FP32 and FP64 (640-step run to eta = 65), and 512^3 with full
+    detection every 8 steps in the radiation and matter eras for beta = 1
+    and beta = 0 (1280-step runs to eta = 129)."""
+    out = {}
+    for prec, tag in ((U.FP32, "fp32"), (U.FP64, "fp64")):
+        p = U.Params.cube(256, m=0.5, beta=1.0, eta0=1.0, eta_ref=65.0, seed=1, precision=prec)
+        out[f"256_radiation_beta1_{tag}"] = period_rate(U, torch, p, 10, 5, warmup, dev)
+    for m, era in ((0.5, "radiation"), (2.0 / 3.0, "matter")):
+        for beta in (1.0, 0.0):
+            p = U.Params.cube(512, m=m, beta=beta, eta0=1.0, eta_ref=129.0 if beta > 0 else 1.0, seed=3,
+                              precision=U.FP32)
+            out[f"512_{era}_beta{int(beta)}_fp32"] = period_rate(U, torch, p, 8, 5, warmup, dev)
+    return out
+
+
 def ensemble_bench(U, torch, dev):
     """The batched configuration: 48 independent boxes (16 x 64^3, 16 x 128^3,
     16 x 192^3), matter era, beta cycling 1, 0, -1, seeds 1000 + b, each run
-    to half its light-crossing time (160 / 320 / 480 steps), FP32.  Each mode
-    is timed on its second run (the first one captures the graph)."""
+    to half its light-crossing time (160 / 320 / 480 steps), FP32.  The
+    library's ensemble autotuner picks the work-item z-chunk (and whether the
+    persistent kernel uses tensor copies) first; then each mode is timed on
+    its second run (the first one captures the graph), without and with
+    detection every 16 steps inside the run."""
     sizes = [64] * 16 + [128] * 16 + [192] * 16
     steps = [n * 5 // 2 for n in sizes]  # n dx / 2 in units of deta = 0.1
     ps = []
@@ -271,57 +320,50 @@ def ensemble_bench(U, torch, dev):
     out = {"boxes": len(sizes), "site_updates_per_run": work, "steps": "160/320/480", "era": "matter",
            "beta": "1,0,-1 round-robin"}
     stream = torch.cuda.current_stream()
-    for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True),
-                              ("per_step_graph", U.ENS_PER_STEP, True),
-                              ("unbatched", U.ENS_UNBATCHED, False)):
-        ens = U.Ensemble(ps, device=dev, horizon=2048)
-        ens.run(steps, mode=mode, use_graph=graph)
+    modes = (("persistent_graph", U.ENS_PERSISTENT, True), ("per_step_graph", U.ENS_PER_STEP, True),
+             ("unbatched", U.ENS_UNBATCHED, False))
+
+    def timed(ens, mode, graph, de):
+        ens.run(steps, mode=mode, use_graph=graph, detect_every=de)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ens.run(steps, mode=mode, use_graph=graph)
+        ens.run(steps, mode=mode, use_graph=graph, detect_every=de)
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
-        status = ens.status()
-        ens.close()
-        del ens
-        torch.cuda.empty_cache()
-        out[name] = {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": status}
+        return {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": ens.status()}
+
+    # one ensemble for every timed run (12 runs of up to 480 steps per box)
+    ens = U.Ensemble(ps, device=dev, horizon=8192)
+    out["autotuned"] = ens.autotune(probe_steps=8)
+    for name, mode, graph in modes:
+        out[name] = timed(ens, mode, graph, 0)
     out["speedup_vs_unbatched"] = out["persistent_graph"]["site_updates_per_s"] / \
         out["unbatched"]["site_updates_per_s"]
     # the same runs with detection every 16 steps inside the run (windings,
     # cells, overlap and diagnostic sums of every box, records in each box's
     # ring); batched modes detect all boxes of a run step in one launch per pass
+    for bx in ens.boxes:
+        bx.read_records(max_records=1024)
     det = {"detect_every": 16}
-    for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True),
-                              ("per_step_graph", U.ENS_PER_STEP, True),
-                              ("unbatched", U.ENS_UNBATCHED, False)):
-        ens = U.Ensemble(ps, device=dev, horizon=2048)
-        ens.run(steps, mode=mode, use_graph=graph, detect_every=16)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ens.run(steps, mode=mode, use_graph=graph, detect_every=16)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        status = ens.status()
-        nrec = sum(len(bx.read_records(max_records=1024)[0]) for bx in ens.boxes)
-        ens.close()
-        del ens
-        torch.cuda.empty_cache()
-        det[name] = {"ms": ms, "site_updates_per_s": work / (ms * 1e-3), "status": status, "records": nrec}
+    for name, mode, graph in modes:
+        det[name] = timed(ens, mode, graph, 16)
+        det[name]["records"] = sum(len(bx.read_records(max_records=1024)[0]) for bx in ens.boxes)
     det["speedup_vs_unbatched"] = det["persistent_graph"]["site_updates_per_s"] / \
         det["unbatched"]["site_updates_per_s"]
     out["with_detection"] = det
+    ens.close()
+    del ens
+    torch.cuda.empty_cache()
     # the small-box class alone (16 x 64^3), where per-box launches cannot fill the GPU
     small = [p for p, n in zip(ps, sizes) if n == 64]
     ssteps = [s_ for s_, n in zip(steps, sizes) if n == 64]
     swork = sum(s_ * 64 ** 3 for s_ in ssteps)
     res = {}
+    ens = U.Ensemble(small, device=dev, horizon=2048)
+    res["autotuned"] = ens.autotune(probe_steps=8)
     for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True), ("unbatched", U.ENS_UNBATCHED, False)):
-        ens = U.Ensemble(small, device=dev, horizon=2048)
         ens.run(ssteps, mode=mode, use_graph=graph)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -330,7 +372,9 @@ def ensemble_bench(U, torch, dev):
         b.record(stream)
         torch.cuda.synchronize()
         res[name] = swork / (a.elapsed_time(b) * 1e-3)
-        ens.close()
+    ens.close()
+    del ens
+    torch.cuda.empty_cache()
     out["small_boxes_64"] = {"site_updates_per_s": res,
                              "speedup_vs_unbatched": res["persistent_graph"] / res["unbatched"]}
     return out
@@ -557,6 +601,10 @@ def run_ours(args):
     if args.ensemble:
         ens = ensemble_bench(U, torch, dev)
 
+    configs = None
+    if args.configs:
+        configs = config_legs(U, torch, dev, args.warmup)
+
     cpu = None
     if rank == 0 and args.cpu:
         v, dt, cores = cpu_baseline(args.cpu_n)
@@ -590,6 +638,7 @@ def run_ours(args):
             "fp64": fp64,
             "beta_m1": beta_m1,
             "ensemble": ens,
+            "configs": configs,
             "cpu_baseline": cpu,
             "records_lost": lost,
             "last_record": None if last is None else {
@@ -623,6 +672,8 @@ def main():
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-ensemble", dest="ensemble", action="store_false")
     ap.add_argument("--no-passes", dest="passes", action="store_false")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the 256^3 and 512^3 configuration legs")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--waves", type=int, default=0,
                     help="fixed wave target of the tiled step kernel (8 .. 256) instead of autotuning")

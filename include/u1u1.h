@@ -444,12 +444,21 @@ int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enable);
 
 /* Autotuner for ensembles: times a probe run of probe_steps steps of every
  * box for each work-item z-chunk (16, 32, 64, 128 planes) and schedule
- * (persistent, per-step), restoring every box's state and step index after
- * each trial (needs a temporary copy of the ensemble state), keeps the
- * fastest z-chunk and returns the fastest schedule in *mode_out for later
- * u1u1_ensemble_run calls.  Synchronises `stream`.
+ * (persistent with and without tensor copies of interior tiles, per-step),
+ * restoring every box's state and step index after each trial (needs a
+ * temporary copy of the ensemble state), keeps the fastest z-chunk and
+ * tensor-copy choice and returns the fastest schedule in *mode_out for
+ * later u1u1_ensemble_run calls.  Synchronises `stream`.
  * Errors: INVALID_ARG, STATE, OUT_OF_MEMORY, CUDA. */
 int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mode_out, int* item_lz_out, void* stream);
+
+/* Set the ensemble's tuning knobs without timing (reproduces a tuned
+ * choice): item_lz, the work-item z-chunk (16, 32, 64 or 128 planes), and
+ * persistent_tma, whether the persistent kernel fills the ring slots of
+ * interior tiles by tensor copies (1, the default) or by cp.async (0).
+ * Results are the same either way.  Drops captured graphs; synchronises
+ * `stream`.  Errors: INVALID_ARG, CUDA. */
+int u1u1_ensemble_set_tuning(u1u1_ensemble* e, int item_lz, int persistent_tma, void* stream);
 
 void u1u1_ensemble_destroy(u1u1_ensemble* e);
 

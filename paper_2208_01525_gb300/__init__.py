@@ -358,6 +358,10 @@ class Ensemble:
                                            _stream_ptr(stream)))
         return {"mode": m.value, "item_lz": lz.value}
 
+    def set_tuning(self, item_lz: int = 32, persistent_tma: bool = True, stream=None):
+        """Work-item z-chunk and the persistent kernel's tensor copies, without timing."""
+        check(lib().u1u1_ensemble_set_tuning(self._h, int(item_lz), int(bool(persistent_tma)), _stream_ptr(stream)))
+
     def status(self, stream=None) -> int:
         v = ctypes.c_int()
         check(lib().u1u1_ensemble_status(self._h, ctypes.byref(v), _stream_ptr(stream)))

@@ -102,6 +102,7 @@ struct u1u1_ensemble {
   int inject = 0;
   int poisoned = 0;
   int item_lz = ENS_LZ;  // z-chunk of a work item (tuning knob)
+  int persistent_tma = 1;  // the persistent kernel fills interior tiles by tensor copies (tuning knob)
   std::map<std::vector<int>, std::unique_ptr<Schedule>> schedules;
   cudaStream_t capture_stream = nullptr;
   // detection inside runs: per-box resources and plans keyed by
@@ -243,7 +244,7 @@ int enqueue_run(u1u1_ensemble* e, Schedule* s, int mode, int de, cudaStream_t st
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->nboxes, st), "counter reset");
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_err, 0, sizeof(int), st), "status reset");
     err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, s->sc, nullptr, e->d_ticket, e->d_done, e->d_err,
-                                   e->wait_limit_ns, e->inject, st);
+                                   e->wait_limit_ns, e->inject, e->persistent_tma, st);
     if (err != cudaSuccess) return cuda_fail(err, "persistent ensemble kernel");
   } else if (mode == U1U1_ENS_PER_STEP) {
     for (int k = 0; k < s->sc.smax; ++k) {
@@ -438,7 +439,7 @@ int enqueue_det_run(u1u1_ensemble* e, Schedule* s, DetPlan* P, int mode, int de,
         U1U1_CUDA_TRY(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), st), "ticket reset");
         U1U1_CUDA_TRY(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->nboxes, st), "counter reset");
         err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, view(P, L), P->d_int + L.kstart, e->d_ticket,
-                                       e->d_done, e->d_err, e->wait_limit_ns, e->inject, st);
+                                       e->d_done, e->d_err, e->wait_limit_ns, e->inject, e->persistent_tma, st);
         if (err != cudaSuccess) return cuda_fail(err, "persistent ensemble kernel");
       }
       if (j < P->groups.size()) {
@@ -700,6 +701,20 @@ extern "C" int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enabl
 // autotuner: work-item z-chunk and schedule
 // ---------------------------------------------------------------------------
 
+extern "C" int u1u1_ensemble_set_tuning(u1u1_ensemble* e, int item_lz, int persistent_tma, void* stream) {
+  if (!e) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  if (item_lz != 16 && item_lz != 32 && item_lz != 64 && item_lz != 128)
+    return fail(U1U1_ERR_INVALID_ARG, "item_lz must be 16, 32, 64 or 128 (got %d)", item_lz);
+  if (persistent_tma != 0 && persistent_tma != 1) return fail(U1U1_ERR_INVALID_ARG, "persistent_tma must be 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
+  e->item_lz = item_lz;
+  e->persistent_tma = persistent_tma;
+  e->schedules.clear();  // tile grids and captured graphs change
+  e->det_plans.clear();
+  return e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
+}
+
 extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mode_out, int* item_lz_out,
                                       void* stream) {
   if (!e) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
@@ -743,11 +758,12 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
     }
     return U1U1_OK;
   };
-  const int lz0 = e->item_lz;
+  const int lz0 = e->item_lz, tma0 = e->persistent_tma;
   const int lzs[] = {16, 32, 64, 128};
-  const int modes[] = {U1U1_ENS_PERSISTENT, U1U1_ENS_PER_STEP};
+  // (mode, tensor copies in the persistent kernel)
+  const int modes[][2] = {{U1U1_ENS_PERSISTENT, 1}, {U1U1_ENS_PERSISTENT, 0}, {U1U1_ENS_PER_STEP, 1}};
   float best = 1e30f;
-  int best_mode = U1U1_ENS_PERSISTENT, best_lz = lz0;
+  int best_mode = U1U1_ENS_PERSISTENT, best_lz = lz0, best_tma = tma0;
   std::vector<int> steps(nb);
   for (int b = 0; b < nb; ++b) steps[b] = (int)std::min<long long>(probe_steps, e->horizon - n0[b]);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -759,8 +775,10 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
     e->schedules.clear();
     e->det_plans.clear();
     rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
-    for (int mode : modes) {
+    for (const auto& mt : modes) {
       if (rc) break;
+      const int mode = mt[0];
+      e->persistent_tma = mt[1];  // the probe runs capture no graph
       float ms_best = 1e30f;
       for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first repetition also warms up
         rc = restore();
@@ -784,6 +802,7 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
         best = ms_best;
         best_mode = mode;
         best_lz = lz;
+        best_tma = mt[1];
       }
     }
   }
@@ -793,6 +812,7 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
   for (void* s : saves) cudaFree(s);
   if (!rc) rc = rrc;
   e->item_lz = rc ? lz0 : best_lz;
+  e->persistent_tma = rc ? tma0 : best_tma;
   e->schedules.clear();
   e->det_plans.clear();
   const int brc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);

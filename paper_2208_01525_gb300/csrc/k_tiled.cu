@@ -875,9 +875,12 @@ __device__ __forceinline__ int upper_index(const long long* a, int n, long long 
   return lo;
 }
 
+// use_tma: fill interior tiles' ring slots by tensor copies from the box's
+// plan (tensor copies read through L2, so they see the positions another
+// CTA of the same persistent launch wrote and fenced)
 template <typename T, bool COHERENT>
 __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T>& B, int cur, const Coef<T>& c,
-                                             long long t) {
+                                             long long t, bool use_tma) {
   constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
   const int bx = (int)(t % B.gx);
   const int by = (int)((t / B.gx) % B.gy);
@@ -896,10 +899,7 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
   v.ny = B.ny;
   v.nz = B.nz;
   MeasureOut mo{nullptr, nullptr, nullptr};
-  // tensor copies in the per-step kernel only: in the persistent kernel,
-  // which runs many small work items per CTA, they made the 64^3 class 8%
-  // slower (30.8 against 33.4 G site-updates/s) and gained nothing overall
-  tile_run<T, TX, TY, MODE_WRITE, COHERENT, false>(smem, v, c, mo, bx, by, z0, z1, 0, COHERENT ? nullptr : B.tma[cur]);
+  tile_run<T, TX, TY, MODE_WRITE, COHERENT, false>(smem, v, c, mo, bx, by, z0, z1, 0, use_tma ? B.tma[cur] : nullptr);
 }
 
 // Persistent ensemble kernel: CTAs take work items (step k, box, tile) in
@@ -912,7 +912,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
                  EnsSched sc, const int* __restrict__ kstart, unsigned long long* ticket, unsigned* done, int* err,
-                 long long limit_ns, int inject) {
+                 long long limit_ns, int inject, int use_tma) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   __shared__ long long s_t;
@@ -958,7 +958,7 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
     __syncthreads();
     if (!s_go) break;
     const EnsBox<T>& B = boxes[s_box];
-    ens_run_item<T, true>(smem_raw, B, (dyn[s_box].cur + s_k) & 1, cs, s_t);
+    ens_run_item<T, true>(smem_raw, B, (dyn[s_box].cur + s_k) & 1, cs, s_t, use_tma != 0);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -979,7 +979,7 @@ k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, 
   const int box = sc.order[si];
   if (threadIdx.x == 0) cs = coef[boxes[box].coef0 + dyn[box].n + k];
   __syncthreads();
-  ens_run_item<T, false>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si]);
+  ens_run_item<T, false>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si], true);
 }
 
 // Measuring step k (a step fused with the diagnostic sums) of the boxes in
@@ -1073,7 +1073,7 @@ int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, in
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                                   const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
-                                  long long limit_ns, int inject, cudaStream_t st) {
+                                  long long limit_ns, int inject, int use_tma, cudaStream_t st) {
   const size_t bytes = ens_smem_bytes<T>();
   cudaError_t e = set_smem_attr(k_ens_persistent<T>, bytes);
   if (e != cudaSuccess) return e;
@@ -1086,7 +1086,7 @@ cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, con
   if (grid > sc.total) grid = sc.total;
   if (grid < 1) return cudaSuccess;
   k_ens_persistent<T><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
-                                                          inject);
+                                                          inject, use_tma);
   return cudaGetLastError();
 }
 
@@ -1120,10 +1120,10 @@ cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de
 
 template cudaError_t launch_ens_persistent<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*,
                                                   const EnsSched&, const int*, unsigned long long*, unsigned*, int*,
-                                                  long long, int, cudaStream_t);
+                                                  long long, int, int, cudaStream_t);
 template cudaError_t launch_ens_persistent<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,
                                                    const EnsSched&, const int*, unsigned long long*, unsigned*, int*,
-                                                   long long, int, cudaStream_t);
+                                                   long long, int, int, cudaStream_t);
 template cudaError_t launch_ens_measure<float>(const EnsBox<float>*, const EnsDet*, const EnsDyn*, const Coef<float>*,
                                                const int*, const long long*, int, long long, int, cudaStream_t);
 template cudaError_t launch_ens_measure<double>(const EnsBox<double>*, const EnsDet*, const EnsDyn*,

@@ -221,11 +221,12 @@ constexpr int ENS_LZ = 32;     // default z-chunk of an ensemble work item
 
 int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, int item_lz = ENS_LZ);
 // kstart (nullable): per box, the run step its first item of this launch
-// advances (a launch covering a segment of a run between detection steps)
+// advances (a launch covering a segment of a run between detection steps);
+// use_tma: interior tiles' ring slots filled by tensor copies
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                                   const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
-                                  long long limit_ns, int inject, cudaStream_t st);
+                                  long long limit_ns, int inject, int use_tma, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                             int k, long long items, cudaStream_t st);

@@ -166,20 +166,26 @@ def test_ensemble_autotune_keeps_states():
         assert torch.equal(ens.boxes[b].state(), alone(p, 6)), b
 
 
-@pytest.mark.parametrize("mode,graph", [(U.ENS_PERSISTENT, False), (U.ENS_PERSISTENT, True),
-                                        (U.ENS_PER_STEP, True), (U.ENS_UNBATCHED, False)])
-def test_ensemble_tensor_copy_boxes(mode, graph):
+@pytest.mark.parametrize("mode,graph,ptma", [(U.ENS_PERSISTENT, False, True), (U.ENS_PERSISTENT, True, True),
+                                             (U.ENS_PERSISTENT, False, False), (U.ENS_PERSISTENT, True, False),
+                                             (U.ENS_PER_STEP, True, True), (U.ENS_UNBATCHED, False, True)])
+@pytest.mark.parametrize("item_lz", [16, 64])
+def test_ensemble_tensor_copy_boxes(mode, graph, ptma, item_lz):
     """FP32 boxes wide and tall enough to have interior tiles, whose ring
-    slots the per-step ensemble kernel fills by tensor copies from per-box
-    tensor maps in device memory (the persistent kernel uses cp.async), next
-    to a box without interior tiles: every box equals the same box stepped
-    alone, bit for bit, in every mode and over graph replays."""
+    slots the ensemble kernels fill by tensor copies from per-box tensor maps
+    in device memory (the persistent kernel with tensor copies or with
+    cp.async, a tuning choice), next to a box without interior tiles: every
+    box equals the same box stepped alone, bit for bit, in every mode, for
+    two work-item z-chunks and over graph replays."""
     shapes = [(104, 32, 20), (136, 40, 12), (16, 16, 16)]
     ps = [U.Params(nx=nx, ny=ny, nz=nz, m=0.5, beta=1.0, eta0=1.0, eta_ref=3.0, seed=2000 + b, precision=U.FP32)
           for b, (nx, ny, nz) in enumerate(shapes)]
     steps = [6, 9, 4]
     reps = 2 if graph else 1
     ens = U.Ensemble(ps)
+    ens.set_tuning(item_lz=item_lz, persistent_tma=ptma)
+    with pytest.raises(U.U1U1Error):
+        ens.set_tuning(item_lz=48)
     for _ in range(reps):
         ens.run(steps, mode=mode, use_graph=graph)
     torch.cuda.synchronize()

@@ -743,3 +743,23 @@ def test_autotune_refuses_foreign_cache_entry(tmp_path):
     with pytest.raises(U.U1U1Error):
         b.set_tile_waves(96)
     assert choice["kernel"] in (U.KERNEL_TILED, U.KERNEL_SIMPLE)
+
+
+def test_fp64_rate_probe():
+    """The FP64 rate probe (the FP64 roofline's denominator) returns a rate
+    between a tenth and twice GB300's nominal 1.25 TFLOP/s of non-tensor
+    FP64, and the FP64 step, which does 389 FP64 operations per site,
+    cannot run faster than that rate allows."""
+    r = U.fp64_fma_rate()
+    assert 0.125 < r < 2.5, r
+    p = U.Params.cube(128, m=0.5, beta=1.0, eta0=1.0, eta_ref=65.0, seed=3, precision=U.FP64)
+    lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+    lat.step(2)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    lat.step(5)
+    b.record()
+    torch.cuda.synchronize()
+    achieved = 389 * p.nsites * 5 / (a.elapsed_time(b) * 1e-3) / 1e12
+    assert achieved < 1.05 * r, (achieved, r)
