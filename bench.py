@@ -336,7 +336,7 @@ def ensemble_bench(U, torch, dev):
 
     # one ensemble for every timed run (12 runs of up to 480 steps per box)
     ens = U.Ensemble(ps, device=dev, horizon=8192)
-    out["autotuned"] = ens.autotune(probe_steps=8)
+    out["autotuned"] = ens.autotune(probe_steps=24)
     for name, mode, graph in modes:
         out[name] = timed(ens, mode, graph, 0)
     out["speedup_vs_unbatched"] = out["persistent_graph"]["site_updates_per_s"] / \
@@ -362,7 +362,7 @@ def ensemble_bench(U, torch, dev):
     swork = sum(s_ * 64 ** 3 for s_ in ssteps)
     res = {}
     ens = U.Ensemble(small, device=dev, horizon=2048)
-    res["autotuned"] = ens.autotune(probe_steps=8)
+    res["autotuned"] = ens.autotune(probe_steps=24)
     for name, mode, graph in (("persistent_graph", U.ENS_PERSISTENT, True), ("unbatched", U.ENS_UNBATCHED, False)):
         ens.run(ssteps, mode=mode, use_graph=graph)
         torch.cuda.synchronize()

@@ -445,7 +445,8 @@ int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enable);
 /* Autotuner for ensembles: times a probe run of probe_steps steps of every
  * box for each work-item z-chunk (16, 32, 64, 128 planes) and schedule
  * (persistent with and without tensor copies of interior tiles, per-step),
- * restoring every box's state and step index after each trial (needs a
+ * each timed as a CUDA-graph replay after a capturing run, restoring every
+ * box's state and step index after each trial (needs a
  * temporary copy of the ensemble state), keeps the fastest z-chunk and
  * tensor-copy choice and returns the fastest schedule in *mode_out for
  * later u1u1_ensemble_run calls.  Synchronises `stream`.

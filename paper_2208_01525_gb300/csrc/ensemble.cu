@@ -778,13 +778,16 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
     for (const auto& mt : modes) {
       if (rc) break;
       const int mode = mt[0];
-      e->persistent_tma = mt[1];  // the probe runs capture no graph
+      e->persistent_tma = mt[1];
+      e->schedules.clear();  // graphs captured with another choice
       float ms_best = 1e30f;
-      for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first repetition also warms up
+      // timed as graph replays, as the runs it tunes are meant to be made:
+      // the first repetition captures the graph and warms up
+      for (int rep = 0; rep < 2 && !rc; ++rep) {
         rc = restore();
         if (rc) break;
         cudaEventRecord(ev0, st);
-        rc = u1u1_ensemble_run(e, steps.data(), 0, mode, 0, stream);
+        rc = u1u1_ensemble_run(e, steps.data(), 0, mode, 1, stream);
         cudaEventRecord(ev1, st);
         if (rc) break;
         if (cudaEventSynchronize(ev1) != cudaSuccess) {
