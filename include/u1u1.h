@@ -461,6 +461,10 @@ int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mode_out, int
  * `stream`.  Errors: INVALID_ARG, CUDA. */
 int u1u1_ensemble_set_tuning(u1u1_ensemble* e, int item_lz, int persistent_tma, void* stream);
 
+/* The ensemble's current tuning knobs (either output may be NULL).
+ * Errors: INVALID_ARG. */
+int u1u1_ensemble_get_tuning(const u1u1_ensemble* e, int* item_lz, int* persistent_tma);
+
 void u1u1_ensemble_destroy(u1u1_ensemble* e);
 
 /* ---- detection without device allocation ------------------------------------ */

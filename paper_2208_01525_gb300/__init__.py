@@ -352,11 +352,17 @@ class Ensemble:
                                       _stream_ptr(stream)))
 
     def autotune(self, probe_steps: int = 4, stream=None) -> dict:
-        """Pick the work-item z-chunk and schedule by timing (states unchanged)."""
+        """Pick the work-item z-chunk, the persistent kernel's tensor copies and
+        the schedule by timing (states unchanged)."""
         m, lz = ctypes.c_int(), ctypes.c_int()
         check(lib().u1u1_ensemble_autotune(self._h, int(probe_steps), ctypes.byref(m), ctypes.byref(lz),
                                            _stream_ptr(stream)))
-        return {"mode": m.value, "item_lz": lz.value}
+        return {"mode": m.value, "item_lz": lz.value, "persistent_tma": self.tuning()["persistent_tma"]}
+
+    def tuning(self) -> dict:
+        lz, t = ctypes.c_int(), ctypes.c_int()
+        check(lib().u1u1_ensemble_get_tuning(self._h, ctypes.byref(lz), ctypes.byref(t)))
+        return {"item_lz": lz.value, "persistent_tma": bool(t.value)}
 
     def set_tuning(self, item_lz: int = 32, persistent_tma: bool = True, stream=None):
         """Work-item z-chunk and the persistent kernel's tensor copies, without timing."""

@@ -141,6 +141,7 @@ PROTOTYPES = {
     "u1u1_ensemble_destroy": (None, [_vp]),
     "u1u1_ensemble_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int), _vp]),
     "u1u1_ensemble_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "u1u1_ensemble_get_tuning": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "u1u1_detect_strings_noalloc": (ctypes.c_int, [_P(CParams), _P(_vp), ctypes.c_int64, ctypes.c_int,
                                                    _P(CStrings), _vp]),
 }

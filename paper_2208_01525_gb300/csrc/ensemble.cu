@@ -701,6 +701,13 @@ extern "C" int u1u1_ensemble_inject_unreachable_wait(u1u1_ensemble* e, int enabl
 // autotuner: work-item z-chunk and schedule
 // ---------------------------------------------------------------------------
 
+extern "C" int u1u1_ensemble_get_tuning(const u1u1_ensemble* e, int* item_lz, int* persistent_tma) {
+  if (!e) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
+  if (item_lz) *item_lz = e->item_lz;
+  if (persistent_tma) *persistent_tma = e->persistent_tma;
+  return U1U1_OK;
+}
+
 extern "C" int u1u1_ensemble_set_tuning(u1u1_ensemble* e, int item_lz, int persistent_tma, void* stream) {
   if (!e) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
   if (item_lz != 16 && item_lz != 32 && item_lz != 64 && item_lz != 128)

@@ -76,13 +76,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned pa
 // never completed would be an arrival too many); the CTA finishes on stale
 // data.  A timed-out wait has given the slot's copies the whole limit to
 // land before the CTA can exit.
+// (The plan's status pointer is read only on that path: for ensembles the
+// plan lives in device memory, and a load per wait would sit on every
+// plane's critical path.)
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity, volatile int* cta_fail,
-                                                  long long limit, int* status) {
+                                                  long long limit, const TmaPlan* plan) {
   if (mbar_try_wait(m, parity)) return true;
   if (*cta_fail) return false;
   const long long t0 = gtimer_ns();
   while (!mbar_try_wait(m, parity)) {
     if (gtimer_ns() - t0 > limit) {
+      int* status = plan->status;
       if (status) atomicExch(status, U1U1_ERR_TIMEOUT);
       *cta_fail = 1;
       return false;
@@ -283,8 +287,7 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
   };
   bool copies_ok = true;  // every wait of this thread completed
   auto tma_wait = [&](int slot) {
-    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, wait_limit, tma->status) &&
-                copies_ok;
+    copies_ok = mbar_wait_bounded(&sm.mbar[slot], (phase >> slot) & 1u, &sm.tma_fail, wait_limit, tma) && copies_ok;
     phase ^= 1u << slot;
   };
   if (use_tma) {
@@ -875,12 +878,14 @@ __device__ __forceinline__ int upper_index(const long long* a, int n, long long 
   return lo;
 }
 
-// use_tma: fill interior tiles' ring slots by tensor copies from the box's
+// USE_TMA: fill interior tiles' ring slots by tensor copies from the box's
 // plan (tensor copies read through L2, so they see the positions another
-// CTA of the same persistent launch wrote and fenced)
-template <typename T, bool COHERENT>
+// CTA of the same persistent launch wrote and fenced); a compile-time
+// choice, since the tensor-copy path costs registers even where it is not
+// taken
+template <typename T, bool COHERENT, bool USE_TMA>
 __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T>& B, int cur, const Coef<T>& c,
-                                             long long t, bool use_tma) {
+                                             long long t) {
   constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
   const int bx = (int)(t % B.gx);
   const int by = (int)((t / B.gx) % B.gy);
@@ -899,7 +904,7 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
   v.ny = B.ny;
   v.nz = B.nz;
   MeasureOut mo{nullptr, nullptr, nullptr};
-  tile_run<T, TX, TY, MODE_WRITE, COHERENT, false>(smem, v, c, mo, bx, by, z0, z1, 0, use_tma ? B.tma[cur] : nullptr);
+  tile_run<T, TX, TY, MODE_WRITE, COHERENT, false>(smem, v, c, mo, bx, by, z0, z1, 0, USE_TMA ? B.tma[cur] : nullptr);
 }
 
 // Persistent ensemble kernel: CTAs take work items (step k, box, tile) in
@@ -908,11 +913,11 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
 // bounded: past limit_ns the kernel records U1U1_ERR_TIMEOUT and all CTAs
 // return.  Deadlock freedom: tickets are taken only by running CTAs and an
 // item depends only on items with smaller tickets.
-template <typename T>
+template <typename T, bool USE_TMA>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
                  EnsSched sc, const int* __restrict__ kstart, unsigned long long* ticket, unsigned* done, int* err,
-                 long long limit_ns, int inject, int use_tma) {
+                 long long limit_ns, int inject) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   __shared__ long long s_t;
@@ -958,7 +963,7 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
     __syncthreads();
     if (!s_go) break;
     const EnsBox<T>& B = boxes[s_box];
-    ens_run_item<T, true>(smem_raw, B, (dyn[s_box].cur + s_k) & 1, cs, s_t, use_tma != 0);
+    ens_run_item<T, true, USE_TMA>(smem_raw, B, (dyn[s_box].cur + s_k) & 1, cs, s_t);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -979,7 +984,7 @@ k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, 
   const int box = sc.order[si];
   if (threadIdx.x == 0) cs = coef[boxes[box].coef0 + dyn[box].n + k];
   __syncthreads();
-  ens_run_item<T, false>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si], true);
+  ens_run_item<T, false, true>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si]);
 }
 
 // Measuring step k (a step fused with the diagnostic sums) of the boxes in
@@ -1045,9 +1050,11 @@ size_t ens_smem_bytes() {
   return sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, false, false>);
 }
 
+// The dynamic shared-memory limit is a per-device function attribute; the
+// caller keeps one `configured` array per kernel (kernels of one signature
+// share a function-pointer type, so a static here would be shared by them).
 template <typename KernelT>
-cudaError_t set_smem_attr(KernelT kernel, size_t bytes) {
-  static bool configured[64] = {};
+cudaError_t set_smem_attr(KernelT kernel, size_t bytes, bool (&configured)[64]) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1070,24 +1077,36 @@ int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, in
   return *gx * *gy * *gz;
 }
 
-template <typename T>
-cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
-                                  const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
-                                  long long limit_ns, int inject, int use_tma, cudaStream_t st) {
+template <typename T, bool USE_TMA>
+cudaError_t launch_ens_persistent_t(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef,
+                                    const EnsSched& sc, const int* kstart, unsigned long long* ticket, unsigned* done,
+                                    int* err, long long limit_ns, int inject, cudaStream_t st) {
+  static bool configured[64] = {};
   const size_t bytes = ens_smem_bytes<T>();
-  cudaError_t e = set_smem_attr(k_ens_persistent<T>, bytes);
+  cudaError_t e = set_smem_attr(k_ens_persistent<T, USE_TMA>, bytes, configured);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<T>, 256, bytes)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<T, USE_TMA>, 256, bytes)) !=
+      cudaSuccess)
     return e;
   long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
   if (grid > sc.total) grid = sc.total;
   if (grid < 1) return cudaSuccess;
-  k_ens_persistent<T><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
-                                                          inject, use_tma);
+  k_ens_persistent<T, USE_TMA><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done, err,
+                                                                   limit_ns, inject);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
+                                  const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
+                                  long long limit_ns, int inject, int use_tma, cudaStream_t st) {
+  return use_tma ? launch_ens_persistent_t<T, true>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns, inject,
+                                                    st)
+                 : launch_ens_persistent_t<T, false>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
+                                                     inject, st);
 }
 
 template <typename T>
@@ -1095,7 +1114,8 @@ cudaError_t launch_ens_measure(const EnsBox<T>* boxes, const EnsDet* det, const 
                                const int* list, const long long* pre, int nlist, long long items, int k,
                                cudaStream_t st) {
   const size_t bytes = sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, true, false>);
-  cudaError_t e = set_smem_attr(k_ens_measure<T>, bytes);
+  static bool configured[64] = {};
+  cudaError_t e = set_smem_attr(k_ens_measure<T>, bytes, configured);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
   k_ens_measure<T><<<(unsigned)items, 256, bytes, st>>>(boxes, det, dyn, coef, list, pre, nlist, k);
@@ -1106,7 +1126,8 @@ template <typename T>
 cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                             int k, long long items, cudaStream_t st) {
   const size_t bytes = ens_smem_bytes<T>();
-  cudaError_t e = set_smem_attr(k_ens_step<T>, bytes);
+  static bool configured[64] = {};
+  cudaError_t e = set_smem_attr(k_ens_step<T>, bytes, configured);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
   k_ens_step<T><<<(unsigned)items, 256, bytes, st>>>(boxes, dyn, coef, sc, k);

@@ -184,6 +184,7 @@ def test_ensemble_tensor_copy_boxes(mode, graph, ptma, item_lz):
     reps = 2 if graph else 1
     ens = U.Ensemble(ps)
     ens.set_tuning(item_lz=item_lz, persistent_tma=ptma)
+    assert ens.tuning() == {"item_lz": item_lz, "persistent_tma": ptma}
     with pytest.raises(U.U1U1Error):
         ens.set_tuning(item_lz=48)
     for _ in range(reps):
