@@ -555,14 +555,16 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
           mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q] = fmax(mx[s == 0 ? M_NEG_PHIMIN_P : M_NEG_PHIMIN_Q], -mod2[s]);
           mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q] = fmax(mx[s == 0 ? M_PHIMAX_P : M_PHIMAX_Q], mod2[s]);
         }
-        // NaN entries among the site's 20 fields: their sum is finite unless
-        // one of them is NaN or infinite (or the sum overflows), and only
-        // then are they counted one by one
-        T all = pr[0] + pim[0] + pr[1] + pim[1];
+        // NaN entries among the site's 20 fields, counted one by one only
+        // where the site's ten new momenta do not sum to a finite number:
+        // every one of its own fields enters one of them (phi and pi the
+        // scalar kick, A and E the gauge kick) with a coefficient that
+        // keeps a NaN or an infinity non-finite, so no NaN field is missed
+        // (a non-finite neighbour or an overflow only triggers a recount
+        // that finds nothing); ten additions instead of twenty
+        T all = (prn[0] + pin_[0]) + (prn[1] + pin_[1]);
 #pragma unroll
-        for (int s = 0; s < 2; ++s) all += E[s][0] + E[s][1] + E[s][2];
-#pragma unroll
-        for (int f = 0; f < U1U1_NPOS; ++f) all += sm.pos[bc][f][a];
+        for (int s = 0; s < 2; ++s) all += En[s][0] + En[s][1] + En[s][2];
         if (!isfinite(all)) {
           int nan = 0;
 #pragma unroll

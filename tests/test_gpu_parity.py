@@ -763,3 +763,27 @@ def test_fp64_rate_probe():
     torch.cuda.synchronize()
     achieved = 389 * p.nsites * 5 / (a.elapsed_time(b) * 1e-3) / 1e12
     assert achieved < 1.05 * r, (achieved, r)
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_nan_fields_counted(prec, kernel):
+    """NaN entries planted in a smooth state -- in a position, a momentum and
+    an electric field at three sites, two of them at the same site, plus an
+    infinity elsewhere -- are counted exactly as the oracle counts them (the
+    infinity is not a NaN), by the diagnostics pass and by a fused
+    detection step."""
+    p = U.Params(nx=40, ny=16, nz=12, m=0.0, precision=prec)
+    st = synth.smooth_state(p.shape, seed=3)
+    st[0][3, 4, 5] = np.nan     # phi re
+    st[12][3, 4, 5] = np.nan    # Psi re, same site
+    st[17][7, 9, 33] = np.nan   # H_0
+    st[8][1, 2, 3] = np.inf     # B_1
+    lat = U.Lattice(p, kernel=kernel)
+    lat.set_state(st)
+    od = O.diagnostics(to_oracle(p), st, 0)
+    assert od["nan_count"] == 3
+    assert lat.diagnostics()["nan_count"] == 3
+    lat.step(1, detect_every=1)
+    (s, d), = lat.read_records()[0]
+    assert d["nan_count"] == 3
