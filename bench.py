@@ -42,6 +42,7 @@ BYTES_PER_SITE = {"fp32": 160, "fp64": 320}  # read 20 + write 20 words
 # FP64 rate measured in the same run by the library's FMA probe (nominal
 # GB300 non-tensor FP64: 1.25 TFLOP/s, used only if the probe fails)
 FP64_FLOPS_PER_SITE = 389
+FP64_INSTR_PER_SITE = 126 + 60 + 77  # FP64 pipe instructions (DFMA, DADD, DMUL) per site
 FP64_NOMINAL_TFLOPS = 1.25
 # standalone string detection: the windings kernel reads the ten position
 # fields (40 B/site in FP32) and writes 2 face bytes per site, the cell pass
@@ -589,9 +590,14 @@ def run_ours(args):
             fp64 = {"lattice": n64, "value": p64.nsites / (t64 * 1e-3), "unit": "site-updates/s",
                     "ms_per_step": t64,
                     "hbm_frac": BYTES_PER_SITE["fp64"] * p64.nsites / (t64 * 1e-3) / 1e9 / peak,
+                    # instr_frac: the same time against the probe's rate of FP64
+                    # instructions (one FMA = two operations), counting DADD and
+                    # DMUL, which occupy the pipe like an FMA, as one each
                     "roofline": {"bound": "alu", "achieved": tflops, "peak": fp64_peak,
                                  "unit": "TFLOP/s (FP64)", "frac": tflops / fp64_peak,
-                                 "peak_kind": fp64_kind, "flops_per_site": FP64_FLOPS_PER_SITE},
+                                 "peak_kind": fp64_kind, "flops_per_site": FP64_FLOPS_PER_SITE,
+                                 "instr_per_site": FP64_INSTR_PER_SITE,
+                                 "instr_frac": FP64_INSTR_PER_SITE * p64.nsites / (t64 * 1e-3) / 1e12 / (fp64_peak / 2)},
                     "steps": args.fp64_steps}
             lat64.close()
             del lat64
