@@ -276,3 +276,25 @@ def test_ensemble_detection_overlap_tolerance_and_oracle():
     for k in ("kin_p", "grad_q", "el_p", "mag_q", "pot", "vint"):
         assert abs(d[k] - od[k]) <= 1e-10 * max(abs(od[k]), abs(od["energy"])), k
     ens.close()
+
+
+@pytest.mark.parametrize("mode", [U.ENS_PERSISTENT, U.ENS_PER_STEP])
+def test_ensemble_detection_two_stage_finalize(mode):
+    """A 256^3 box has more block partials (4712) than one finalize CTA
+    takes, so its batched detection runs the two-stage merge, next to a box
+    that needs one stage: both boxes' records equal those of the boxes
+    stepped alone, sums bit for bit."""
+    ps = [U.Params.cube(256, m=0.5, beta=1.0, eta0=1.0, eta_ref=65.0, seed=31),
+          U.Params(nx=40, ny=24, nz=20, m=2.0 / 3.0, beta=0.0, eta0=1.0, eta_ref=1.0, seed=32)]
+    ens = U.Ensemble(ps)
+    ens.run([8, 8], mode=mode, use_graph=True, detect_every=4)
+    for b, p in enumerate(ps):
+        ref = U.Lattice(p, kernel=U.KERNEL_TILED)
+        ref.step(8, detect_every=4)
+        want, _ = ref.read_records()
+        got, _ = ens.boxes[b].read_records()
+        assert [r[0]["n"] for r in got] == [r[0]["n"] for r in want] == [0, 4]
+        for (gs, gd), (ws, wd) in zip(got, want):
+            assert _same_record(gs, ws) and _same_record(gd, wd), b
+        ref.close()
+    ens.close()

@@ -59,15 +59,22 @@ def oracle_run(p, phases, st):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("era,physical", [("radiation", True), ("matter", True), ("matter", False)])
-def test_schedule_gpu_matches_oracle(era, physical):
+@pytest.mark.parametrize("era,physical,unequal", [("radiation", True, False), ("matter", True, False),
+                                                  ("matter", False, False), ("radiation", True, True)])
+def test_schedule_gpu_matches_oracle(era, physical, unequal):
+    """The whole run schedule (cooling flow, damping, core growth, physical
+    evolution), FP64 GPU against the oracle; the last case with every
+    per-sector coupling different (the cooling flow's per-sector
+    coefficients included)."""
     torch = pytest.importorskip("torch")
-    base = U.Params(nx=20, ny=16, nz=12, seed=21, precision=U.FP64)
+    kw = dict(lambda_p=2.0, lambda_q=1.62, e_p=1.0, e_q=0.9, sigma_p=1.0, sigma_q=0.8, kappa=0.5) if unequal else {}
+    base = U.Params(nx=20, ny=16, nz=12, seed=21, precision=U.FP64, **kw)
     phases = S.paper_schedule(base, era, physical=physical, eta_end=9.0, eta_tr=7.0)
     lat = U.Lattice(base)
     S.run(lat, phases)
     got = lat.state().cpu().numpy()
-    p0 = O.Params(20, 16, 12, seed=21)
+    p0 = O.Params(20, 16, 12, seed=21, lam=(base.lambda_p, base.lambda_q), e=(base.e_p, base.e_q),
+                  sigma=(base.sigma_p, base.sigma_q), kappa=base.kappa)
     ref = oracle_run(p0, phases, O.init(p0))
     # relative to each field's maximum, but never to a scale below the unit
     # vacuum value: after the heavily damped phase (m_damp gives delta ~ 2)
