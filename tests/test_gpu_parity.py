@@ -434,6 +434,8 @@ def test_full_size_sampled_sites(n, prec):
     properties (even cells, sum of cells = 2 sum |W|) hold everywhere.  The
     largest case is the FP64 1024^3 box (258 GB of fields)."""
     if n == 1024:
+        import gc
+        gc.collect()  # handles and tensors of earlier tests
         torch.cuda.empty_cache()
         free = torch.cuda.mem_get_info()[0]
         need = 150e9 if prec == U.FP32 else 285e9
