@@ -94,3 +94,17 @@ def test_null_handles_are_rejected_without_gpu():
     assert L.u1u1_current(None, None, None) == -1
     assert L.u1u1_set_overlap_tol(None, 1) == -1
     L.u1u1_destroy(None)
+
+
+def test_ensemble_and_probe_entry_points_reject_bad_arguments_without_gpu():
+    """Argument checks that come before any device work: NULL handles and
+    outputs, a negative detection cadence, unknown modes."""
+    L = U.lib()
+    steps = (ctypes.c_int * 2)(1, 1)
+    assert L.u1u1_ensemble_run(None, steps, 0, 0, 0, None) == -1
+    assert L.u1u1_ensemble_set_tuning(None, 32, 1, None) == -1
+    assert L.u1u1_ensemble_get_tuning(None, None, None) == -1
+    assert L.u1u1_ensemble_autotune(None, 4, None, None, None) == -1
+    assert L.u1u1_fp64_fma_rate(None, None) == -1
+    assert L.u1u1_inject_copy_timeout(1, 10) == -1  # limit below 1000 ns
+    L.u1u1_ensemble_destroy(None)
