@@ -799,3 +799,51 @@ def test_nan_fields_counted(prec, kernel):
     lat.step(1, detect_every=1)
     (s, d), = lat.read_records()[0]
     assert d["nan_count"] == 3
+
+
+def _swap_sectors(st):
+    """phi <-> psi, A <-> B, Pi <-> Psi, E <-> H in a (20, ...) state."""
+    idx = [2, 3, 0, 1, 7, 8, 9, 4, 5, 6, 12, 13, 10, 11, 17, 18, 19, 14, 15, 16]
+    return st[idx]
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_sector_symmetries_on_gpu(prec, kernel):
+    """The symmetries of Sec. II on the GPU kernels, bit for bit: exchanging
+    the sectors' fields and couplings exchanges the results of 6 steps (a
+    p/q mix-up of any per-sector coefficient or field index breaks it), the
+    windings and string counts swap likewise; and with kappa = 0 the p
+    sector evolves independently of anything done to the q sector."""
+    kw = dict(m=0.5, beta=-1.0, eta0=1.0, eta_ref=1.0)
+    p = U.Params(nx=36, ny=20, nz=12, precision=prec, **kw, **UNEQUAL)
+    q = U.Params(nx=36, ny=20, nz=12, precision=prec, **kw, lambda_p=UNEQUAL["lambda_q"],
+                 lambda_q=UNEQUAL["lambda_p"], e_p=UNEQUAL["e_q"], e_q=UNEQUAL["e_p"],
+                 sigma_p=UNEQUAL["sigma_q"], sigma_q=UNEQUAL["sigma_p"], kappa=UNEQUAL["kappa"])
+    st = synth.random_state(p.shape, seed=23, a_amp=1.0, mom_amp=0.5)
+    a = U.Lattice(p, kernel=kernel)
+    a.set_state(st)
+    b = U.Lattice(q, kernel=kernel)
+    b.set_state(_swap_sectors(st))
+    sa, sb = a.detect_strings(tol=0), b.detect_strings(tol=0)
+    for k1, k2 in (("n_p", "n_q"), ("nonzero_p", "nonzero_q"), ("n_w2_p", "n_w2_q")):
+        assert sa[k1] == sb[k2] and sa[k2] == sb[k1], k1
+    assert sa["n_pq_plaq"] == sb["n_pq_plaq"] and sa["n_pq_cell"] == sb["n_pq_cell_q"]
+    a.step(6)
+    b.step(6)
+    assert torch.equal(a.state(), _swap_sectors(b.state()))
+    # kappa = 0: the q sector cannot act on the p sector
+    p0 = U.Params(nx=36, ny=20, nz=12, precision=prec, **kw, **dict(UNEQUAL, kappa=0.0))
+    c = U.Lattice(p0, kernel=kernel)
+    c.set_state(st)
+    st2 = st.copy()
+    st2[2:4] *= 1.7          # psi
+    st2[[7, 8, 9]] += 0.3    # B
+    st2[[12, 13]] -= 0.2     # Psi
+    st2[[17, 18, 19]] *= 0.5  # H
+    d = U.Lattice(p0, kernel=kernel)
+    d.set_state(st2)
+    c.step(6)
+    d.step(6)
+    pfields = [0, 1, 4, 5, 6, 10, 11, 14, 15, 16]
+    assert torch.equal(c.state()[pfields], d.state()[pfields])
