@@ -490,6 +490,9 @@ def test_wave_targets_agree_bit_exact():
     chunks of 300, 150, 75, 38 (ragged last chunk of 34) and 32 (ragged last
     chunk of 12) planes, so chunk prologues and their carries fall on
     different planes; 1024-wide rows put most tiles on tensor copies."""
+    import gc
+    gc.collect()  # earlier tests' objects, and the blocks the allocator keeps for them
+    torch.cuda.empty_cache()
     free = torch.cuda.mem_get_info()[0]
     if free < 100e9:
         pytest.skip("needs ~90 GB of free device memory")

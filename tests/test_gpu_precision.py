@@ -73,6 +73,9 @@ def test_fp32_sums_match_fp64_summation_512():
     network from random phases) in an FP32 and, widened exactly, in an FP64
     lattice: the FP32 measuring pass's compensated sums against the FP64
     pass's over 134 M sites."""
+    import gc
+    gc.collect()  # earlier tests' objects, and the blocks the allocator keeps for them
+    torch.cuda.empty_cache()
     free = torch.cuda.mem_get_info()[0]
     if free < 60e9:
         pytest.skip("needs ~50 GB of free device memory")
