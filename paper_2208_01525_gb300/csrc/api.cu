@@ -430,6 +430,7 @@ static cudaError_t strings_pass(u1u1_lattice* h, int8_t* windings, cudaStream_t 
 }
 
 extern "C" int u1u1_step(u1u1_lattice* h, int nsteps, int detect_every, void* stream) {
+  const NvtxRange range("u1u1_step");
   if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
   if (nsteps < 0) return fail(U1U1_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (detect_every < 0) return fail(U1U1_ERR_INVALID_ARG, "detect_every must be >= 0");
@@ -660,6 +661,7 @@ static int read_scratch(u1u1_lattice* h, RawRecord* r, cudaStream_t st) {
 
 extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* cell_p, uint8_t* cell_q,
                                    int8_t* windings, u1u1_strings* out, void* stream) {
+  const NvtxRange range("u1u1_detect_strings");
   if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
   if (overlap_tol < 0 || overlap_tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
   if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
@@ -682,6 +684,7 @@ extern "C" int u1u1_detect_strings(u1u1_lattice* h, int overlap_tol, uint8_t* ce
 
 extern "C" int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells, int32_t* labels_out,
                                 u1u1_segments* out, void* stream) {
+  const NvtxRange range("u1u1_pq_segments");
   if (!h || !out) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
   if (overlap_tol < 0 || overlap_tol > 1) return fail(U1U1_ERR_INVALID_ARG, "overlap tolerance must be 0 or 1");
   if (min_cells < 0) return fail(U1U1_ERR_INVALID_ARG, "min_cells must be >= 0");
@@ -735,6 +738,7 @@ extern "C" int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells,
 }
 
 extern "C" int u1u1_diagnostics(u1u1_lattice* h, u1u1_diag* out, void* stream) {
+  const NvtxRange range("u1u1_diagnostics");
   if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
   if (!out) return fail(U1U1_ERR_INVALID_ARG, "out is NULL");
   cudaStream_t st = (cudaStream_t)stream;

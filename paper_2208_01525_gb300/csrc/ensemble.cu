@@ -564,6 +564,7 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
 
 extern "C" int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int detect_every, int mode, int use_graph,
                                  void* stream) {
+  const NvtxRange range("u1u1_ensemble_run");
   if (!e || !steps) return fail(U1U1_ERR_INVALID_ARG, "NULL argument");
   if (mode < U1U1_ENS_PERSISTENT || mode > U1U1_ENS_UNBATCHED) return fail(U1U1_ERR_INVALID_ARG, "unknown mode %d", mode);
   if (detect_every < 0) return fail(U1U1_ERR_INVALID_ARG, "detect_every must be >= 0");

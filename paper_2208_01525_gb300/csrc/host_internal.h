@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -22,6 +23,15 @@ int cuda_fail(cudaError_t e, const char* where);
     cudaError_t e_ = (expr);                            \
     if (e_ != cudaSuccess) return ::u1u1::cuda_fail(e_, where); \
   } while (0)
+
+// A named range on the host timeline around an entry point's enqueue work,
+// for profilers that read NVTX (free when none is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // step coefficients of step n (Eqs. 12, 19, 22), FP64
 void coeffs(const u1u1_params* p, int64_t n, double out[6]);
