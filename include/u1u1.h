@@ -380,6 +380,21 @@ int u1u1_set_tile_waves(u1u1_lattice* h, int waves);
  * Errors: INVALID_ARG. */
 int u1u1_inject_copy_timeout(int enable, int64_t limit_ns);
 
+/* Failure-detection test hook and accounting for the library's own
+ * allocations: device scratch, tables and page-locked record buffers of
+ * handles and ensembles (never the caller's field arrays).
+ * u1u1_inject_alloc_failure(nth): nth >= 1 makes the nth allocation the
+ * library attempts from now on fail as if the device were out of memory
+ * (nothing is allocated and the device is not touched); the call that
+ * needed it releases what it had taken and returns OUT_OF_MEMORY, leaving
+ * the handle or ensemble it was called on as it was.  The hook fires once;
+ * nth = 0 disarms it.  Process-wide.  Errors: INVALID_ARG (nth < 0).
+ * u1u1_live_allocations: number and total bytes of the library allocations
+ * held at the moment by every handle and ensemble of the process.  Neither
+ * call needs a GPU. */
+int u1u1_inject_alloc_failure(int nth);
+int u1u1_live_allocations(int64_t* count, int64_t* bytes);
+
 /* ---- ensembles of independent boxes ---------------------------------------- */
 
 /* How u1u1_ensemble_run schedules the boxes' steps. */

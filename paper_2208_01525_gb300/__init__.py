@@ -91,6 +91,19 @@ def fp64_fma_rate(stream=None) -> float:
     return v.value
 
 
+def inject_alloc_failure(nth: int) -> None:
+    """Make the nth library allocation from now on fail as out of memory
+    (0 disarms the hook)."""
+    check(lib().u1u1_inject_alloc_failure(int(nth)))
+
+
+def live_allocations() -> tuple:
+    """(count, bytes) of the library's own allocations held at the moment."""
+    c, b = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().u1u1_live_allocations(ctypes.byref(c), ctypes.byref(b)))
+    return c.value, b.value
+
+
 def check_params(p: Params) -> None:
     check(lib().u1u1_check_params(ctypes.byref(p.c())))
 

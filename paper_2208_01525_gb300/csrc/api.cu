@@ -34,7 +34,8 @@ int fail(int code, const char* fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char* where) {
-  return fail(U1U1_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  return fail(e == cudaErrorMemoryAllocation ? U1U1_ERR_OUT_OF_MEMORY : U1U1_ERR_CUDA, "%s: %s", where,
+              cudaGetErrorString(e));
 }
 
 }  // namespace u1u1
@@ -202,20 +203,20 @@ static int check_buffers(const u1u1_params* p, const u1u1_buffers* b) {
 
 void u1u1::lattice_free_scratch(u1u1_lattice* h) {
   if (!h) return;
-  cudaFree(h->faces);
-  cudaFree(h->ge4);
-  cudaFree(h->masks);
-  cudaFree(h->mpq);
-  cudaFree(h->seg_label);
-  cudaFree(h->seg_size);
-  cudaFree(h->seg_counts);
-  cudaFree(h->partials);
-  cudaFree(h->cpartials);
-  cudaFree(h->ring);
-  cudaFree(h->scratch_rec);
-  cudaFree(h->tma_status);
-  cudaFreeHost(h->host_rec);
-  cudaFreeHost(h->host_status);
+  dev_free(h->faces);
+  dev_free(h->ge4);
+  dev_free(h->masks);
+  dev_free(h->mpq);
+  dev_free(h->seg_label);
+  dev_free(h->seg_size);
+  dev_free(h->seg_counts);
+  dev_free(h->partials);
+  dev_free(h->cpartials);
+  dev_free(h->ring);
+  dev_free(h->scratch_rec);
+  dev_free(h->tma_status);
+  host_free(h->host_rec);
+  host_free(h->host_status);
 }
 
 int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out) {
@@ -241,20 +242,20 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   }
   h->ncpartials = cells_grid_blocks();
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->faces, 2 * h->V);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->ge4, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = dev_alloc(&h->faces, 2 * h->V);
+  if (e == cudaSuccess) e = dev_alloc(&h->ge4, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess)
-    e = cudaMalloc((void**)&h->masks, 2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
+    e = dev_alloc(&h->masks, 2 * sizeof(uint32_t) * cell_mask_words(p->nx, p->ny, p->nz));
   // block partials, plus the finalize's first-stage slots after the last one
   if (e == cudaSuccess)
-    e = cudaMalloc((void**)&h->partials, sizeof(BlockPartial) * (size_t)(h->npartials + FIN_STAGE_BLOCKS));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->cpartials, sizeof(CellPartial) * (size_t)h->ncpartials);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->ring, sizeof(RawRecord) * RING_CAP);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->scratch_rec, sizeof(RawRecord));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_rec, sizeof(RawRecord) * RING_CAP);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->tma_status, sizeof(int));
+    e = dev_alloc(&h->partials, sizeof(BlockPartial) * (size_t)(h->npartials + FIN_STAGE_BLOCKS));
+  if (e == cudaSuccess) e = dev_alloc(&h->cpartials, sizeof(CellPartial) * (size_t)h->ncpartials);
+  if (e == cudaSuccess) e = dev_alloc(&h->ring, sizeof(RawRecord) * RING_CAP);
+  if (e == cudaSuccess) e = dev_alloc(&h->scratch_rec, sizeof(RawRecord));
+  if (e == cudaSuccess) e = host_alloc(&h->host_rec, sizeof(RawRecord) * RING_CAP);
+  if (e == cudaSuccess) e = dev_alloc(&h->tma_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->tma_status, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_status, sizeof(int));
+  if (e == cudaSuccess) e = host_alloc(&h->host_status, sizeof(int));
   if (e != cudaSuccess) {
     lattice_free_scratch(h);
     free(h);
@@ -692,15 +693,15 @@ extern "C" int u1u1_pq_segments(u1u1_lattice* h, int overlap_tol, int min_cells,
   cudaStream_t st = (cudaStream_t)stream;
   if (!h->seg_size) {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->mpq, sizeof(uint32_t) * cell_mask_words(h->p.nx, h->p.ny, h->p.nz));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->seg_label, sizeof(int) * h->V);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->seg_size, sizeof(int) * h->V);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->seg_counts, sizeof(SegCounts));
+    if (e == cudaSuccess) e = dev_alloc(&h->mpq, sizeof(uint32_t) * cell_mask_words(h->p.nx, h->p.ny, h->p.nz));
+    if (e == cudaSuccess) e = dev_alloc(&h->seg_label, sizeof(int) * h->V);
+    if (e == cudaSuccess) e = dev_alloc(&h->seg_size, sizeof(int) * h->V);
+    if (e == cudaSuccess) e = dev_alloc(&h->seg_counts, sizeof(SegCounts));
     if (e != cudaSuccess) {
-      cudaFree(h->mpq);
-      cudaFree(h->seg_label);
-      cudaFree(h->seg_size);
-      cudaFree(h->seg_counts);
+      dev_free(h->mpq);
+      dev_free(h->seg_label);
+      dev_free(h->seg_size);
+      dev_free(h->seg_counts);
       h->mpq = nullptr;
       h->seg_label = h->seg_size = nullptr;
       h->seg_counts = nullptr;
@@ -1059,7 +1060,7 @@ extern "C" int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kerne
     // the state is unchanged afterwards
     const size_t bytes = h->V * h->esize;
     void* save = nullptr;
-    cudaError_t e = cudaMalloc(&save, bytes * U1U1_NMOM);
+    cudaError_t e = dev_alloc(&save, bytes * U1U1_NMOM);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(U1U1_ERR_OUT_OF_MEMORY, "autotune needs %zu bytes to save the momenta", bytes * U1U1_NMOM);
@@ -1110,7 +1111,7 @@ extern "C" int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kerne
     if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "autotune sync");
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(save);
+    dev_free(save);
     if (rc) {
       h->kernel = kernel0;
       h->tile_waves = waves0;

@@ -33,10 +33,10 @@ struct Schedule {
   ~Schedule() {
     for (auto& g : graph)
       if (g) cudaGraphExecDestroy(g);
-    cudaFree(d_order);
-    cudaFree(d_steps);
-    cudaFree(d_box_prefix);
-    cudaFree(d_step_off);
+    dev_free(d_order);
+    dev_free(d_steps);
+    dev_free(d_box_prefix);
+    dev_free(d_step_off);
   }
 };
 
@@ -75,8 +75,8 @@ struct DetPlan {
   ~DetPlan() {
     for (auto& g : graph)
       if (g) cudaGraphExecDestroy(g);
-    cudaFree(d_int);
-    cudaFree(d_ll);
+    dev_free(d_int);
+    dev_free(d_ll);
   }
 };
 
@@ -141,12 +141,12 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
       make_tma_plan<T>(hb[b].pos[k], hb[b].nx, hb[b].ny, hb[b].nz, &hp[2 * b + k]);
       hp[2 * b + k].status = e->d_err + 1;  // a copy timeout is this ensemble's, reported by its status
     }
-  if (!e->d_tma) U1U1_CUDA_TRY(cudaMalloc((void**)&e->d_tma, sizeof(TmaPlan) * hp.size()), "ensemble tensor maps");
+  if (!e->d_tma) U1U1_CUDA_TRY(dev_alloc(&e->d_tma, sizeof(TmaPlan) * hp.size()), "ensemble tensor maps");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_tma, hp.data(), sizeof(TmaPlan) * hp.size(), cudaMemcpyHostToDevice),
                 "tensor map copy");
   for (int b = 0; b < nb; ++b)
     for (int k = 0; k < 2; ++k) hb[b].tma[k] = e->d_tma + 2 * b + k;
-  if (!e->d_boxes) U1U1_CUDA_TRY(cudaMalloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
+  if (!e->d_boxes) U1U1_CUDA_TRY(dev_alloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_boxes, hb.data(), sizeof(EnsBox<T>) * nb, cudaMemcpyHostToDevice), "box table copy");
   // detection resources: each box's own handle scratch, and the grids of a
   // single lattice's measuring and windings passes of its shape
@@ -172,7 +172,7 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
     if (D.nmeas + D.nwind > h->npartials)
       return fail(U1U1_ERR_STATE, "box %d: detection partials exceed the handle's buffer", b);
   }
-  if (!e->d_det) U1U1_CUDA_TRY(cudaMalloc((void**)&e->d_det, sizeof(EnsDet) * nb), "detection table");
+  if (!e->d_det) U1U1_CUDA_TRY(dev_alloc(&e->d_det, sizeof(EnsDet) * nb), "detection table");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_det, e->hdet.data(), sizeof(EnsDet) * nb, cudaMemcpyHostToDevice),
                 "detection table copy");
   if (e->d_coef) return U1U1_OK;  // a re-tiling keeps the coefficient table
@@ -180,7 +180,7 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
   std::vector<Coef<T>> hc((size_t)nb * e->horizon);
   for (int b = 0; b < nb; ++b)
     for (int n = 0; n < e->horizon; ++n) hc[(size_t)b * e->horizon + n] = make_coef<T>(&e->boxes[b]->p, n);
-  U1U1_CUDA_TRY(cudaMalloc(&e->d_coef, sizeof(Coef<T>) * hc.size()), "coefficient table");
+  U1U1_CUDA_TRY(dev_alloc(&e->d_coef, sizeof(Coef<T>) * hc.size()), "coefficient table");
   U1U1_CUDA_TRY(cudaMemcpy(e->d_coef, hc.data(), sizeof(Coef<T>) * hc.size(), cudaMemcpyHostToDevice),
                 "coefficient copy");
   (void)st;
@@ -210,10 +210,10 @@ int make_schedule(u1u1_ensemble* e, const std::vector<int>& steps, Schedule** ou
     s->items_per_step[k] = prefix[active];
     off[k + 1] = off[k] + prefix[active];
   }
-  U1U1_CUDA_TRY(cudaMalloc(&s->d_order, sizeof(int) * std::max(nb, 1)), "schedule");
-  U1U1_CUDA_TRY(cudaMalloc(&s->d_steps, sizeof(int) * std::max(nb, 1)), "schedule");
-  U1U1_CUDA_TRY(cudaMalloc(&s->d_box_prefix, sizeof(long long) * (nb + 1)), "schedule");
-  U1U1_CUDA_TRY(cudaMalloc(&s->d_step_off, sizeof(long long) * (smax + 1)), "schedule");
+  U1U1_CUDA_TRY(dev_alloc(&s->d_order, sizeof(int) * std::max(nb, 1)), "schedule");
+  U1U1_CUDA_TRY(dev_alloc(&s->d_steps, sizeof(int) * std::max(nb, 1)), "schedule");
+  U1U1_CUDA_TRY(dev_alloc(&s->d_box_prefix, sizeof(long long) * (nb + 1)), "schedule");
+  U1U1_CUDA_TRY(dev_alloc(&s->d_step_off, sizeof(long long) * (smax + 1)), "schedule");
   U1U1_CUDA_TRY(cudaMemcpy(s->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice), "schedule");
   U1U1_CUDA_TRY(cudaMemcpy(s->d_steps, steps.data(), sizeof(int) * nb, cudaMemcpyHostToDevice), "schedule");
   U1U1_CUDA_TRY(cudaMemcpy(s->d_box_prefix, prefix.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice),
@@ -385,8 +385,8 @@ int make_det_plan(u1u1_ensemble* e, const std::vector<int>& steps, int de, DetPl
     for (long long v : per) L.total += v;
     P->segments.push_back(L);
   }
-  U1U1_CUDA_TRY(cudaMalloc((void**)&P->d_int, sizeof(int) * std::max<size_t>(ints.size(), 1)), "detection plan");
-  U1U1_CUDA_TRY(cudaMalloc((void**)&P->d_ll, sizeof(long long) * std::max<size_t>(lls.size(), 1)), "detection plan");
+  U1U1_CUDA_TRY(dev_alloc(&P->d_int, sizeof(int) * std::max<size_t>(ints.size(), 1)), "detection plan");
+  U1U1_CUDA_TRY(dev_alloc(&P->d_ll, sizeof(long long) * std::max<size_t>(lls.size(), 1)), "detection plan");
   U1U1_CUDA_TRY(cudaMemcpy(P->d_int, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice), "plan copy");
   U1U1_CUDA_TRY(cudaMemcpy(P->d_ll, lls.data(), sizeof(long long) * lls.size(), cudaMemcpyHostToDevice), "plan copy");
   *out = P.get();
@@ -501,14 +501,14 @@ extern "C" void u1u1_ensemble_destroy(u1u1_ensemble* e) {
   e->schedules.clear();
   e->det_plans.clear();
   for (u1u1_lattice* h : e->boxes) u1u1_destroy(h);
-  cudaFree(e->d_boxes);
-  cudaFree(e->d_tma);
-  cudaFree(e->d_dyn);
-  cudaFree(e->d_coef);
-  cudaFree(e->d_ticket);
-  cudaFree(e->d_done);
-  cudaFree(e->d_err);
-  cudaFree(e->d_det);
+  dev_free(e->d_boxes);
+  dev_free(e->d_tma);
+  dev_free(e->d_dyn);
+  dev_free(e->d_coef);
+  dev_free(e->d_ticket);
+  dev_free(e->d_done);
+  dev_free(e->d_err);
+  dev_free(e->d_det);
   if (e->capture_stream) cudaStreamDestroy(e->capture_stream);
   delete e;
 }
@@ -542,14 +542,14 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
   }
   int rc = U1U1_OK;
   cudaError_t err = cudaSuccess;
-  if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_err, 2 * sizeof(int));
+  if (err == cudaSuccess) err = dev_alloc(&e->d_err, 2 * sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(e->d_err, 0, 2 * sizeof(int));
   if (err != cudaSuccess) rc = cuda_fail(err, "ensemble allocation");
   if (!rc) rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
   if (!rc) {
-    if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_dyn, sizeof(EnsDyn) * nboxes);
-    if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_ticket, sizeof(unsigned long long));
-    if (err == cudaSuccess) err = cudaMalloc((void**)&e->d_done, sizeof(unsigned) * nboxes);
+    if (err == cudaSuccess) err = dev_alloc(&e->d_dyn, sizeof(EnsDyn) * nboxes);
+    if (err == cudaSuccess) err = dev_alloc(&e->d_ticket, sizeof(unsigned long long));
+    if (err == cudaSuccess) err = dev_alloc(&e->d_done, sizeof(unsigned) * nboxes);
     if (err == cudaSuccess) err = cudaMemset(e->d_dyn, 0, sizeof(EnsDyn) * nboxes);
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->capture_stream, cudaStreamNonBlocking);
     if (err != cudaSuccess) rc = cuda_fail(err, "ensemble allocation");
@@ -732,16 +732,21 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
   // save every box's state (current positions and momenta) and step index
   const int nb = e->nboxes;
+  // (a box whose copy did not complete is left alone by the restore: nothing
+  // has run on it yet)
   std::vector<void*> saves(nb, nullptr);
+  std::vector<char> saved(nb, 0);
   std::vector<long long> n0(nb);
   std::vector<int> c0(nb);
+  for (int b = 0; b < nb; ++b) {
+    n0[b] = e->boxes[b]->n;
+    c0[b] = e->boxes[b]->cur;
+  }
   int rc = U1U1_OK;
   for (int b = 0; b < nb && !rc; ++b) {
     u1u1_lattice* h = e->boxes[b];
-    n0[b] = h->n;
-    c0[b] = h->cur;
     const size_t bytes = h->V * h->esize;
-    cudaError_t err = cudaMalloc(&saves[b], bytes * U1U1_NFIELDS);
+    cudaError_t err = dev_alloc(&saves[b], bytes * U1U1_NFIELDS);
     if (err != cudaSuccess) {
       cudaGetLastError();
       rc = fail(U1U1_ERR_OUT_OF_MEMORY, "autotune needs a copy of the ensemble state");
@@ -752,9 +757,11 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
       err = cudaMemcpy((char*)saves[b] + f * bytes, src, bytes, cudaMemcpyDeviceToDevice);
       if (err != cudaSuccess) rc = cuda_fail(err, "autotune save");
     }
+    saved[b] = rc ? 0 : 1;
   }
   auto restore = [&]() -> int {
     for (int b = 0; b < nb; ++b) {
+      if (!saved[b]) continue;
       u1u1_lattice* h = e->boxes[b];
       h->n = n0[b];
       h->cur = c0[b];
@@ -820,7 +827,7 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   const int rrc = restore();
-  for (void* s : saves) cudaFree(s);
+  for (void* s : saves) dev_free(s);
   if (!rc) rc = rrc;
   e->item_lz = rc ? lz0 : best_lz;
   e->persistent_tma = rc ? tma0 : best_tma;

@@ -24,6 +24,21 @@ int cuda_fail(cudaError_t e, const char* where);
     if (e_ != cudaSuccess) return ::u1u1::cuda_fail(e_, where); \
   } while (0)
 
+// The library's device and page-locked host allocations, counted, with an
+// injectable failure (alloc.cu).  Frees of NULL are no-ops.
+cudaError_t dev_alloc_bytes(void** p, size_t bytes);
+cudaError_t host_alloc_bytes(void** p, size_t bytes);
+void dev_free(void* p);
+void host_free(void* p);
+template <typename P>
+cudaError_t dev_alloc(P** p, size_t bytes) {
+  return dev_alloc_bytes((void**)p, bytes);
+}
+template <typename P>
+cudaError_t host_alloc(P** p, size_t bytes) {
+  return host_alloc_bytes((void**)p, bytes);
+}
+
 // A named range on the host timeline around an entry point's enqueue work,
 // for profilers that read NVTX (free when none is attached).
 struct NvtxRange {

@@ -23,7 +23,9 @@ paper's beta_growth to 1e-4.
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
+import os
 from dataclasses import dataclass
 
 from . import Params
@@ -67,11 +69,60 @@ def paper_schedule(base: Params, era: str = "radiation", physical: bool = True, 
     return phases
 
 
-def run(lat, phases, detect_every: int = 0, stream=None):
-    """Apply the phases to a Lattice (cooling, then leapfrog phases)."""
-    for ph in phases:
-        if ph.kind == "cool":
-            lat.cool(ph.dt, ph.nsteps, stream=stream)
-        else:
+RING_RECORDS = 1024  # capacity of a handle's detection-record ring (u1u1_read_records)
+
+
+def _json_value(v):
+    if isinstance(v, float) and not math.isfinite(v):
+        return None
+    return v
+
+
+def record_line(phase: int, strings: dict, diag: dict) -> str:
+    """One detection record as a JSON line: the phase index, the string
+    estimators and the diagnostics (Sec. III.A, Eqs. 31-37); NaN and
+    infinities (e.g. xi_W with no strings) are written as null."""
+    rec = {"phase": phase,
+           "strings": {k: _json_value(v) for k, v in strings.items()},
+           "diag": {k: _json_value(v) for k, v in diag.items()}}
+    return json.dumps(rec, allow_nan=False)
+
+
+def run(lat, phases, detect_every: int = 0, log=None, stream=None) -> int:
+    """Apply the phases to a Lattice (cooling, then leapfrog phases).
+
+    With detect_every > 0 every leapfrog phase is stepped in chunks of at
+    most RING_RECORDS detection periods, and each chunk's records are read
+    before the next chunk starts, so no record is overwritten in the
+    handle's ring however long the phase; with a log (a path, appended to,
+    or a text file) every record goes to it as one JSON line
+    (record_line).  Returns the number of records read."""
+    if detect_every < 0:
+        raise ValueError("detect_every must be >= 0")
+    out = open(log, "a") if isinstance(log, (str, os.PathLike)) else log
+    nrec = 0
+    try:
+        for i, ph in enumerate(phases):
+            if ph.kind == "cool":
+                lat.cool(ph.dt, ph.nsteps, stream=stream)
+                continue
             lat.set_params(ph.params, 0)
-            lat.step(ph.nsteps, detect_every=detect_every, stream=stream)
+            if detect_every == 0:
+                lat.step(ph.nsteps, stream=stream)
+                continue
+            left = ph.nsteps
+            while left > 0:
+                chunk = min(left, RING_RECORDS * detect_every)
+                lat.step(chunk, detect_every=detect_every, stream=stream)
+                left -= chunk
+                recs, lost = lat.read_records(max_records=RING_RECORDS, stream=stream)
+                if lost:
+                    raise RuntimeError(f"{lost} detection records were overwritten before they were read")
+                nrec += len(recs)
+                if out is not None:
+                    for strings, diag in recs:
+                        out.write(record_line(i, strings, diag) + "\n")
+    finally:
+        if out is not None and out is not log:
+            out.close()
+    return nrec

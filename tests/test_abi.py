@@ -108,3 +108,20 @@ def test_ensemble_and_probe_entry_points_reject_bad_arguments_without_gpu():
     assert L.u1u1_fp64_fma_rate(None, None) == -1
     assert L.u1u1_inject_copy_timeout(1, 10) == -1  # limit below 1000 ns
     L.u1u1_ensemble_destroy(None)
+
+
+def test_allocation_hook_and_accounting_without_gpu():
+    """The allocation-failure hook and the live-allocation count are host
+    state: without a GPU no handle can exist, so nothing is held, and a
+    negative nth is rejected."""
+    import torch
+    count, nbytes = U.live_allocations()
+    assert count >= 0 and nbytes >= 0
+    if not torch.cuda.is_available():
+        assert (count, nbytes) == (0, 0)
+    U.inject_alloc_failure(3)
+    U.inject_alloc_failure(0)
+    with pytest.raises(U.U1U1Error) as ei:
+        U.inject_alloc_failure(-1)
+    assert ei.value.code == -1
+    assert U.lib().u1u1_live_allocations(None, None) == -1

@@ -83,3 +83,87 @@ def test_schedule_gpu_matches_oracle(era, physical, unequal):
     err = np.abs(got - ref).reshape(20, -1).max(axis=1) / scale
     assert err.max() < 1e-10, err
     assert torch.cuda.is_available()
+
+
+class RingLattice:
+    """Host stand-in with a lattice handle's record semantics: a step whose
+    input index n has n % detect_every == 0 appends a record, and the ring
+    keeps the last 1024, counting the ones overwritten before being read."""
+
+    def __init__(self):
+        self.n = 0
+        self.ring = []
+        self.lost = 0
+        self.calls = []
+
+    def cool(self, dt, nsteps, stream=None):
+        self.calls.append(("cool", nsteps))
+
+    def set_params(self, params, n, stream=None):
+        self.n = n
+
+    def step(self, nsteps, detect_every=0, stream=None):
+        self.calls.append(("step", nsteps))
+        for _ in range(nsteps):
+            if detect_every and self.n % detect_every == 0:
+                self.ring.append(({"n": self.n, "xi_w": math.inf}, {"n": self.n, "lag": math.nan}))
+                if len(self.ring) > 1024:
+                    self.ring.pop(0)
+                    self.lost += 1
+            self.n += 1
+
+    def read_records(self, max_records=1024, stream=None):
+        recs, self.ring = self.ring[:max_records], self.ring[max_records:]
+        lost, self.lost = self.lost, 0
+        return recs, lost
+
+
+def test_run_reads_every_record_of_long_phases(tmp_path):
+    """A phase with more detections than the record ring holds is stepped in
+    ring-sized chunks: every record reaches the JSON-lines log, in order,
+    with non-finite values as null."""
+    base = U.Params.cube(8, deta=0.1)
+    phases = [S.Phase("cool", 5, dt=0.1), S.Phase("leapfrog", 2500, params=base),
+              S.Phase("leapfrog", 7, params=base)]
+    lat = RingLattice()
+    log = tmp_path / "records.jsonl"
+    assert S.run(lat, phases, detect_every=2, log=str(log)) == 1250 + 4
+    assert lat.calls == [("cool", 5), ("step", 2048), ("step", 452), ("step", 7)]
+    lines = [json.loads(s) for s in log.read_text().splitlines()]
+    assert [r["phase"] for r in lines] == [1] * 1250 + [2] * 4
+    assert [r["strings"]["n"] for r in lines] == list(range(0, 2500, 2)) + [0, 2, 4, 6]
+    assert all(r["strings"]["xi_w"] is None and r["diag"]["lag"] is None for r in lines)
+    # without detection a phase is one call and nothing is read
+    lat = RingLattice()
+    assert S.run(lat, phases) == 0 and lat.calls == [("cool", 5), ("step", 2500), ("step", 7)]
+
+
+def test_run_reports_records_lost_before_it_started():
+    lat = RingLattice()
+    lat.step(1100, detect_every=1)  # 76 records overwritten before the run
+    with pytest.raises(RuntimeError, match="overwritten"):
+        S.run(lat, [S.Phase("leapfrog", 4, params=U.Params.cube(8))], detect_every=1)
+
+
+@pytest.mark.gpu
+def test_schedule_log_keeps_every_record_on_gpu(tmp_path):
+    """A leapfrog phase with more detections (1100) than the record ring
+    holds, on a lattice handle: the runner steps it in ring-sized chunks,
+    every record reaches the log in order, the last one is what a standalone
+    detection reports on the same state, and the state is that of a run
+    without detection."""
+    torch = pytest.importorskip("torch")
+    base = U.Params.cube(16, m=0.5, beta=1.0, eta0=1.0, eta_ref=111.0, seed=8)
+    lat = U.Lattice(base)
+    log = tmp_path / "records.jsonl"
+    assert S.run(lat, [S.Phase("leapfrog", 1100, params=base)], detect_every=1, log=str(log)) == 1100
+    lines = [json.loads(s) for s in log.read_text().splitlines()]
+    assert [r["strings"]["n"] for r in lines] == list(range(1100))
+    assert all(r["phase"] == 0 for r in lines)
+    ref = U.Lattice(base)
+    ref.step(1099)
+    s_ref = ref.detect_strings(tol=1)
+    for k in ("n_p", "n_q", "nonzero_p", "nonzero_q", "n_pq_plaq", "n_pq_cell", "n_flagged"):
+        assert lines[-1]["strings"][k] == s_ref[k], k
+    ref.step(1)
+    assert torch.equal(lat.state(), ref.state())
