@@ -95,32 +95,40 @@ def test_ensemble_creation_fails_cleanly_at_every_allocation():
 
 @pytest.mark.parametrize("mode", [U.ENS_PERSISTENT, U.ENS_PER_STEP])
 def test_ensemble_run_and_autotune_fail_cleanly(mode):
-    """A detecting run (schedule and detection plan allocated on first use)
-    and the autotuner (a copy of every box's state), failed at each of their
-    allocations, leave states, records and the allocation count of a run
-    that never failed."""
+    """A detecting run (its schedule and detection plan are allocated on
+    first use) and the autotuner (a copy of every box's state), failed at
+    each of their allocations: a failed plan leaves only the run's schedule
+    cached, a failed autotune nothing, and a run afterwards gives the states,
+    records and allocation count of a run that never failed."""
     steps, de = [12, 9, 5], 4
     ref = U.Ensemble(_ensemble_params())
     before = live()
     ref.run(steps, mode=mode, use_graph=True, detect_every=de)
     n_run = live()[0] - before[0]
-    assert n_run >= 6  # four schedule tables and the two plan arrays
     ref_states = [b.state().clone() for b in ref.boxes]
     ref_recs = [b.read_records()[0] for b in ref.boxes]
     ref_tuning = ref.tuning()
     ref.close()
+    probe = U.Ensemble(_ensemble_params())
+    before = live()
+    probe.run(steps, mode=mode, use_graph=True)  # without detection: the schedule alone
+    n_sched = live()[0] - before[0]
+    probe.close()
+    assert n_sched >= 4 and n_run > n_sched
 
-    e = U.Ensemble(_ensemble_params())
-    held = live()
     for k in range(1, n_run + 1):
+        e = U.Ensemble(_ensemble_params())
+        held = live()
         U.inject_alloc_failure(k)
         fails_with_oom(lambda: e.run(steps, mode=mode, use_graph=True, detect_every=de))
-        assert live()[0] <= held[0] + n_run, k
+        assert live()[0] == held[0] + (n_sched if k > n_sched else 0), k
+        if k < n_run:
+            e.close()
     # the autotuner's state copies: fail the first and the last box's
     for k in (1, 3):
         U.inject_alloc_failure(k)
         fails_with_oom(lambda: e.autotune(probe_steps=2))
-        assert live()[0] <= held[0] + n_run, k
+        assert live() == held, k
     assert all(b.n == 0 for b in e.boxes)
     assert e.tuning() == ref_tuning  # a failed autotune keeps the previous choice
     e.run(steps, mode=mode, use_graph=True, detect_every=de)
