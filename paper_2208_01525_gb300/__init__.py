@@ -248,9 +248,10 @@ class Lattice:
         import torch
         V = self.params.nsites
         cp = cq = w = None
-        if cells:
-            cp = torch.empty(V, dtype=torch.uint8, device=self.device)
-            cq = torch.empty(V, dtype=torch.uint8, device=self.device)
+        if cells:  # one buffer, the p and q arrays its two rows (256-byte aligned)
+            vpad = (V + 255) // 256 * 256
+            cbuf = torch.empty((2, vpad), dtype=torch.uint8, device=self.device)[:, :V]
+            cp, cq = cbuf[0], cbuf[1]
         if windings:
             w = torch.empty(6 * V, dtype=torch.int8, device=self.device)
         out = _abi.CStrings()
@@ -259,7 +260,7 @@ class Lattice:
                                         _stream_ptr(stream)))
         res = _abi.struct_to_dict(out)
         if cells:
-            res["cells"] = torch.stack([cp, cq]).view(2, *self.params.shape)
+            res["cells"] = cbuf.view(2, *self.params.shape)
         if windings:
             res["windings"] = w.view(2, 3, *self.params.shape)
         return res

@@ -483,6 +483,50 @@ def test_full_size_sampled_sites(n, prec):
     assert res["n_p"] == total(Wg[0])
 
 
+def test_beyond_two_to_the_31_sites():
+    """An FP32 box past 2^31 sites, 1024 x 1024 x 2056 (2.16e9 sites, 259 GB
+    of fields): half of 192 sampled sites lie in the top eight planes, where
+    site offsets exceed 2^31, and after 20 steps one more step there equals
+    the oracle's step of each site's 5^3 patch; the detection of the whole
+    box keeps its any-size properties (cells even, their sum twice the
+    winding total, the top planes included)."""
+    import gc
+    gc.collect()
+    torch.cuda.empty_cache()
+    if torch.cuda.mem_get_info()[0] < 272e9:
+        pytest.skip("needs ~270 GB of free device memory")
+    n, nz = 1024, 2056
+    p = radiation((n, n, nz), 2560, precision=U.FP32, seed=6)
+    assert p.nsites > 2 ** 31
+    lat = U.Lattice(p)
+    lat.set_kernel(U.KERNEL_TILED)  # default chunking: no room for the tuner's copy of the momenta
+    lat.step(20)
+    top = synth.site_sample((8, n, n), 96, seed=1) + np.array([nz - 8, 0, 0])
+    sites = np.concatenate([top, synth.site_sample(p.shape, 96, seed=2)])
+    assert ((sites[:, 0] * n + sites[:, 1]) * n + sites[:, 2] >= 2 ** 31).sum() == 96
+    pt = patches(lat.fields(), p.shape, sites, radius=2)
+    lat.step(1)
+    got = gather_sites(lat.fields(), p.shape, sites)
+    op = to_oracle(p)
+    op.nx = op.ny = op.nz = 5
+    want = np.zeros_like(got)
+    for k in range(len(sites)):
+        st = np.ascontiguousarray(pt[k])
+        O.step(op, st, 20, 1)
+        want[k] = st[:, 2, 2, 2]
+    scale = np.abs(want).max(axis=0)
+    rel = np.abs(got - want).max(axis=0) / np.where(scale > 0, scale, 1.0)
+    assert rel.max() <= 1e-6, rel
+    res = lat.detect_strings(tol=1, cells=True)
+    cells = res["cells"]
+    slabs = [(z, min(z + 64, nz)) for z in range(0, nz, 64)]  # no whole-box temporaries
+    assert not any((cells[:, a:b] & 1).any().item() for a, b in slabs)
+    for sec, key in ((0, "n_p"), (1, "n_q")):
+        tot = sum(int(cells[sec, a:b].sum(dtype=torch.int64).item()) for a, b in slabs)
+        assert tot == 2 * res[key] and res[key] > 0, (sec, tot, res[key])
+    assert cells[:, nz - 8:].any().item()
+
+
 def test_wave_targets_agree_bit_exact():
     """Every z-chunking the autotuner may choose gives the same fields bit for
     bit, since each site's update does not depend on where its z-chunk
