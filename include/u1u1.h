@@ -395,6 +395,23 @@ int u1u1_inject_copy_timeout(int enable, int64_t limit_ns);
 int u1u1_inject_alloc_failure(int nth);
 int u1u1_live_allocations(int64_t* count, int64_t* bytes);
 
+/* Debugging aid in place of a device memory checker.  With guard_bytes > 0
+ * (a multiple of 256, at most 2^30) every library allocation made from then
+ * on is handed out with guard_bytes of a fixed byte pattern (0xA5) on each
+ * side, so that the blocks keep their 256-byte alignment; 0 turns guards off
+ * for later allocations (earlier ones keep theirs).  Filling the guards
+ * synchronises the device.  u1u1_check_alloc_guards synchronises the device
+ * and sets *corrupted to the number of live allocations with a changed
+ * guard byte, i.e. one that a kernel or a copy wrote past either end of.
+ * Process-wide.  Errors: INVALID_ARG, CUDA. */
+int u1u1_set_alloc_guard(int64_t guard_bytes);
+int u1u1_check_alloc_guards(int64_t* corrupted);
+/* Test hook for the check above: sets the first byte of the tail guard of one
+ * live guarded allocation to 0 (memory the library owns, so nothing is
+ * accessed out of bounds), so that the next check reports one corrupted
+ * allocation.  Errors: STATE (no guarded allocation is live), CUDA. */
+int u1u1_inject_guard_damage(void);
+
 /* ---- ensembles of independent boxes ---------------------------------------- */
 
 /* How u1u1_ensemble_run schedules the boxes' steps. */

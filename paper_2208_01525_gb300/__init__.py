@@ -104,6 +104,19 @@ def live_allocations() -> tuple:
     return c.value, b.value
 
 
+def set_alloc_guard(nbytes: int) -> None:
+    """Guard zones of nbytes (a multiple of 256) around every library
+    allocation made from now on (0: none)."""
+    check(lib().u1u1_set_alloc_guard(int(nbytes)))
+
+
+def check_alloc_guards() -> int:
+    """Number of live library allocations whose guard zones were written."""
+    v = ctypes.c_int64()
+    check(lib().u1u1_check_alloc_guards(ctypes.byref(v)))
+    return v.value
+
+
 def check_params(p: Params) -> None:
     check(lib().u1u1_check_params(ctypes.byref(p.c())))
 
@@ -123,7 +136,10 @@ class Lattice:
     """
 
     def __init__(self, params: Params, device="cuda", init: bool = True, stream=None,
-                 kernel: int = KERNEL_AUTO, _borrow=None):
+                 kernel: int = KERNEL_AUTO, guard: int = 0, _borrow=None):
+        """guard > 0 (bytes, a multiple of 256): every field array, and every
+        cell, winding and label array a call returns, sits between guard
+        zones of a fixed pattern, a debugging aid that check_guards reads."""
         import torch
         check_params(params)
         if not torch.cuda.is_available():
@@ -132,12 +148,15 @@ class Lattice:
         self.device = torch.device(device)
         self.dtype = torch.float64 if params.precision == FP64 else torch.float32
         self._owner = None
+        self._guard = guard
+        self._guarded = []     # (full tensor, guard elements) of the guarded field arrays
+        self._guard_hits = 0   # output arrays found with a changed guard zone
         if _borrow is not None:  # a box of an Ensemble: tensors and handle belong to it
             self.pos, self.mom, handle, self._owner = _borrow
             self._bufs = None
             self._h = handle
             return
-        self.pos, self.mom, self._bufs = _alloc_fields(params, self.dtype, self.device)
+        self.pos, self.mom, self._bufs = _alloc_fields(params, self.dtype, self.device, guard, self._guarded)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             if init:
@@ -180,6 +199,12 @@ class Lattice:
     @property
     def n(self) -> int:
         return self.current()[0]
+
+    def check_guards(self) -> int:
+        """Number of guarded arrays of this lattice (fields, and the outputs of
+        past calls) whose guard zones were written: 0 unless something wrote
+        past the end of an array."""
+        return _guards_damaged(self._guarded) + self._guard_hits
 
     def fields(self):
         """The 20 current field tensors (positions of the current buffer, then momenta)."""
@@ -248,16 +273,19 @@ class Lattice:
         import torch
         V = self.params.nsites
         cp = cq = w = None
+        out_guarded = []
         if cells:  # one buffer, the p and q arrays its two rows (256-byte aligned)
             vpad = (V + 255) // 256 * 256
-            cbuf = torch.empty((2, vpad), dtype=torch.uint8, device=self.device)[:, :V]
+            cbuf = _guarded_empty(2 * vpad, torch.uint8, self.device, self._guard, out_guarded).view(2, vpad)[:, :V]
             cp, cq = cbuf[0], cbuf[1]
         if windings:
-            w = torch.empty(6 * V, dtype=torch.int8, device=self.device)
+            w = _guarded_empty(6 * V, torch.int8, self.device, self._guard, out_guarded)
         out = _abi.CStrings()
         ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
         check(lib().u1u1_detect_strings(self._h, int(tol), ptr(cp), ptr(cq), ptr(w), ctypes.byref(out),
                                         _stream_ptr(stream)))
+        if out_guarded:
+            self._guard_hits += _guards_damaged(out_guarded)
         res = _abi.struct_to_dict(out)
         if cells:
             res["cells"] = cbuf.view(2, *self.params.shape)
@@ -268,11 +296,14 @@ class Lattice:
     def pq_segments(self, tol: int = 1, min_cells: int = 41, labels: bool = False, stream=None) -> dict:
         """Robust-method bound-state segments (connected pq-cell components)."""
         import torch
-        lab = torch.empty(self.params.nsites, dtype=torch.int32, device=self.device) if labels else None
+        out_guarded = []
+        lab = _guarded_empty(self.params.nsites, torch.int32, self.device, self._guard, out_guarded) if labels else None
         out = _abi.CSegments()
         check(lib().u1u1_pq_segments(self._h, int(tol), int(min_cells),
                                      ctypes.c_void_p(lab.data_ptr()) if lab is not None else None,
                                      ctypes.byref(out), _stream_ptr(stream)))
+        if out_guarded:
+            self._guard_hits += _guards_damaged(out_guarded)
         res = _abi.struct_to_dict(out)
         if labels:
             res["labels"] = lab.view(*self.params.shape)
@@ -311,11 +342,59 @@ class Lattice:
         check(lib().u1u1_load(self._h, str(path).encode(), _stream_ptr(stream)))
 
 
-def _alloc_fields(params: Params, dtype, device):
+def _guard_zones(full, g):
+    """The two guard zones of a guarded tensor (g elements each side) as
+    integer views, and the pattern they hold: a NaN for floating-point
+    arrays (a read past the array brings a NaN into the result), 0xA5 bytes
+    otherwise."""
     import torch
+    n = full.numel() - 2 * g
+    if full.dtype == torch.float32:
+        iv, pat, r = full.view(torch.int32), 0x7FA5A5A5, 1
+    elif full.dtype == torch.float64:
+        iv, pat, r = full.view(torch.int64), 0x7FF5A5A5A5A5A5A5, 1
+    else:
+        iv, pat, r = full.view(torch.uint8), 0xA5, full.element_size()
+    return (iv[: g * r], iv[(g + n) * r:]), pat
+
+
+def _guarded_empty(n: int, dtype, device, guard: int, guarded: list):
+    """A flat tensor of n elements.  With guard > 0 (bytes, a multiple of 256)
+    it is the middle of a larger tensor whose guard zones on both sides hold
+    a fixed pattern; (full, g) is appended to guarded for checking."""
+    import torch
+    if not guard:
+        return torch.empty(n, dtype=dtype, device=device)
+    es = torch.empty(0, dtype=dtype).element_size()
+    if guard % 256:
+        raise ValueError("guard must be a multiple of 256 bytes")
+    g = guard // es
+    full = torch.empty(n + 2 * g, dtype=dtype, device=device)
+    zones, pat = _guard_zones(full, g)
+    for z in zones:
+        z.fill_(pat)
+    guarded.append((full, g))
+    return full[g:g + n]
+
+
+def _guards_damaged(guarded: list) -> int:
+    """Number of guarded tensors with a changed guard zone (synchronises the
+    device first)."""
+    import torch
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+    bad = 0
+    for full, g in guarded:
+        zones, pat = _guard_zones(full, g)
+        bad += int(any(not bool((z == pat).all()) for z in zones))
+    return bad
+
+
+def _alloc_fields(params: Params, dtype, device, guard: int = 0, guarded: list = None):
     V = params.nsites
-    pos = [[torch.empty(V, dtype=dtype, device=device) for _ in range(NPOS)] for _ in range(2)]
-    mom = [torch.empty(V, dtype=dtype, device=device) for _ in range(NMOM)]
+    guarded = [] if guarded is None else guarded
+    pos = [[_guarded_empty(V, dtype, device, guard, guarded) for _ in range(NPOS)] for _ in range(2)]
+    mom = [_guarded_empty(V, dtype, device, guard, guarded) for _ in range(NMOM)]
     bufs = _abi.CBuffers()
     for k in range(2):
         for f in range(NPOS):
@@ -331,7 +410,8 @@ class Ensemble:
     ``boxes[b]`` is a Lattice view of box b (detection, diagnostics, state);
     its tensors and handle belong to the ensemble."""
 
-    def __init__(self, params_list, device="cuda", horizon: int = 0, stream=None):
+    def __init__(self, params_list, device="cuda", horizon: int = 0, stream=None, guard: int = 0):
+        """guard: as for Lattice, for every box's field arrays and outputs."""
         import torch
         if not torch.cuda.is_available():
             raise U1U1Error(-4, "no CUDA device: libu1u1 has no CPU path")
@@ -341,10 +421,11 @@ class Ensemble:
         cps = (_abi.CParams * nb)(*[p.c() for p in self.params])
         bufs = (_abi.CBuffers * nb)()
         fields = []
+        self._guarded = []
         for b, p in enumerate(self.params):
             check_params(p)
             dtype = torch.float64 if p.precision == FP64 else torch.float32
-            pos, mom, cb = _alloc_fields(p, dtype, self.device)
+            pos, mom, cb = _alloc_fields(p, dtype, self.device, guard, self._guarded)
             bufs[b] = cb
             fields.append((pos, mom))
         self._fields = fields
@@ -356,7 +437,7 @@ class Ensemble:
             hb = ctypes.c_void_p()
             check(lib().u1u1_ensemble_lattice(self._h, b, ctypes.byref(hb)))
             pos, mom = fields[b]
-            self.boxes.append(Lattice(p, device=device, _borrow=(pos, mom, hb, self)))
+            self.boxes.append(Lattice(p, device=device, guard=guard, _borrow=(pos, mom, hb, self)))
 
     def run(self, steps, mode: int = ENS_PERSISTENT, use_graph: bool = False, detect_every: int = 0, stream=None):
         """Advance box b by steps[b]; with detect_every > 0 the detection records
@@ -381,6 +462,11 @@ class Ensemble:
     def set_tuning(self, item_lz: int = 32, persistent_tma: bool = True, stream=None):
         """Work-item z-chunk and the persistent kernel's tensor copies, without timing."""
         check(lib().u1u1_ensemble_set_tuning(self._h, int(item_lz), int(bool(persistent_tma)), _stream_ptr(stream)))
+
+    def check_guards(self) -> int:
+        """Number of guarded arrays of every box (fields and past outputs)
+        whose guard zones were written."""
+        return _guards_damaged(self._guarded) + sum(b._guard_hits for b in self.boxes)
 
     def status(self, stream=None) -> int:
         v = ctypes.c_int()

@@ -128,6 +128,9 @@ PROTOTYPES = {
     "u1u1_inject_copy_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64]),
     "u1u1_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int]),
     "u1u1_live_allocations": (ctypes.c_int, [_P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "u1u1_set_alloc_guard": (ctypes.c_int, [ctypes.c_int64]),
+    "u1u1_check_alloc_guards": (ctypes.c_int, [_P(ctypes.c_int64)]),
+    "u1u1_inject_guard_damage": (ctypes.c_int, []),
     "u1u1_get_kernel": (ctypes.c_int, [_vp, _P(ctypes.c_int)]),
     "u1u1_autotune": (ctypes.c_int, [_vp, ctypes.c_char_p, _P(ctypes.c_int), _P(ctypes.c_int), _vp]),
     "u1u1_eval_link_phase": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp]),

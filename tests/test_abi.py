@@ -125,3 +125,35 @@ def test_allocation_hook_and_accounting_without_gpu():
         U.inject_alloc_failure(-1)
     assert ei.value.code == -1
     assert U.lib().u1u1_live_allocations(None, None) == -1
+
+
+def test_guard_zones_detect_writes_and_poison_reads():
+    """The guard zones of the debugging aid (host logic, on CPU tensors): a
+    write one element past either end of a guarded array is counted, and a
+    read past a floating-point array yields NaN."""
+    import torch
+    from paper_2208_01525_gb300 import _guarded_empty, _guards_damaged
+    for dtype in (torch.float32, torch.float64, torch.uint8, torch.int8, torch.int32):
+        guarded = []
+        t = _guarded_empty(1000, dtype, "cpu", 256, guarded)
+        full, g = guarded[0]
+        assert t.numel() == 1000 and t.data_ptr() - full.data_ptr() == 256
+        t.fill_(1)
+        assert _guards_damaged(guarded) == 0
+        if dtype.is_floating_point:
+            assert torch.isnan(full[g - 1]) and torch.isnan(full[g + 1000])
+        full[g + 1000] = 0  # one past the end
+        assert _guards_damaged(guarded) == 1
+        full[g + 1000] = t[0]
+        guarded2 = []
+        _guarded_empty(10, dtype, "cpu", 512, guarded2)[0] = 3
+        full2, g2 = guarded2[0]
+        full2[g2 - 1] = 0  # one before the start
+        assert _guards_damaged(guarded2) == 1
+    with pytest.raises(ValueError):
+        _guarded_empty(10, torch.float32, "cpu", 100, [])
+    assert U.lib().u1u1_set_alloc_guard(100) == -1
+    assert U.lib().u1u1_set_alloc_guard(-256) == -1
+    U.set_alloc_guard(256)
+    U.set_alloc_guard(0)
+    assert U.lib().u1u1_check_alloc_guards(None) == -1
