@@ -219,7 +219,9 @@ int u1u1_init_lattice(const u1u1_params* p, const u1u1_buffers* b, void* stream,
 int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, int64_t n, int current,
                         u1u1_lattice** out);
 
-/* Release the handle and its scratch (not the caller's buffers). */
+/* Release the handle and its scratch (not the caller's buffers).  A box
+ * handle of an ensemble (u1u1_ensemble_lattice) is left alone: it is
+ * released by u1u1_ensemble_destroy. */
 void u1u1_destroy(u1u1_lattice* h);
 
 /* Current step index and position buffer of the handle's state. */
@@ -258,7 +260,9 @@ int u1u1_cool(u1u1_lattice* h, double dt, int nsteps, void* stream);
  * step index to n, keeping the lattice, precision, seed, buffers and the
  * current state: this chains the phases of a run schedule (damping with
  * m_damp, core growth with beta < 0, physical evolution; Sec. V, Table 3).
- * Errors: INVALID_ARG (invalid parameters or a different lattice/precision). */
+ * Errors: INVALID_ARG (invalid parameters or a different lattice/precision),
+ * STATE (the handle is a box of an ensemble, whose device tables were built
+ * from the box's parameters at creation). */
 int u1u1_set_params(u1u1_lattice* h, const u1u1_params* p, int64_t n);
 
 /* Overlap tolerance (0: same cell, 1: one cell in any of the 26 directions)
@@ -332,8 +336,13 @@ int u1u1_host_span_mapped(const void* host, size_t bytes, int* mapped);
 
 /* Checkpoint / resume: write or read the parameters, step index and all 20
  * fields to or from a file; resuming continues bit for bit.  Synchronous.
- * u1u1_load requires a handle whose parameters match the file's lattice.
- * Errors: IO, INVALID_ARG, CUDA. */
+ * u1u1_load writes the fields into the handle's current position buffer and
+ * momenta and sets its step index.  It refuses, before writing anything, a
+ * file whose lattice, precision or physical parameters (all but the seed)
+ * differ from the handle's (INVALID_ARG, naming the first that differs),
+ * and a file that is not a checkpoint or whose length is not exactly that
+ * of the 20 fields (IO).
+ * Errors: IO, INVALID_ARG, OUT_OF_MEMORY (host buffer), CUDA. */
 int u1u1_save(const u1u1_lattice* h, const char* path, void* stream);
 int u1u1_load(u1u1_lattice* h, const char* path, void* stream);
 
@@ -456,7 +465,8 @@ int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, const u1u1_buff
 int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int detect_every, int mode, int use_graph, void* stream);
 
 /* Borrow the handle of box b (for detection, diagnostics, state transfer);
- * it stays owned by the ensemble and valid until u1u1_ensemble_destroy. */
+ * it stays owned by the ensemble and valid until u1u1_ensemble_destroy
+ * (u1u1_destroy leaves it alone; u1u1_set_params refuses it). */
 int u1u1_ensemble_lattice(u1u1_ensemble* e, int box, u1u1_lattice** h);
 
 /* Device status word of the last persistent run: U1U1_OK or

@@ -323,10 +323,15 @@ extern "C" int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, 
   return U1U1_OK;
 }
 
-extern "C" void u1u1_destroy(u1u1_lattice* h) {
+void u1u1::lattice_destroy(u1u1_lattice* h) {
   if (!h) return;
   lattice_free_scratch(h);
   free(h);
+}
+
+extern "C" void u1u1_destroy(u1u1_lattice* h) {
+  if (!h || h->ensemble_box) return;  // a box handle is released with its ensemble
+  lattice_destroy(h);
 }
 
 extern "C" int u1u1_current(const u1u1_lattice* h, int64_t* n, int* current) {
@@ -523,6 +528,8 @@ extern "C" int u1u1_cool(u1u1_lattice* h, double dt, int nsteps, void* stream) {
 
 extern "C" int u1u1_set_params(u1u1_lattice* h, const u1u1_params* p, int64_t n) {
   if (!h) return fail(U1U1_ERR_INVALID_ARG, "handle is NULL");
+  if (h->ensemble_box)
+    return fail(U1U1_ERR_STATE, "the handle is a box of an ensemble, whose coefficient tables hold its parameters");
   int rc = u1u1_check_params(p);
   if (rc) return rc;
   if (p->nx != h->p.nx || p->ny != h->p.ny || p->nz != h->p.nz || p->precision != h->p.precision)
@@ -941,7 +948,35 @@ extern "C" int u1u1_load(u1u1_lattice* h, const char* path, void* stream) {
     return fail(U1U1_ERR_INVALID_ARG, "checkpoint lattice %dx%dx%d/%d does not match the handle", p.nx, p.ny, p.nz,
                 p.precision);
   }
+  // a resumed run continues bit for bit only under the parameters it was
+  // saved with (a phase switched by u1u1_set_params included)
+  const struct {
+    const char* name;
+    double file, handle;
+  } phys[] = {{"dx", p.dx, h->p.dx},           {"deta", p.deta, h->p.deta},
+              {"eta0", p.eta0, h->p.eta0},     {"m", p.m, h->p.m},
+              {"eta_ref", p.eta_ref, h->p.eta_ref}, {"beta", p.beta, h->p.beta},
+              {"alpha", p.alpha, h->p.alpha},  {"lambda_p", p.lambda_p, h->p.lambda_p},
+              {"lambda_q", p.lambda_q, h->p.lambda_q}, {"e_p", p.e_p, h->p.e_p},
+              {"e_q", p.e_q, h->p.e_q},        {"sigma_p", p.sigma_p, h->p.sigma_p},
+              {"sigma_q", p.sigma_q, h->p.sigma_q}, {"kappa", p.kappa, h->p.kappa}};
+  for (const auto& q : phys)
+    if (q.file != q.handle) {
+      fclose(f);
+      return fail(U1U1_ERR_INVALID_ARG, "checkpoint %s = %.17g, the handle's %.17g", q.name, q.file, q.handle);
+    }
   size_t bytes = h->V * h->esize;
+  // the rest of the file must be exactly the 20 fields: a truncated or
+  // overlong file is refused before anything is written
+  const long start = ftell(f);
+  long end = -1;
+  if (start >= 0 && fseek(f, 0, SEEK_END) == 0) end = ftell(f);
+  if (end < 0 || fseek(f, start, SEEK_SET) != 0 ||
+      (unsigned long long)(end - start) != (unsigned long long)bytes * U1U1_NFIELDS) {
+    fclose(f);
+    return fail(U1U1_ERR_IO, "%s holds %lld bytes of fields, %llu expected", path, (long long)(end - start),
+                (unsigned long long)bytes * U1U1_NFIELDS);
+  }
   void* buf = malloc(bytes);
   if (!buf) {
     fclose(f);

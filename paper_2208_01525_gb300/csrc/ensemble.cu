@@ -500,7 +500,7 @@ extern "C" void u1u1_ensemble_destroy(u1u1_ensemble* e) {
   if (!e) return;
   e->schedules.clear();
   e->det_plans.clear();
-  for (u1u1_lattice* h : e->boxes) u1u1_destroy(h);
+  for (u1u1_lattice* h : e->boxes) lattice_destroy(h);
   dev_free(e->d_boxes);
   dev_free(e->d_tma);
   dev_free(e->d_dyn);
@@ -538,6 +538,7 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
       return rc;
     }
     h->kernel = U1U1_KERNEL_TILED;
+    h->ensemble_box = 1;
     e->boxes.push_back(h);
   }
   int rc = U1U1_OK;

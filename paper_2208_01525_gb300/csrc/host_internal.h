@@ -91,12 +91,15 @@ struct u1u1_lattice {
   RawRecord* host_rec;  // pinned, RING_CAP entries
   int64_t rec_written;
   int64_t rec_read;
+  int ensemble_box;  // nonzero: owned by an ensemble, whose tables hold its parameters
 };
 
 namespace u1u1 {
 // validate, allocate the handle and its scratch (no kernel launched)
 int lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_lattice** out);
 void lattice_free_scratch(u1u1_lattice* h);
+// release a handle and its scratch (the ensemble's path for its boxes)
+void lattice_destroy(u1u1_lattice* h);
 // enqueue the random-phase initial conditions into buffer 0 (and zero the rest)
 cudaError_t lattice_init_fields(u1u1_lattice* h, cudaStream_t st);
 }  // namespace u1u1

@@ -5,6 +5,8 @@ the same box advanced alone by the single-lattice tiled kernel, bit for bit,
 in all three scheduling modes and through CUDA graph replays; the persistent
 kernel's bounded dependency wait turns an unreachable wait into a reported
 timeout."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -148,6 +150,17 @@ def test_ensemble_errors():
     assert all(b.n == 0 for b in ens.boxes)
     with pytest.raises(U.U1U1Error):
         U.Ensemble([ps[0], U.Params(nx=8, ny=8, nz=8, precision=U.FP64)])
+    # box handles belong to the ensemble: their parameters live in its device
+    # tables, so a phase switch is refused, and destroying one does nothing
+    with pytest.raises(U.U1U1Error) as ei:
+        ens.boxes[0].set_params(ps[0], 0)
+    assert ei.value.code == -8
+    h = ctypes.c_void_p()
+    U.check(U.lib().u1u1_ensemble_lattice(ens._h, 1, ctypes.byref(h)))
+    U.lib().u1u1_destroy(h)
+    ens.run([2] * 6)
+    assert all(b.n == 2 for b in ens.boxes) and ens.status() == 0
+    ens.close()
 
 
 def test_ensemble_autotune_keeps_states():

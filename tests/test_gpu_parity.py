@@ -573,6 +573,35 @@ def test_checkpoint_resume_bit_exact(tmp_path):
     assert torch.equal(a.state(), b.state())
 
 
+def test_checkpoint_refusals_leave_the_state(tmp_path):
+    """A checkpoint saved under other couplings, a truncated one and an
+    overlong one are refused before anything is written: the handle keeps
+    its state and step index, and the right file still loads afterwards."""
+    import dataclasses
+    p = radiation(16, 50, precision=U.FP32, seed=13)
+    a = U.Lattice(p)
+    a.step(5)
+    path = tmp_path / "a.u1u1"
+    a.save(str(path))
+    data = path.read_bytes()
+    (tmp_path / "short.u1u1").write_bytes(data[:-1])
+    (tmp_path / "long.u1u1").write_bytes(data + b"\0")
+    other = U.Lattice(dataclasses.replace(p, kappa=0.8))
+    b = U.Lattice(p)
+    for lat in (other, b):
+        lat.step(3)
+    cases = [(other, path, -1, "kappa"), (b, tmp_path / "short.u1u1", -9, "expected"),
+             (b, tmp_path / "long.u1u1", -9, "expected")]
+    for lat, f, code, word in cases:
+        before = lat.state().clone()
+        with pytest.raises(U.U1U1Error) as ei:
+            lat.load(str(f))
+        assert ei.value.code == code and word in str(ei.value)
+        assert lat.n == 3 and torch.equal(lat.state(), before)
+    b.load(str(path))
+    assert b.n == 5 and torch.equal(b.state(), a.state())
+
+
 @pytest.mark.parametrize("shape,prec", [((16, 8, 8), U.FP64), ((16, 8, 8), U.FP32), ((12, 6, 5), U.FP32)])
 def test_upload_download_roundtrip(shape, prec):
     """State transfers: pinned, 16-byte aligned host tensors are copied by
