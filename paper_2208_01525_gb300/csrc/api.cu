@@ -853,9 +853,10 @@ bool mapped_host_span(const void* p, size_t bytes, void** dev) {
 int transfer_state(const u1u1_lattice* h, void* const dev[U1U1_NFIELDS], const void* const host[U1U1_NFIELDS],
                    bool upload, cudaStream_t st) {
   const size_t bytes = h->V * h->esize;
+  for (int f = 0; f < U1U1_NFIELDS; ++f)  // every pointer checked before any copy is enqueued
+    if (!host[f]) return fail(U1U1_ERR_INVALID_ARG, "host[%d] is NULL", f);
   XferTable t{};
   for (int f = 0; f < U1U1_NFIELDS; ++f) {
-    if (!host[f]) return fail(U1U1_ERR_INVALID_ARG, "host[%d] is NULL", f);
     void* hd = nullptr;
     if (mapped_host_span(host[f], bytes, &hd)) {
       t.src[t.m] = upload ? hd : dev[f];

@@ -650,6 +650,21 @@ def test_upload_download_roundtrip(shape, prec):
         assert all(torch.equal(out[f], st[f]) for f in range(20)), name
 
 
+def test_upload_with_a_null_host_array_changes_nothing():
+    """A NULL among the 20 host arrays is refused before any copy is
+    enqueued: no field of the state changes."""
+    import ctypes
+    p = U.Params(nx=16, ny=8, nz=8, seed=3)
+    lat = U.Lattice(p)
+    before = lat.state().clone()
+    host = [torch.full((p.nsites,), 7.0).pin_memory() for _ in range(20)]
+    arr = (ctypes.c_void_p * 20)(*[t.data_ptr() for t in host])
+    arr[7] = None
+    assert U.lib().u1u1_upload_state(lat._h, arr, None) == -1
+    torch.cuda.synchronize()
+    assert torch.equal(lat.state(), before)
+
+
 def test_vacuum_special_values():
     p = U.Params(nx=8, ny=8, nz=8, precision=U.FP64)
     lat = U.Lattice(p)
