@@ -217,22 +217,21 @@ class Lattice:
         return torch.stack(self.fields()).view(NFIELDS, *self.params.shape)
 
     def set_state(self, st, n: int = 0):
-        """Write a (20, nz, ny, nx) array (torch or numpy) into buffer 0 and reset
-        the step index to n (the handle is re-attached)."""
+        """Write a (20, nz, ny, nx) array (torch or numpy) into the current
+        position buffer and the momenta, and set the step index to n.  The
+        handle keeps its kernel choice, tuning, overlap tolerance and record
+        ring.  Not for ensemble boxes, whose step index the ensemble tracks."""
         if self._owner is not None:
-            raise U1U1Error(-8, "set_state re-attaches the handle; not available for ensemble boxes")
+            raise U1U1Error(-8, "set_state is not available for ensemble boxes")
         import torch
         t = torch.as_tensor(st).to(device=self.device, dtype=self.dtype).reshape(NFIELDS, -1)
+        cur = self.current()[1]
         for f in range(NPOS):
-            self.pos[0][f].copy_(t[f])
+            self.pos[cur][f].copy_(t[f])
         for f in range(NMOM):
             self.mom[f].copy_(t[NPOS + f])
         torch.cuda.synchronize(self.device)
-        kern = self.kernel()
-        self.close()
-        check(lib().u1u1_attach_lattice(ctypes.byref(self.params.c()), ctypes.byref(self._bufs), int(n), 0,
-                                        ctypes.byref(self._h)))
-        self.set_kernel(kern)
+        check(lib().u1u1_set_params(self._h, ctypes.byref(self.params.c()), int(n)))
 
     def set_kernel(self, kernel: int):
         check(lib().u1u1_set_kernel(self._h, int(kernel)))

@@ -678,6 +678,25 @@ def test_vacuum_special_values():
     assert torch.equal(lat.state().cpu(), torch.from_numpy(st))
 
 
+def test_set_state_keeps_the_handle():
+    """set_state writes the current position buffer (here buffer 1, after an
+    odd number of steps) and the momenta, sets the step index and keeps the
+    handle's kernel choice; stepping on equals a fresh lattice given the same
+    state."""
+    p = U.Params(nx=16, ny=8, nz=8, seed=2)
+    lat = U.Lattice(p, kernel=U.KERNEL_TILED)
+    lat.step(3)
+    st = synth.random_state(p.shape, seed=5)
+    lat.set_state(st, n=7)
+    assert lat.current() == (7, 1) and lat.kernel() == U.KERNEL_TILED
+    assert torch.equal(lat.state().cpu(), torch.as_tensor(st).float())
+    ref = U.Lattice(p, kernel=U.KERNEL_TILED)
+    ref.set_state(st, n=7)
+    lat.step(4)
+    ref.step(4)
+    assert torch.equal(lat.state(), ref.state())
+
+
 def test_edge_cases_and_errors():
     p = U.Params(nx=8, ny=8, nz=8, m=0.0)
     lat = U.Lattice(p)
