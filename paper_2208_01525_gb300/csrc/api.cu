@@ -254,7 +254,6 @@ int u1u1::lattice_create(const u1u1_params* p, const u1u1_buffers* b, u1u1_latti
   if (e == cudaSuccess) e = dev_alloc(&h->scratch_rec, sizeof(RawRecord));
   if (e == cudaSuccess) e = host_alloc(&h->host_rec, sizeof(RawRecord) * RING_CAP);
   if (e == cudaSuccess) e = dev_alloc(&h->tma_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->tma_status, 0, sizeof(int));
   if (e == cudaSuccess) e = host_alloc(&h->host_status, sizeof(int));
   if (e != cudaSuccess) {
     lattice_free_scratch(h);
@@ -301,7 +300,9 @@ extern "C" int u1u1_init_lattice(const u1u1_params* p, const u1u1_buffers* b, vo
   h->cur = 0;
   h->n = 0;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = lattice_init_fields(h, st);
+  // the handle's status word, cleared on the stream its launches will use
+  cudaError_t e = cudaMemsetAsync(h->tma_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = lattice_init_fields(h, st);
   if (e != cudaSuccess) {
     lattice_free_scratch(h);
     free(h);
@@ -319,6 +320,14 @@ extern "C" int u1u1_attach_lattice(const u1u1_params* p, const u1u1_buffers* b, 
   if (rc) return rc;
   h->cur = current;
   h->n = n;
+  // no stream is given: clear the status word and wait for it, so that
+  // launches on any stream see it cleared
+  cudaError_t e = cudaMemset(h->tma_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
+  if (e != cudaSuccess) {
+    lattice_destroy(h);
+    return cuda_fail(e, "status word");
+  }
   *out = h;
   return U1U1_OK;
 }
@@ -988,9 +997,14 @@ extern "C" int u1u1_load(u1u1_lattice* h, const char* path, void* stream) {
     void* dst = k < U1U1_NPOS ? h->pos[h->cur][k] : h->mom[k - U1U1_NPOS];
     if (fread(buf, 1, bytes, f) != bytes) rc = fail(U1U1_ERR_IO, "short read on %s", path);
     else {
-      cudaError_t e = cudaMemcpy(dst, buf, bytes, cudaMemcpyHostToDevice);
+      // staged from the pageable buffer before the call returns, ordered on st
+      cudaError_t e = cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) rc = cuda_fail(e, "checkpoint upload");
     }
+  }
+  if (rc == U1U1_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "stream synchronize");
   }
   free(buf);
   fclose(f);
@@ -1144,7 +1158,8 @@ extern "C" int u1u1_autotune(u1u1_lattice* h, const char* cache_path, int* kerne
       }
     }
     if (!rc && (e = copy_mom(false)) != cudaSuccess) rc = cuda_fail(e, "autotune restore");
-    if (!rc && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "autotune sync");
+    // the save buffer is read by copies on st: wait for them on every path
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess && !rc) rc = cuda_fail(e, "autotune sync");
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     dev_free(save);

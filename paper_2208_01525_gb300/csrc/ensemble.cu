@@ -142,12 +142,13 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
       hp[2 * b + k].status = e->d_err + 1;  // a copy timeout is this ensemble's, reported by its status
     }
   if (!e->d_tma) U1U1_CUDA_TRY(dev_alloc(&e->d_tma, sizeof(TmaPlan) * hp.size()), "ensemble tensor maps");
-  U1U1_CUDA_TRY(cudaMemcpy(e->d_tma, hp.data(), sizeof(TmaPlan) * hp.size(), cudaMemcpyHostToDevice),
+  U1U1_CUDA_TRY(cudaMemcpyAsync(e->d_tma, hp.data(), sizeof(TmaPlan) * hp.size(), cudaMemcpyHostToDevice, st),
                 "tensor map copy");
   for (int b = 0; b < nb; ++b)
     for (int k = 0; k < 2; ++k) hb[b].tma[k] = e->d_tma + 2 * b + k;
   if (!e->d_boxes) U1U1_CUDA_TRY(dev_alloc(&e->d_boxes, sizeof(EnsBox<T>) * nb), "ensemble box table");
-  U1U1_CUDA_TRY(cudaMemcpy(e->d_boxes, hb.data(), sizeof(EnsBox<T>) * nb, cudaMemcpyHostToDevice), "box table copy");
+  U1U1_CUDA_TRY(cudaMemcpyAsync(e->d_boxes, hb.data(), sizeof(EnsBox<T>) * nb, cudaMemcpyHostToDevice, st),
+                "box table copy");
   // detection resources: each box's own handle scratch, and the grids of a
   // single lattice's measuring and windings passes of its shape
   e->hdet.assign(nb, EnsDet{});
@@ -173,7 +174,7 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
       return fail(U1U1_ERR_STATE, "box %d: detection partials exceed the handle's buffer", b);
   }
   if (!e->d_det) U1U1_CUDA_TRY(dev_alloc(&e->d_det, sizeof(EnsDet) * nb), "detection table");
-  U1U1_CUDA_TRY(cudaMemcpy(e->d_det, e->hdet.data(), sizeof(EnsDet) * nb, cudaMemcpyHostToDevice),
+  U1U1_CUDA_TRY(cudaMemcpyAsync(e->d_det, e->hdet.data(), sizeof(EnsDet) * nb, cudaMemcpyHostToDevice, st),
                 "detection table copy");
   if (e->d_coef) return U1U1_OK;  // a re-tiling keeps the coefficient table
   // per-step coefficients of every box up to the horizon
@@ -181,13 +182,12 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
   for (int b = 0; b < nb; ++b)
     for (int n = 0; n < e->horizon; ++n) hc[(size_t)b * e->horizon + n] = make_coef<T>(&e->boxes[b]->p, n);
   U1U1_CUDA_TRY(dev_alloc(&e->d_coef, sizeof(Coef<T>) * hc.size()), "coefficient table");
-  U1U1_CUDA_TRY(cudaMemcpy(e->d_coef, hc.data(), sizeof(Coef<T>) * hc.size(), cudaMemcpyHostToDevice),
+  U1U1_CUDA_TRY(cudaMemcpyAsync(e->d_coef, hc.data(), sizeof(Coef<T>) * hc.size(), cudaMemcpyHostToDevice, st),
                 "coefficient copy");
-  (void)st;
   return U1U1_OK;
 }
 
-int make_schedule(u1u1_ensemble* e, const std::vector<int>& steps, Schedule** out) {
+int make_schedule(u1u1_ensemble* e, const std::vector<int>& steps, Schedule** out, cudaStream_t st) {
   auto it = e->schedules.find(steps);
   if (it != e->schedules.end()) {
     *out = it->second.get();
@@ -214,11 +214,12 @@ int make_schedule(u1u1_ensemble* e, const std::vector<int>& steps, Schedule** ou
   U1U1_CUDA_TRY(dev_alloc(&s->d_steps, sizeof(int) * std::max(nb, 1)), "schedule");
   U1U1_CUDA_TRY(dev_alloc(&s->d_box_prefix, sizeof(long long) * (nb + 1)), "schedule");
   U1U1_CUDA_TRY(dev_alloc(&s->d_step_off, sizeof(long long) * (smax + 1)), "schedule");
-  U1U1_CUDA_TRY(cudaMemcpy(s->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice), "schedule");
-  U1U1_CUDA_TRY(cudaMemcpy(s->d_steps, steps.data(), sizeof(int) * nb, cudaMemcpyHostToDevice), "schedule");
-  U1U1_CUDA_TRY(cudaMemcpy(s->d_box_prefix, prefix.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice),
+  U1U1_CUDA_TRY(cudaMemcpyAsync(s->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st), "schedule");
+  U1U1_CUDA_TRY(cudaMemcpyAsync(s->d_steps, steps.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st), "schedule");
+  U1U1_CUDA_TRY(cudaMemcpyAsync(s->d_box_prefix, prefix.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice,
+                                st),
                 "schedule");
-  U1U1_CUDA_TRY(cudaMemcpy(s->d_step_off, off.data(), sizeof(long long) * (smax + 1), cudaMemcpyHostToDevice),
+  U1U1_CUDA_TRY(cudaMemcpyAsync(s->d_step_off, off.data(), sizeof(long long) * (smax + 1), cudaMemcpyHostToDevice, st),
                 "schedule");
   s->sc.order = s->d_order;
   s->sc.steps = s->d_steps;
@@ -272,7 +273,7 @@ int enqueue(u1u1_ensemble* e, Schedule* s, int mode, int de, cudaStream_t st) {
 bool detects(long long n0, int k, int steps, int de) { return de > 0 && k < steps && (n0 + k) % de == 0; }
 
 // Plan of a run with detection every de steps (host tables, then one upload).
-int make_det_plan(u1u1_ensemble* e, const std::vector<int>& steps, int de, DetPlan** out) {
+int make_det_plan(u1u1_ensemble* e, const std::vector<int>& steps, int de, DetPlan** out, cudaStream_t st) {
   const int nb = e->nboxes;
   std::vector<int> key(steps);
   key.push_back(de);
@@ -387,8 +388,10 @@ int make_det_plan(u1u1_ensemble* e, const std::vector<int>& steps, int de, DetPl
   }
   U1U1_CUDA_TRY(dev_alloc(&P->d_int, sizeof(int) * std::max<size_t>(ints.size(), 1)), "detection plan");
   U1U1_CUDA_TRY(dev_alloc(&P->d_ll, sizeof(long long) * std::max<size_t>(lls.size(), 1)), "detection plan");
-  U1U1_CUDA_TRY(cudaMemcpy(P->d_int, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice), "plan copy");
-  U1U1_CUDA_TRY(cudaMemcpy(P->d_ll, lls.data(), sizeof(long long) * lls.size(), cudaMemcpyHostToDevice), "plan copy");
+  U1U1_CUDA_TRY(cudaMemcpyAsync(P->d_int, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st),
+                "plan copy");
+  U1U1_CUDA_TRY(cudaMemcpyAsync(P->d_ll, lls.data(), sizeof(long long) * lls.size(), cudaMemcpyHostToDevice, st),
+                "plan copy");
   *out = P.get();
   e->det_plans[key] = std::move(P);
   return U1U1_OK;
@@ -490,7 +493,8 @@ int sync_dyn(u1u1_ensemble* e, cudaStream_t st) {
     e->shadow_rec[b] = hd[b].rec;
   }
   U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
-  U1U1_CUDA_TRY(cudaMemcpy(e->d_dyn, hd.data(), sizeof(EnsDyn) * e->nboxes, cudaMemcpyHostToDevice), "step table");
+  U1U1_CUDA_TRY(cudaMemcpyAsync(e->d_dyn, hd.data(), sizeof(EnsDyn) * e->nboxes, cudaMemcpyHostToDevice, st),
+                "step table");
   return U1U1_OK;
 }
 
@@ -544,14 +548,14 @@ extern "C" int u1u1_ensemble_create(const u1u1_params* per_box, int nboxes, cons
   int rc = U1U1_OK;
   cudaError_t err = cudaSuccess;
   if (err == cudaSuccess) err = dev_alloc(&e->d_err, 2 * sizeof(int));
-  if (err == cudaSuccess) err = cudaMemset(e->d_err, 0, 2 * sizeof(int));
+  if (err == cudaSuccess) err = cudaMemsetAsync(e->d_err, 0, 2 * sizeof(int), st);
   if (err != cudaSuccess) rc = cuda_fail(err, "ensemble allocation");
   if (!rc) rc = e->precision == U1U1_FP64 ? build_tables<double>(e, st) : build_tables<float>(e, st);
   if (!rc) {
     if (err == cudaSuccess) err = dev_alloc(&e->d_dyn, sizeof(EnsDyn) * nboxes);
     if (err == cudaSuccess) err = dev_alloc(&e->d_ticket, sizeof(unsigned long long));
     if (err == cudaSuccess) err = dev_alloc(&e->d_done, sizeof(unsigned) * nboxes);
-    if (err == cudaSuccess) err = cudaMemset(e->d_dyn, 0, sizeof(EnsDyn) * nboxes);
+    if (err == cudaSuccess) err = cudaMemsetAsync(e->d_dyn, 0, sizeof(EnsDyn) * nboxes, st);
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->capture_stream, cudaStreamNonBlocking);
     if (err != cudaSuccess) rc = cuda_fail(err, "ensemble allocation");
   }
@@ -594,18 +598,19 @@ extern "C" int u1u1_ensemble_run(u1u1_ensemble* e, const int* steps, int detect_
       }
     if (changed) {
       U1U1_CUDA_TRY(cudaStreamSynchronize(st), "stream synchronize");
-      U1U1_CUDA_TRY(cudaMemcpy(e->d_det, e->hdet.data(), sizeof(EnsDet) * e->nboxes, cudaMemcpyHostToDevice),
+      U1U1_CUDA_TRY(cudaMemcpyAsync(e->d_det, e->hdet.data(), sizeof(EnsDet) * e->nboxes, cudaMemcpyHostToDevice,
+                                    st),
                     "detection table copy");
     }
   }
   int rc = sync_dyn(e, st);
   if (rc) return rc;
   Schedule* s = nullptr;
-  rc = make_schedule(e, sv, &s);
+  rc = make_schedule(e, sv, &s, st);
   if (rc) return rc;
   DetPlan* P = nullptr;
   if (de > 0 && mode != U1U1_ENS_UNBATCHED) {
-    rc = make_det_plan(e, sv, de, &P);
+    rc = make_det_plan(e, sv, de, &P, st);
     if (rc) return rc;
   }
   auto run_on = [&](cudaStream_t q) { return P ? enqueue_det(e, s, P, mode, de, q) : enqueue(e, s, mode, de, q); };
@@ -755,7 +760,7 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
     }
     for (int f = 0; f < U1U1_NFIELDS && !rc; ++f) {
       void* src = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
-      err = cudaMemcpy((char*)saves[b] + f * bytes, src, bytes, cudaMemcpyDeviceToDevice);
+      err = cudaMemcpyAsync((char*)saves[b] + f * bytes, src, bytes, cudaMemcpyDeviceToDevice, st);
       if (err != cudaSuccess) rc = cuda_fail(err, "autotune save");
     }
     saved[b] = rc ? 0 : 1;
@@ -769,7 +774,8 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
       const size_t bytes = h->V * h->esize;
       for (int f = 0; f < U1U1_NFIELDS; ++f) {
         void* dst = f < U1U1_NPOS ? h->pos[h->cur][f] : h->mom[f - U1U1_NPOS];
-        U1U1_CUDA_TRY(cudaMemcpy(dst, (char*)saves[b] + f * bytes, bytes, cudaMemcpyDeviceToDevice), "autotune restore");
+        U1U1_CUDA_TRY(cudaMemcpyAsync(dst, (char*)saves[b] + f * bytes, bytes, cudaMemcpyDeviceToDevice, st),
+                      "autotune restore");
       }
     }
     return U1U1_OK;
@@ -827,7 +833,9 @@ extern "C" int u1u1_ensemble_autotune(u1u1_ensemble* e, int probe_steps, int* mo
   }
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
-  const int rrc = restore();
+  int rrc = restore();
+  // the restore's copies read the saves on the stream: let them finish first
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rrc) rrc = cuda_fail(cudaGetLastError(), "stream synchronize");
   for (void* s : saves) dev_free(s);
   if (!rc) rc = rrc;
   e->item_lz = rc ? lz0 : best_lz;
