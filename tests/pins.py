@@ -682,10 +682,45 @@ def pin_segments_planted():
     assert O.segments(p, st, tol=1, min_cells=nz)["n_segments"] == 0
 
 
+def pin_cooling_homogeneous_flow():
+    """Cooling flow (Eqs. 27-30, read with sigma^2 and without a kappa term):
+    for a spatially constant scalar of each sector and zero links, the
+    covariant Laplacian and the current vanish, so a forward-Euler step of
+    size dt is exactly phi -> phi (1 - dt (lambda_s / 2)(|phi|^2 - sigma_s^2))
+    in each sector on its own, whatever kappa and the other sector are.
+    Unequal couplings and kappa != 0 make a sector mix-up, a kappa term, a
+    wrong factor or sign, or sigma in place of sigma^2 change the result; the
+    links stay zero.  600 steps are checked against the same recurrence."""
+    p = O.Params(4, 4, 4, m=0.0, lam=(2.0, 1.3), e=(1.0, 0.7), sigma=(1.0, 0.6), kappa=0.45)
+    st = np.zeros((20,) + p.shape)
+    phi0 = (0.5 * np.exp(0.3j), 1.5 * np.exp(-1.1j))  # |phi| far from each sigma
+    for s, f in enumerate(phi0):
+        st[2 * s] = f.real
+        st[2 * s + 1] = f.imag
+    dt, steps = 0.05, 600
+    want = list(phi0)
+    for k in range(steps):
+        for s in range(2):
+            r = abs(want[s]) ** 2 - p.sigma[s] ** 2
+            want[s] = want[s] * (1.0 - dt * 0.5 * p.lam[s] * r)
+        if k == 0:
+            one = O.cool(p, st.copy(), dt, 1)
+            for s in range(2):
+                got = one[2 * s] + 1j * one[2 * s + 1]
+                assert np.abs(got - want[s]).max() <= 1e-15 * abs(want[s]), (s, got.flat[0], want[s])
+    out = O.cool(p, st, dt, steps)
+    for s in range(2):
+        got = out[2 * s] + 1j * out[2 * s + 1]
+        assert np.abs(got - want[s]).max() <= 1e-12 * abs(want[s]), (s, got.flat[0], want[s])
+    assert not out[4:10].any()
+    # the flow ends at the vacuum of each sector: |phi_s| -> sigma_s
+    assert abs(abs(want[0]) - p.sigma[0]) < 1e-3 and abs(abs(want[1]) - p.sigma[1]) < 1e-3
+
+
 ALL_PINS = [
     pin_gauss_conserved, pin_gauss_step_identity, pin_energy_second_order,
     pin_linear_dispersion, pin_homogeneous_modes, pin_gauge_covariance, pin_sector_swap,
     pin_kappa_decoupling, pin_winding_topology, pin_planted_vortices, pin_bruteforce_windings, pin_bruteforce_overlap,
     pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic, pin_components,
-    pin_segments_planted, pin_unequal_tensions, pin_higher_winding_census,
+    pin_segments_planted, pin_unequal_tensions, pin_higher_winding_census, pin_cooling_homogeneous_flow,
 ]

@@ -50,6 +50,8 @@ MUTATIONS = [
     ("components_one_sided", "          for (int dx = -1; dx <= 1; ++dx) {\n            long nb",
      "          for (int dx = 0; dx <= 1; ++dx) {\n            long nb"),
     ("pq_mask_anchor_ignored", "        if (anchor[site] > 0)\n", "        if (anchor[site] >= 0)\n"),
+    ("cool_keeps_kappa", "  q.kappa = 0.0;\n", "  q.kappa = p->kappa;\n"),
+    ("cool_step_sign", "st[f_phi(s, c) * V + site] += dt * work", "st[f_phi(s, c) * V + site] -= dt * work"),
 ]
 
 
