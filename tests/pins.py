@@ -446,6 +446,31 @@ def pin_planted_vortices():
         assert res["n_p"] == 4 * nz and res["n_q"] == 4 * nz
         assert res["L_pq"] == p.dx * want1
         assert res["L_p"] == p.dx * (4 * nz) - p.dx * want1
+        # the estimators of Eqs. 31-35 from the planted geometry: four strings
+        # of length nz dx per sector, bound (within one cell) or not
+        vol = nx * ny * nz * p.dx ** 3
+        bound = p.dx * want1
+        alone = 4 * nz * p.dx - bound  # per sector
+        total = 2 * alone + bound
+
+        def sep(length):
+            return math.inf if length == 0 else math.sqrt(vol / length)
+
+        for k, v in (("xi_p", sep(alone)), ("xi_q", sep(alone)), ("xi_pq", sep(bound)), ("xi_w", sep(total)),
+                     ("f_total", bound / total)):
+            assert math.isclose(res[k], v, rel_tol=1e-14) or res[k] == v, (shift, k, res[k], v)
+        assert math.isnan(res["f_p"]) if alone == 0 else math.isclose(res["f_p"], bound / alone, rel_tol=1e-14)
+    # p strings only (the q sector in its vacuum): the separations of the two
+    # sectors differ, so a p/q mix-up in the estimators shows
+    st = O.new_state(p)
+    st[0], st[1] = vm.real, vm.imag
+    st[2] = 1.0
+    res = O.strings(p, st, tol=1)
+    vol, lp = nx * ny * nz * p.dx ** 3, 4 * nz * p.dx
+    assert res["n_q"] == 0 and res["L_pq"] == 0.0 and res["L_p"] == lp
+    assert math.isclose(res["xi_p"], math.sqrt(vol / lp), rel_tol=1e-14) and res["xi_q"] == math.inf
+    assert res["xi_pq"] == math.inf and math.isclose(res["xi_w"], math.sqrt(vol / lp), rel_tol=1e-14)
+    assert res["f_total"] == 0.0 and res["f_p"] == 0.0
 
 
 def pin_bruteforce_windings():

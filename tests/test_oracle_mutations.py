@@ -69,3 +69,43 @@ def test_mutation_is_caught(name, old, new, tmp_path):
                 caught.append((pin.__name__, type(exc).__name__))
                 break
     assert caught, f"mutation {name} passed every pin"
+
+
+# Plausible mistakes in the oracle's host epilogue (oracle/__init__.py: the
+# estimators of Eqs. 31-37 formed from the lattice counts and sums).  Each
+# mutated copy of the module is executed on its own, and its functions stand
+# in for the oracle's while the pins run.
+PY_MUTATIONS = [
+    ("xi_w_from_p_only", "xi_w=_sqrt_ratio(vol, tot)", "xi_w=_sqrt_ratio(vol, L_p)"),
+    ("volume_dx_squared", "    vol = p.nsites * dx ** 3\n    L_pq", "    vol = p.nsites * dx ** 2\n    L_pq"),
+    ("f_total_over_p", "f_total=(L_pq / tot)", "f_total=(L_pq / L_p)"),
+    ("bound_length_not_removed", "L_p = dx * n_p - L_pq", "L_p = dx * n_p"),
+    ("xi_pair_swapped", "xi_p=_sqrt_ratio(vol, L_p), xi_q=_sqrt_ratio(vol, L_q)",
+     "xi_p=_sqrt_ratio(vol, L_q), xi_q=_sqrt_ratio(vol, L_p)"),
+    ("velocity_factor", "2.0 * R / (1.0 + R)", "R / (1.0 + R)"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_epilogue_mutation_is_caught(name, old, new, monkeypatch):
+    import sys
+    import types
+    path = O.__file__
+    src = open(path).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} must occur exactly once"
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = path
+    mod.__package__ = O.__package__
+    monkeypatch.setitem(sys.modules, "oracle_mutant", mod)  # dataclasses look their module up here
+    exec(compile(src.replace(old, new), path, "exec"), mod.__dict__)  # noqa: S102 - test of a planted mistake
+    mod._lib = O.lib()  # the same compiled oracle
+    for fn in ("strings", "diagnostics"):
+        monkeypatch.setattr(O, fn, getattr(mod, fn))
+    caught = []
+    for pin in pins.ALL_PINS:
+        try:
+            pin()
+        except Exception as exc:  # noqa: BLE001 - any failure counts as detection
+            caught.append((pin.__name__, type(exc).__name__))
+            break
+    assert caught, f"mutation {name} passed every pin"
