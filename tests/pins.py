@@ -572,25 +572,32 @@ def pin_string_tension():
 
 def pin_unequal_tensions():
     """Unequal tensions (the next step the paper names, Sec. VI): with
-    sigma_q = 0.8 and lambda_q = 2 e_q^2 the q strings are BPS with tension
-    2 pi sigma_q^2; after cooling, each sector's static energy per length
-    is 4 x 2 pi sigma_s^2 within the lattice and finite-box error, and its
-    Lagrangian separation xi_L,s = sqrt(-mu_s V / L_s), mu_s = 2 pi sigma_s^2,
-    equals the winding separation sqrt(V / L) of its four planted strings."""
+    sigma_p = 1.1, sigma_q = 0.8 and lambda_s = 2 e_s^2 the strings of both
+    sectors are BPS with tension 2 pi sigma_s^2; after cooling, each
+    sector's static energy per length is 4 x 2 pi sigma_s^2 within the
+    lattice and finite-box error, and its Lagrangian separation
+    xi_L,s = sqrt(-mu_s V / L_s), mu_s = 2 pi sigma_s^2, equals the winding
+    separation sqrt(V / L) of its four planted strings.  The whole network's
+    xi_L (mu = 2 pi sigma_p^2 over both sectors' Lagrangian, which for
+    static strings is minus their energy) is then
+    sqrt(V / L * sigma_p^2 / (sigma_p^2 + sigma_q^2))."""
     n, dx = 32, 0.5
-    p = O.Params(n, n, 2, dx=dx, m=0.0, kappa=0.0, lam=(2.0, 1.62), e=(1.0, 0.9), sigma=(1.0, 0.8))
+    p = O.Params(n, n, 2, dx=dx, m=0.0, kappa=0.0, lam=(2.0, 1.62), e=(1.0, 0.9), sigma=(1.1, 0.8))
     st = O.new_state(p)
-    f = synth.vortex_map(p.shape, sigma=1.0)
+    f = synth.vortex_map(p.shape, sigma=1.1)
     g = synth.vortex_map(p.shape, sigma=0.8)
     st[0], st[1], st[2], st[3] = f.real, f.imag, g.real, g.imag
-    O.cool(p, st, 0.16 * dx * dx, 900)
+    O.cool(p, st, 0.15 * dx * dx, 960)  # forward Euler stays stable for the stiffest mode
     d = O.diagnostics(p, st, 0)
     vol = p.nsites * dx ** 3
+    length = 4 * p.nz * dx
     for k, sec in enumerate("pq"):
         e_static = dx ** 3 * (d["grad_" + sec] + d["mag_" + sec] + d["pot_" + sec])
-        tension = e_static / (p.nz * dx) / 4.0
+        tension = e_static / length
         assert abs(tension / (TWO_PI * p.sigma[k] ** 2) - 1.0) < 0.02, (sec, tension)
-        assert abs(d["xi_l_" + sec] / math.sqrt(vol / (4 * p.nz * dx)) - 1.0) < 0.01, sec
+        assert abs(d["xi_l_" + sec] / math.sqrt(vol / length) - 1.0) < 0.01, sec
+    sp2, sq2 = p.sigma[0] ** 2, p.sigma[1] ** 2
+    assert abs(d["xi_l"] / math.sqrt(vol / length * sp2 / (sp2 + sq2)) - 1.0) < 0.01
 
 
 def pin_higher_winding_census():

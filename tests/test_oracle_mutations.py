@@ -83,6 +83,9 @@ PY_MUTATIONS = [
     ("xi_pair_swapped", "xi_p=_sqrt_ratio(vol, L_p), xi_q=_sqrt_ratio(vol, L_q)",
      "xi_p=_sqrt_ratio(vol, L_q), xi_q=_sqrt_ratio(vol, L_p)"),
     ("velocity_factor", "2.0 * R / (1.0 + R)", "R / (1.0 + R)"),
+    ("tension_sigma_not_squared", "mu = 2.0 * math.pi * p.sigma[0] ** 2", "mu = 2.0 * math.pi * p.sigma[0]"),
+    ("sector_tension_sigma_not_squared", "_sqrt_ratio(-2.0 * math.pi * p.sigma[k] ** 2 * vol, lag_s)",
+     "_sqrt_ratio(-2.0 * math.pi * p.sigma[k] * vol, lag_s)"),
 ]
 
 
