@@ -521,6 +521,13 @@ def pin_velocity_closed_form():
     assert abs(d["R_pq"] - R) < 1e-11 * R, (d["R_pq"], R)
     assert abs(d["v2_l"] - 2 * R / (1 + R)) < 1e-11
     assert abs(d["grad_p"] - p.nsites * r[0] ** 2 * khat2) < 1e-10 * p.nsites
+    # the potential of Eq. 4 at a = 1, the same at every site
+    rp, rq = r[0] ** 2 - p.sigma[0] ** 2, r[1] ** 2 - p.sigma[1] ** 2
+    vp, vq = p.lam[0] / 4 * rp * rp, p.lam[1] / 4 * rq * rq
+    for k, want in (("pot", vp + vq - p.kappa * rp * rq), ("pot_p", vp), ("pot_q", vq), ("vint", p.kappa * rp * rq)):
+        assert abs(d[k] - p.nsites * want) < 1e-12 * p.nsites * max(abs(want), 1e-3), (k, d[k], p.nsites * want)
+    for s, sec in enumerate("pq"):
+        assert abs(d["phi_min_" + sec] - r[s]) < 1e-14 and abs(d["phi_max_" + sec] - r[s]) < 1e-14
 
 
 def pin_vacuum():

@@ -51,6 +51,11 @@ MUTATIONS = [
      "          for (int dx = 0; dx <= 1; ++dx) {\n            long nb"),
     ("pq_mask_anchor_ignored", "        if (anchor[site] > 0)\n", "        if (anchor[site] >= 0)\n"),
     ("cool_keeps_kappa", "  q.kappa = 0.0;\n", "  q.kappa = p->kappa;\n"),
+    ("vint_sign", "double vint = p->kappa * rp * rq;", "double vint = -p->kappa * rp * rq;"),
+    ("potential_kappa_sign", "0.25 * p->lambda[1] * rq * rq - p->kappa * rp * rq;",
+     "0.25 * p->lambda[1] * rq * rq + p->kappa * rp * rq;"),
+    ("self_potential_wrong_sector", "nadd(&acc[D_POT_P], c * 0.25 * p->lambda[0] * rp * rp);",
+     "nadd(&acc[D_POT_P], c * 0.25 * p->lambda[1] * rp * rp);"),
     ("cool_step_sign", "st[f_phi(s, c) * V + site] += dt * work", "st[f_phi(s, c) * V + site] -= dt * work"),
 ]
 
