@@ -1058,8 +1058,8 @@ void tune_key(const u1u1_lattice* h, char* key, size_t n) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) snprintf(prop.name, sizeof(prop.name), "unknown");
-  char name[64];
-  snprintf(name, sizeof(name), "%s", prop.name);
+  char name[64];  // the device name, cut to 63 characters
+  snprintf(name, sizeof(name), "%.63s", prop.name);
   for (char* c = name; *c; ++c)
     if (*c == ' ') *c = '_';
   snprintf(key, n, "%s/%dx%dx%d/%s", name, h->p.nx, h->p.ny, h->p.nz, h->esize == 8 ? "fp64" : "fp32");
