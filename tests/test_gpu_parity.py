@@ -527,6 +527,28 @@ def test_beyond_two_to_the_31_sites():
     assert cells[:, nz - 8:].any().item()
 
 
+def test_band_order_covers_every_tile():
+    """The tiled plain step hands tiles out in bands of tile rows, each band
+    through all its z-chunks.  On 1024 x 136 x 8 (17 rows of 32 tiles: one
+    band of 14 rows and a shorter last band at three CTAs per SM, each
+    column cut into z-chunks of 32, 32 and 8 planes) two steps of the tiled
+    kernel agree with the one-thread-per-site kernel, which has no bands, to
+    rounding: a tile or chunk left out would keep its input values."""
+    p = U.Params(nx=1024, ny=136, nz=72, m=0.5, beta=1.0, eta0=1.0, eta_ref=2.0, seed=15, precision=U.FP32)
+    st = synth.random_state(p.shape, seed=16, a_amp=1.0, mom_amp=0.5)
+    out = []
+    for kernel in (U.KERNEL_TILED, U.KERNEL_SIMPLE):
+        lat = U.Lattice(p, kernel=kernel, init=False)
+        lat.set_state(st, n=0)
+        if kernel == U.KERNEL_TILED:
+            lat.set_tile_waves(256)
+        lat.step(2)
+        out.append(host_state(lat))
+        lat.close()
+    err = field_maxrel(out[0], out[1])
+    assert err.max() < 1e-5, err
+
+
 def test_wave_targets_agree_bit_exact():
     """Every z-chunking the autotuner may choose gives the same fields bit for
     bit, since each site's update does not depend on where its z-chunk
