@@ -335,11 +335,21 @@ def test_planted_vortices_detected():
         assert int(r0["cells"][0].sum().item()) == 2 * 4 * nz
 
 
+ERAS = {"radiation_beta1": {}, "matter_beta0": dict(m=2.0 / 3.0, beta=0.0),
+        "radiation_growth": dict(m=0.5, beta=-1.0, eta_ref=1.0)}
+
+
+@pytest.mark.parametrize("era", sorted(ERAS))
 @pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-10), (U.FP32, 2e-5)])
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_diagnostics_match_oracle(prec, tol, kernel, couplings):
-    p = radiation((32, 24, 16), 100, precision=prec, seed=6, **COUPLINGS[couplings])
+def test_diagnostics_match_oracle(prec, tol, kernel, couplings, era):
+    """Every diagnostic sum and estimator of Sec. III.A against the oracle on
+    the same state, in the radiation era with beta = 1, the matter era with
+    beta = 0 and the core-growth regime (beta = -1): the coupling factor
+    a^{2 beta}, the gauge-energy factor 1/(2 e^2 c) and the Gauss charge
+    factor of the previous step all enter the sums."""
+    p = radiation((32, 24, 16), 100, precision=prec, seed=6, **COUPLINGS[couplings], **ERAS[era])
     lat = U.Lattice(p, kernel=kernel)
     lat.step(25)
     d = lat.diagnostics()
