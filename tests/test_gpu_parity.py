@@ -392,12 +392,13 @@ def test_gauss_law_preserved(prec):
             assert d["gauss_max_" + sec] < bound, (lat.n, sec, d["gauss_max_" + sec])
 
 
+@pytest.mark.parametrize("era", sorted(ERAS))
 @pytest.mark.parametrize("couplings", sorted(COUPLINGS))
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_fused_detection_equals_standalone(kernel, couplings):
+def test_fused_detection_equals_standalone(kernel, couplings, era):
     """A step fused with detection records exactly what the standalone
-    detection and diagnostics report on the same input state."""
-    p = radiation(40, 400, precision=U.FP32, seed=10, **COUPLINGS[couplings])
+    detection and diagnostics report on the same input state, in each era."""
+    p = radiation(40, 400, precision=U.FP32, seed=10, **COUPLINGS[couplings], **ERAS[era])
     a = U.Lattice(p, kernel=kernel)
     b = U.Lattice(p, kernel=kernel)
     a.step(16)
