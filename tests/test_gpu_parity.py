@@ -115,6 +115,26 @@ def test_fp32_matches_oracle_20_steps(kernel, cfg, couplings):
     assert err.max() <= 1e-5, err
 
 
+@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-11), (U.FP32, 1e-5)])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_cooling_matches_oracle(prec, tol, kernel):
+    """The diffusive cooling flow (Eqs. 27-30): 30 forward-Euler steps from a
+    rough state, with unequal couplings and kappa != 0 (which the flow
+    leaves out), against the oracle's flow; the momenta are zero after."""
+    p = U.Params(nx=36, ny=20, nz=12, seed=5, precision=prec, **UNEQUAL)
+    lat = U.Lattice(p, kernel=kernel)
+    st0 = synth.random_state(p.shape, seed=29, a_amp=1.0, mom_amp=0.5)
+    lat.set_state(st0, n=0)
+    dt = 0.1 * p.dx ** 2
+    lat.cool(dt, 30)
+    ref = st0.copy()
+    O.cool(to_oracle(p), ref, dt, 30)
+    got = host_state(lat)
+    err = field_maxrel(got[:10], ref[:10])
+    assert err.max() <= tol, err
+    assert not got[10:].any()
+
+
 def _windings_compare(p, st_gpu_lat):
     res = st_gpu_lat.detect_strings(tol=1, cells=True, windings=True)
     snap = host_state(st_gpu_lat)
