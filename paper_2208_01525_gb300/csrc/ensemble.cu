@@ -111,9 +111,17 @@ struct u1u1_ensemble {
   std::vector<EnsDet> hdet;
   std::vector<long long> shadow_rec;
   std::map<std::vector<int>, std::unique_ptr<DetPlan>> det_plans;
+  // the boxes' step views (an EnsViews<T>, host memory) passed to the step
+  // kernels as a parameter; empty above ENS_VIEW_MAX boxes
+  std::vector<unsigned char> views;
 };
 
 namespace {
+
+template <typename T>
+const EnsViews<T>* host_views(const u1u1_ensemble* e) {
+  return e->views.empty() ? nullptr : reinterpret_cast<const EnsViews<T>*>(e->views.data());
+}
 
 template <typename T>
 int build_tables(u1u1_ensemble* e, cudaStream_t st) {
@@ -132,6 +140,23 @@ int build_tables(u1u1_ensemble* e, cudaStream_t st) {
     e->ntiles[b] = ens_tile_grid(B.nx, B.ny, B.nz, &B.gx, &B.gy, &B.lz, &B.gz, e->item_lz);
     B.ntiles = e->ntiles[b];
     B.coef0 = (long long)b * e->horizon;
+  }
+  e->views.clear();
+  if (nb <= ENS_VIEW_MAX) {
+    e->views.assign(sizeof(EnsViews<T>), 0);
+    EnsViews<T>* V = reinterpret_cast<EnsViews<T>*>(e->views.data());
+    for (int b = 0; b < nb; ++b)
+      for (int k = 0; k < 2; ++k) {
+        LatticeView<T>& v = V->v[b][k];
+        for (int f = 0; f < U1U1_NPOS; ++f) {
+          v.pin[f] = hb[b].pos[k][f];
+          v.pout[f] = hb[b].pos[k ^ 1][f];
+        }
+        for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = hb[b].mom[f];
+        v.nx = hb[b].nx;
+        v.ny = hb[b].ny;
+        v.nz = hb[b].nz;
+      }
   }
   // tensor maps of each box's two position buffers (FP32; disabled plans
   // otherwise), read by the kernels from device memory
@@ -245,11 +270,11 @@ int enqueue_run(u1u1_ensemble* e, Schedule* s, int mode, int de, cudaStream_t st
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->nboxes, st), "counter reset");
     U1U1_CUDA_TRY(cudaMemsetAsync(e->d_err, 0, sizeof(int), st), "status reset");
     err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, s->sc, nullptr, e->d_ticket, e->d_done, e->d_err,
-                                   e->wait_limit_ns, e->inject, e->persistent_tma, st);
+                                   e->wait_limit_ns, e->inject, e->persistent_tma, host_views<T>(e), st);
     if (err != cudaSuccess) return cuda_fail(err, "persistent ensemble kernel");
   } else if (mode == U1U1_ENS_PER_STEP) {
     for (int k = 0; k < s->sc.smax; ++k) {
-      err = launch_ens_step<T>(boxes, e->d_dyn, coef, s->sc, k, s->items_per_step[k], st);
+      err = launch_ens_step<T>(boxes, e->d_dyn, coef, s->sc, k, s->items_per_step[k], host_views<T>(e), st);
       if (err != cudaSuccess) return cuda_fail(err, "ensemble step kernel");
     }
   } else {
@@ -417,7 +442,7 @@ int enqueue_group(u1u1_ensemble* e, const DetPlan* P, const DetGroup& g, int de,
   const Coef<T>* coef = (const Coef<T>*)e->d_coef;
   const int* list = P->d_int + g.list;
   cudaError_t err = launch_ens_measure<T>(boxes, e->d_det, e->d_dyn, coef, list, P->d_ll + g.pm, g.nlist, g.m_items,
-                                          g.k, st);
+                                          g.k, host_views<T>(e), st);
   if (err != cudaSuccess) return cuda_fail(err, "ensemble measuring step");
   err = launch_ens_windings<T>(boxes, e->d_det, e->d_dyn, list, P->d_ll + g.pw, g.nlist, g.w_items, g.k, st);
   if (err != cudaSuccess) return cuda_fail(err, "ensemble windings");
@@ -442,7 +467,8 @@ int enqueue_det_run(u1u1_ensemble* e, Schedule* s, DetPlan* P, int mode, int de,
         U1U1_CUDA_TRY(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), st), "ticket reset");
         U1U1_CUDA_TRY(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->nboxes, st), "counter reset");
         err = launch_ens_persistent<T>(boxes, e->d_dyn, coef, view(P, L), P->d_int + L.kstart, e->d_ticket,
-                                       e->d_done, e->d_err, e->wait_limit_ns, e->inject, e->persistent_tma, st);
+                                       e->d_done, e->d_err, e->wait_limit_ns, e->inject, e->persistent_tma,
+                                       host_views<T>(e), st);
         if (err != cudaSuccess) return cuda_fail(err, "persistent ensemble kernel");
       }
       if (j < P->groups.size()) {
@@ -454,7 +480,7 @@ int enqueue_det_run(u1u1_ensemble* e, Schedule* s, DetPlan* P, int mode, int de,
     size_t gi = 0;
     for (const PlainLaunch& L : P->per_step) {
       if (L.items > 0) {
-        err = launch_ens_step<T>(boxes, e->d_dyn, coef, view(P, L), L.k, L.items, st);
+        err = launch_ens_step<T>(boxes, e->d_dyn, coef, view(P, L), L.k, L.items, host_views<T>(e), st);
         if (err != cudaSuccess) return cuda_fail(err, "ensemble step kernel");
       }
       if (gi < P->groups.size() && P->groups[gi].k == L.k) {

@@ -919,15 +919,10 @@ __device__ __forceinline__ int upper_index(const long long* a, int n, long long 
 // CTA of the same persistent launch wrote and fenced); a compile-time
 // choice, since the tensor-copy path costs registers even where it is not
 // taken
-template <typename T, bool COHERENT, bool USE_TMA>
-__device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T>& B, int cur, const Coef<T>& c,
-                                             long long t) {
-  constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
-  const int bx = (int)(t % B.gx);
-  const int by = (int)((t / B.gx) % B.gy);
-  const int bz = (int)(t / ((long long)B.gx * B.gy));
-  const int z0 = bz * B.lz;
-  const int z1 = min(z0 + B.lz, B.nz);
+// A box's step view (input buffer cur) built in the thread: the fallback for
+// ensembles too large for the parameter table of views
+template <typename T>
+__device__ __forceinline__ LatticeView<T> box_view(const EnsBox<T>& B, int cur) {
   LatticeView<T> v;
 #pragma unroll
   for (int f = 0; f < U1U1_NPOS; ++f) {
@@ -939,6 +934,18 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
   v.nx = B.nx;
   v.ny = B.ny;
   v.nz = B.nz;
+  return v;
+}
+
+template <typename T, bool COHERENT, bool USE_TMA>
+__device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T>& B, const LatticeView<T>& v, int cur,
+                                             const Coef<T>& c, long long t) {
+  constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
+  const int bx = (int)(t % B.gx);
+  const int by = (int)((t / B.gx) % B.gy);
+  const int bz = (int)(t / ((long long)B.gx * B.gy));
+  const int z0 = bz * B.lz;
+  const int z1 = min(z0 + B.lz, B.nz);
   MeasureOut mo{nullptr, nullptr, nullptr};
   tile_run<T, TX, TY, MODE_WRITE, COHERENT, false>(smem, v, c, mo, bx, by, z0, z1, 0, USE_TMA ? B.tma[cur] : nullptr);
 }
@@ -953,7 +960,7 @@ template <typename T, bool USE_TMA>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
                  EnsSched sc, const int* __restrict__ kstart, unsigned long long* ticket, unsigned* done, int* err,
-                 long long limit_ns, int inject) {
+                 long long limit_ns, int inject, const __grid_constant__ EnsViews<T> views, int use_views) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   __shared__ long long s_t;
@@ -999,7 +1006,11 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
     __syncthreads();
     if (!s_go) break;
     const EnsBox<T>& B = boxes[s_box];
-    ens_run_item<T, true, USE_TMA>(smem_raw, B, (dyn[s_box].cur + s_k) & 1, cs, s_t);
+    const int cur = (dyn[s_box].cur + s_k) & 1;
+    if (use_views)
+      ens_run_item<T, true, USE_TMA>(smem_raw, B, views.v[s_box][cur], cur, cs, s_t);
+    else
+      ens_run_item<T, true, USE_TMA>(smem_raw, B, box_view(B, cur), cur, cs, s_t);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -1012,7 +1023,7 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
-           EnsSched sc, int k) {
+           EnsSched sc, int k, const __grid_constant__ EnsViews<T> views, int use_views) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   const long long r = blockIdx.x;
@@ -1020,7 +1031,11 @@ k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, 
   const int box = sc.order[si];
   if (threadIdx.x == 0) cs = coef[boxes[box].coef0 + dyn[box].n + k];
   __syncthreads();
-  ens_run_item<T, false, true>(smem_raw, boxes[box], (dyn[box].cur + k) & 1, cs, r - sc.box_prefix[si]);
+  const int cur = (dyn[box].cur + k) & 1;
+  if (use_views)
+    ens_run_item<T, false, true>(smem_raw, boxes[box], views.v[box][cur], cur, cs, r - sc.box_prefix[si]);
+  else
+    ens_run_item<T, false, true>(smem_raw, boxes[box], box_view(boxes[box], cur), cur, cs, r - sc.box_prefix[si]);
 }
 
 // Measuring step k (a step fused with the diagnostic sums) of the boxes in
@@ -1032,7 +1047,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
 k_ens_measure(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ det, const EnsDyn* __restrict__ dyn,
               const Coef<T>* __restrict__ coef, const int* __restrict__ list, const long long* __restrict__ pre,
-              int nlist, int k) {
+              int nlist, int k, const __grid_constant__ EnsViews<T> views, int use_views) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   const long long r = blockIdx.x;
@@ -1050,20 +1065,16 @@ k_ens_measure(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ de
   const int cur = (dyn[b].cur + k) & 1;
   const int bx = (int)(t % D.mgx), by = (int)((t / D.mgx) % D.mgy), bz = (int)(t / ((long long)D.mgx * D.mgy));
   const int z0 = bz * D.mlz, z1 = min(z0 + D.mlz, B.nz);
-  LatticeView<T> v;
-#pragma unroll
-  for (int f = 0; f < U1U1_NPOS; ++f) {
-    v.pin[f] = B.pos[cur][f];
-    v.pout[f] = B.pos[cur ^ 1][f];
-  }
-#pragma unroll
-  for (int f = 0; f < U1U1_NMOM; ++f) v.mom[f] = B.mom[f];
-  v.nx = B.nx;
-  v.ny = B.ny;
-  v.nz = B.nz;
   MeasureOut mo{D.part, nullptr, nullptr};
-  tile_run<T, TileShape<T>::TX, TileShape<T>::TY, MODE_WRITE | MODE_MEASURE, false, false>(smem_raw, v, cs, mo, bx, by,
-                                                                                         z0, z1, (int)t, B.tma[cur]);
+  constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
+  if (use_views) {
+    tile_run<T, TX, TY, MODE_WRITE | MODE_MEASURE, false, false>(smem_raw, views.v[b][cur], cs, mo, bx, by, z0, z1,
+                                                                 (int)t, B.tma[cur]);
+  } else {
+    const LatticeView<T> v = box_view(B, cur);
+    tile_run<T, TX, TY, MODE_WRITE | MODE_MEASURE, false, false>(smem_raw, v, cs, mo, bx, by, z0, z1, (int)t,
+                                                                 B.tma[cur]);
+  }
 }
 
 // After a run: advance each box's step index, buffer parity and count of
@@ -1113,10 +1124,19 @@ int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, in
   return *gx * *gy * *gz;
 }
 
+// the view table a launch passes: the ensemble's, or an empty one (the
+// kernels then build each box's view in the thread)
+template <typename T>
+const EnsViews<T>& views_or_empty(const EnsViews<T>* views) {
+  static const EnsViews<T> empty{};
+  return views ? *views : empty;
+}
+
 template <typename T, bool USE_TMA>
 cudaError_t launch_ens_persistent_t(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef,
                                     const EnsSched& sc, const int* kstart, unsigned long long* ticket, unsigned* done,
-                                    int* err, long long limit_ns, int inject, cudaStream_t st) {
+                                    int* err, long long limit_ns, int inject, const EnsViews<T>* views,
+                                    cudaStream_t st) {
   static bool configured[64] = {};
   const size_t bytes = ens_smem_bytes<T>();
   cudaError_t e = set_smem_attr(k_ens_persistent<T, USE_TMA>, bytes, configured);
@@ -1131,42 +1151,45 @@ cudaError_t launch_ens_persistent_t(const EnsBox<T>* boxes, const EnsDyn* dyn, c
   if (grid > sc.total) grid = sc.total;
   if (grid < 1) return cudaSuccess;
   k_ens_persistent<T, USE_TMA><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done, err,
-                                                                   limit_ns, inject);
+                                                                   limit_ns, inject, views_or_empty(views),
+                                                                   views ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                                   const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
-                                  long long limit_ns, int inject, int use_tma, cudaStream_t st) {
+                                  long long limit_ns, int inject, int use_tma, const EnsViews<T>* views,
+                                  cudaStream_t st) {
   return use_tma ? launch_ens_persistent_t<T, true>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns, inject,
-                                                    st)
+                                                    views, st)
                  : launch_ens_persistent_t<T, false>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
-                                                     inject, st);
+                                                     inject, views, st);
 }
 
 template <typename T>
 cudaError_t launch_ens_measure(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const Coef<T>* coef,
                                const int* list, const long long* pre, int nlist, long long items, int k,
-                               cudaStream_t st) {
+                               const EnsViews<T>* views, cudaStream_t st) {
   const size_t bytes = sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, true, false>);
   static bool configured[64] = {};
   cudaError_t e = set_smem_attr(k_ens_measure<T>, bytes, configured);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
-  k_ens_measure<T><<<(unsigned)items, 256, bytes, st>>>(boxes, det, dyn, coef, list, pre, nlist, k);
+  k_ens_measure<T><<<(unsigned)items, 256, bytes, st>>>(boxes, det, dyn, coef, list, pre, nlist, k,
+                                                        views_or_empty(views), views ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
-                            int k, long long items, cudaStream_t st) {
+                            int k, long long items, const EnsViews<T>* views, cudaStream_t st) {
   const size_t bytes = ens_smem_bytes<T>();
   static bool configured[64] = {};
   cudaError_t e = set_smem_attr(k_ens_step<T>, bytes, configured);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
-  k_ens_step<T><<<(unsigned)items, 256, bytes, st>>>(boxes, dyn, coef, sc, k);
+  k_ens_step<T><<<(unsigned)items, 256, bytes, st>>>(boxes, dyn, coef, sc, k, views_or_empty(views), views ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1177,19 +1200,20 @@ cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de
 
 template cudaError_t launch_ens_persistent<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*,
                                                   const EnsSched&, const int*, unsigned long long*, unsigned*, int*,
-                                                  long long, int, int, cudaStream_t);
+                                                  long long, int, int, const EnsViews<float>*, cudaStream_t);
 template cudaError_t launch_ens_persistent<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,
                                                    const EnsSched&, const int*, unsigned long long*, unsigned*, int*,
-                                                   long long, int, int, cudaStream_t);
+                                                   long long, int, int, const EnsViews<double>*, cudaStream_t);
 template cudaError_t launch_ens_measure<float>(const EnsBox<float>*, const EnsDet*, const EnsDyn*, const Coef<float>*,
-                                               const int*, const long long*, int, long long, int, cudaStream_t);
+                                               const int*, const long long*, int, long long, int,
+                                               const EnsViews<float>*, cudaStream_t);
 template cudaError_t launch_ens_measure<double>(const EnsBox<double>*, const EnsDet*, const EnsDyn*,
                                                 const Coef<double>*, const int*, const long long*, int, long long, int,
-                                                cudaStream_t);
+                                                const EnsViews<double>*, cudaStream_t);
 template cudaError_t launch_ens_step<float>(const EnsBox<float>*, const EnsDyn*, const Coef<float>*, const EnsSched&,
-                                            int, long long, cudaStream_t);
+                                            int, long long, const EnsViews<float>*, cudaStream_t);
 template cudaError_t launch_ens_step<double>(const EnsBox<double>*, const EnsDyn*, const Coef<double>*,
-                                             const EnsSched&, int, long long, cudaStream_t);
+                                             const EnsSched&, int, long long, const EnsViews<double>*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_tiled(int mode, const LatticeView<T>& v, const Coef<T>& c, const MeasureOut& mo,

@@ -219,17 +219,34 @@ struct EnsSched {              // one run's work-item order
 };
 constexpr int ENS_LZ = 32;     // default z-chunk of an ensemble work item
 
+// Each box's two step views (input buffer 0 and 1) for ensembles of up to
+// ENS_VIEW_MAX boxes, passed to the ensemble step kernels as one kernel
+// parameter.  The tile body then reads a box's field pointers from the
+// parameter bank, as a single lattice's kernel does, instead of from a
+// per-thread copy, which the copy plan's run-time field index keeps in local
+// memory (measured: a 1024^3 box stepped 4% faster).  Larger ensembles use
+// the per-thread copy.  56 x 2 views of 256 bytes stay inside the 32 KB
+// kernel-parameter limit.
+constexpr int ENS_VIEW_MAX = 56;
+template <typename T>
+struct EnsViews {
+  LatticeView<T> v[ENS_VIEW_MAX][2];
+};
+
 int ens_tile_grid(int nx, int ny, int nz, int* gx, int* gy, int* lz, int* gz, int item_lz = ENS_LZ);
 // kstart (nullable): per box, the run step its first item of this launch
 // advances (a launch covering a segment of a run between detection steps);
 // use_tma: interior tiles' ring slots filled by tensor copies
+// views (host memory, nullable): the boxes' step views when the ensemble
+// has at most ENS_VIEW_MAX boxes
 template <typename T>
 cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                                   const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
-                                  long long limit_ns, int inject, int use_tma, cudaStream_t st);
+                                  long long limit_ns, int inject, int use_tma, const EnsViews<T>* views,
+                                  cudaStream_t st);
 template <typename T>
 cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
-                            int k, long long items, cudaStream_t st);
+                            int k, long long items, const EnsViews<T>* views, cudaStream_t st);
 // de: detection cadence of the run (0: none), for the record counters
 cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de, cudaStream_t st);
 
@@ -241,7 +258,7 @@ cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de
 template <typename T>
 cudaError_t launch_ens_measure(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const Coef<T>* coef,
                                const int* list, const long long* pre, int nlist, long long items, int k,
-                               cudaStream_t st);
+                               const EnsViews<T>* views, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ens_windings(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const int* list,
                                 const long long* pre, int nlist, long long items, int k, cudaStream_t st);
