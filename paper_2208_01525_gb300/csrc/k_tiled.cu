@@ -956,11 +956,16 @@ __device__ __forceinline__ void ens_run_item(unsigned char* smem, const EnsBox<T
 // bounded: past limit_ns the kernel records U1U1_ERR_TIMEOUT and all CTAs
 // return.  Deadlock freedom: tickets are taken only by running CTAs and an
 // item depends only on items with smaller tickets.
-template <typename T, bool USE_TMA>
+//
+// VIEWS (all three ensemble kernels): each box's step view is read from the
+// kernel-parameter table `views`; otherwise it is built in the thread from
+// the box record.  A compile-time choice, so that each instantiation holds
+// one copy of the tile body and the view path keeps no local view copy.
+template <typename T, bool USE_TMA, bool VIEWS>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
                  EnsSched sc, const int* __restrict__ kstart, unsigned long long* ticket, unsigned* done, int* err,
-                 long long limit_ns, int inject, const __grid_constant__ EnsViews<T> views, int use_views) {
+                 long long limit_ns, int inject, const __grid_constant__ EnsViews<T> views) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   __shared__ long long s_t;
@@ -1007,7 +1012,7 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
     if (!s_go) break;
     const EnsBox<T>& B = boxes[s_box];
     const int cur = (dyn[s_box].cur + s_k) & 1;
-    if (use_views)
+    if constexpr (VIEWS)
       ens_run_item<T, true, USE_TMA>(smem_raw, B, views.v[s_box][cur], cur, cs, s_t);
     else
       ens_run_item<T, true, USE_TMA>(smem_raw, B, box_view(B, cur), cur, cs, s_t);
@@ -1020,10 +1025,10 @@ k_ens_persistent(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__
 }
 
 // One step k of every box that still has steps: one CTA per work item.
-template <typename T>
+template <typename T, bool VIEWS>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 3)
 k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, const Coef<T>* __restrict__ coef,
-           EnsSched sc, int k, const __grid_constant__ EnsViews<T> views, int use_views) {
+           EnsSched sc, int k, const __grid_constant__ EnsViews<T> views) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   const long long r = blockIdx.x;
@@ -1032,7 +1037,7 @@ k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, 
   if (threadIdx.x == 0) cs = coef[boxes[box].coef0 + dyn[box].n + k];
   __syncthreads();
   const int cur = (dyn[box].cur + k) & 1;
-  if (use_views)
+  if constexpr (VIEWS)
     ens_run_item<T, false, true>(smem_raw, boxes[box], views.v[box][cur], cur, cs, r - sc.box_prefix[si]);
   else
     ens_run_item<T, false, true>(smem_raw, boxes[box], box_view(boxes[box], cur), cur, cs, r - sc.box_prefix[si]);
@@ -1043,11 +1048,11 @@ k_ens_step(const EnsBox<T>* __restrict__ boxes, const EnsDyn* __restrict__ dyn, 
 // partial slots of a single lattice's measuring launch.  The CTA of a box's
 // first tile also clears the box's overlap and census counters for the
 // passes that follow in stream order.
-template <typename T>
+template <typename T, bool VIEWS>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
 k_ens_measure(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ det, const EnsDyn* __restrict__ dyn,
               const Coef<T>* __restrict__ coef, const int* __restrict__ list, const long long* __restrict__ pre,
-              int nlist, int k, const __grid_constant__ EnsViews<T> views, int use_views) {
+              int nlist, int k, const __grid_constant__ EnsViews<T> views) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ Coef<T> cs;
   const long long r = blockIdx.x;
@@ -1067,7 +1072,7 @@ k_ens_measure(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ de
   const int z0 = bz * D.mlz, z1 = min(z0 + D.mlz, B.nz);
   MeasureOut mo{D.part, nullptr, nullptr};
   constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
-  if (use_views) {
+  if constexpr (VIEWS) {
     tile_run<T, TX, TY, MODE_WRITE | MODE_MEASURE, false, false>(smem_raw, views.v[b][cur], cs, mo, bx, by, z0, z1,
                                                                  (int)t, B.tma[cur]);
   } else {
@@ -1132,27 +1137,27 @@ const EnsViews<T>& views_or_empty(const EnsViews<T>* views) {
   return views ? *views : empty;
 }
 
-template <typename T, bool USE_TMA>
+template <typename T, bool USE_TMA, bool VIEWS>
 cudaError_t launch_ens_persistent_t(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef,
                                     const EnsSched& sc, const int* kstart, unsigned long long* ticket, unsigned* done,
                                     int* err, long long limit_ns, int inject, const EnsViews<T>* views,
                                     cudaStream_t st) {
   static bool configured[64] = {};
   const size_t bytes = ens_smem_bytes<T>();
-  cudaError_t e = set_smem_attr(k_ens_persistent<T, USE_TMA>, bytes, configured);
+  cudaError_t e = set_smem_attr(k_ens_persistent<T, USE_TMA, VIEWS>, bytes, configured);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<T, USE_TMA>, 256, bytes)) !=
-      cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<T, USE_TMA, VIEWS>, 256,
+                                                         bytes)) != cudaSuccess)
     return e;
   long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
   if (grid > sc.total) grid = sc.total;
   if (grid < 1) return cudaSuccess;
-  k_ens_persistent<T, USE_TMA><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done, err,
-                                                                   limit_ns, inject, views_or_empty(views),
-                                                                   views ? 1 : 0);
+  k_ens_persistent<T, USE_TMA, VIEWS><<<(unsigned)grid, 256, bytes, st>>>(boxes, dyn, coef, sc, kstart, ticket, done,
+                                                                          err, limit_ns, inject,
+                                                                          views_or_empty(views));
   return cudaGetLastError();
 }
 
@@ -1161,36 +1166,56 @@ cudaError_t launch_ens_persistent(const EnsBox<T>* boxes, const EnsDyn* dyn, con
                                   const int* kstart, unsigned long long* ticket, unsigned* done, int* err,
                                   long long limit_ns, int inject, int use_tma, const EnsViews<T>* views,
                                   cudaStream_t st) {
-  return use_tma ? launch_ens_persistent_t<T, true>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns, inject,
-                                                    views, st)
-                 : launch_ens_persistent_t<T, false>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
-                                                     inject, views, st);
+  if (use_tma)
+    return views ? launch_ens_persistent_t<T, true, true>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
+                                                          inject, views, st)
+                 : launch_ens_persistent_t<T, true, false>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
+                                                           inject, views, st);
+  return views ? launch_ens_persistent_t<T, false, true>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
+                                                         inject, views, st)
+               : launch_ens_persistent_t<T, false, false>(boxes, dyn, coef, sc, kstart, ticket, done, err, limit_ns,
+                                                          inject, views, st);
+}
+
+template <typename T, bool VIEWS>
+cudaError_t launch_ens_measure_t(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const Coef<T>* coef,
+                                 const int* list, const long long* pre, int nlist, long long items, int k,
+                                 const EnsViews<T>* views, cudaStream_t st) {
+  const size_t bytes = sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, true, false>);
+  static bool configured[64] = {};
+  cudaError_t e = set_smem_attr(k_ens_measure<T, VIEWS>, bytes, configured);
+  if (e != cudaSuccess) return e;
+  if (items <= 0) return cudaSuccess;
+  k_ens_measure<T, VIEWS><<<(unsigned)items, 256, bytes, st>>>(boxes, det, dyn, coef, list, pre, nlist, k,
+                                                               views_or_empty(views));
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ens_measure(const EnsBox<T>* boxes, const EnsDet* det, const EnsDyn* dyn, const Coef<T>* coef,
                                const int* list, const long long* pre, int nlist, long long items, int k,
                                const EnsViews<T>* views, cudaStream_t st) {
-  const size_t bytes = sizeof(Smem<T, TileShape<T>::TX, TileShape<T>::TY, true, false>);
+  return views ? launch_ens_measure_t<T, true>(boxes, det, dyn, coef, list, pre, nlist, items, k, views, st)
+               : launch_ens_measure_t<T, false>(boxes, det, dyn, coef, list, pre, nlist, items, k, views, st);
+}
+
+template <typename T, bool VIEWS>
+cudaError_t launch_ens_step_t(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
+                              int k, long long items, const EnsViews<T>* views, cudaStream_t st) {
+  const size_t bytes = ens_smem_bytes<T>();
   static bool configured[64] = {};
-  cudaError_t e = set_smem_attr(k_ens_measure<T>, bytes, configured);
+  cudaError_t e = set_smem_attr(k_ens_step<T, VIEWS>, bytes, configured);
   if (e != cudaSuccess) return e;
   if (items <= 0) return cudaSuccess;
-  k_ens_measure<T><<<(unsigned)items, 256, bytes, st>>>(boxes, det, dyn, coef, list, pre, nlist, k,
-                                                        views_or_empty(views), views ? 1 : 0);
+  k_ens_step<T, VIEWS><<<(unsigned)items, 256, bytes, st>>>(boxes, dyn, coef, sc, k, views_or_empty(views));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ens_step(const EnsBox<T>* boxes, const EnsDyn* dyn, const Coef<T>* coef, const EnsSched& sc,
                             int k, long long items, const EnsViews<T>* views, cudaStream_t st) {
-  const size_t bytes = ens_smem_bytes<T>();
-  static bool configured[64] = {};
-  cudaError_t e = set_smem_attr(k_ens_step<T>, bytes, configured);
-  if (e != cudaSuccess) return e;
-  if (items <= 0) return cudaSuccess;
-  k_ens_step<T><<<(unsigned)items, 256, bytes, st>>>(boxes, dyn, coef, sc, k, views_or_empty(views), views ? 1 : 0);
-  return cudaGetLastError();
+  return views ? launch_ens_step_t<T, true>(boxes, dyn, coef, sc, k, items, views, st)
+               : launch_ens_step_t<T, false>(boxes, dyn, coef, sc, k, items, views, st);
 }
 
 cudaError_t launch_ens_advance(EnsDyn* dyn, const int* steps, int nboxes, int de, cudaStream_t st) {
