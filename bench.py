@@ -346,6 +346,12 @@ def ensemble_bench(U, torch, dev):
     for name, mode, graph in modes:
         out[name] = timed(ens, mode, graph, 0)
     out["speedup_vs_unbatched"] = out[tuned]["site_updates_per_s"] / out["unbatched"]["site_updates_per_s"]
+    # the tuned run against the copy bandwidth at the step's 160 algorithmic
+    # bytes per site update (whole run: every launch of the graph counted)
+    hbm, kind = peaks()
+    gbs = out[tuned]["site_updates_per_s"] * BYTES_PER_SITE["fp32"] / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                       "peak_kind": kind, "bytes_per_site": BYTES_PER_SITE["fp32"]}
     # the same runs with detection every 16 steps inside the run (windings,
     # cells, overlap and diagnostic sums of every box, records in each box's
     # ring); batched modes detect all boxes of a run step in one launch per pass
