@@ -224,12 +224,28 @@ __device__ __forceinline__ T ld_mom(const T* p) {
   return *p;
 }
 
+// A field store of the step: streaming (st.global.cs) or plain.
+template <bool STREAM, typename T>
+__device__ __forceinline__ void st_field(T* p, T x) {
+  if (STREAM)
+    __stcs(p, x);
+  else
+    *p = x;
+}
+
 // One tile column (tile (bx, by), planes [z0, z1)) of a step or measuring
 // pass; `bid` indexes the block partial of a measuring pass.
 // HOOKS: the plan's test-hook fields are read (single-lattice kernels, whose
 // plan is a kernel parameter); ensemble kernels, whose plans live in device
 // memory, use the exact slot size and the 2 s limit instead.
-template <typename T, int TX, int TY, int MODE, bool COHERENT, bool HOOKS = true>
+// STREAM: the step's stores (new positions, momenta) are streaming stores,
+// evict-first in L2, which leaves L2 to the position planes that
+// neighbouring tiles re-read as halos.  Measured at 1024^3: the plain step
+// 27.59 against 28.18 ms, DRAM reads +2.0 % instead of +3.0 % over the
+// algorithmic bytes.  The ensemble kernels keep plain stores: with streaming
+// stores their 32-plane work items ran 2 % slower and 64-plane ones no
+// faster.
+template <typename T, int TX, int TY, int MODE, bool COHERENT, bool HOOKS = true, bool STREAM = false>
 __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeView<T>& v, const Coef<T>& c,
                                          const MeasureOut& mo, int bx, int by, int z0, int z1, int bid,
                                          const TmaPlan* tma) {
@@ -510,14 +526,14 @@ __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeV
       if (WRITE) {
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          v.mom[2 * s][gsite] = prn[s];
-          v.mom[2 * s + 1][gsite] = pin_[s];
-          v.pout[2 * s][gsite] = in[s].fr + c.deta * prn[s];
-          v.pout[2 * s + 1][gsite] = in[s].fi + c.deta * pin_[s];
+          st_field<STREAM>(&v.mom[2 * s][gsite], prn[s]);
+          st_field<STREAM>(&v.mom[2 * s + 1][gsite], pin_[s]);
+          st_field<STREAM>(&v.pout[2 * s][gsite], in[s].fr + c.deta * prn[s]);
+          st_field<STREAM>(&v.pout[2 * s + 1][gsite], in[s].fi + c.deta * pin_[s]);
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            v.mom[4 + 3 * s + i][gsite] = En[s][i];
-            v.pout[4 + 3 * s + i][gsite] = in[s].A[i] + c.deta * En[s][i];
+            st_field<STREAM>(&v.mom[4 + 3 * s + i][gsite], En[s][i]);
+            st_field<STREAM>(&v.pout[4 + 3 * s + i][gsite], in[s].A[i] + c.deta * En[s][i]);
           }
         }
       }
@@ -720,7 +736,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz, int band_rows, const
   }
   const int z0 = bzc * lz;
   const int z1 = min(z0 + lz, v.nz);
-  tile_run<T, TX, TY, MODE, false>(smem_raw, v, c, mo, bx, by, z0, z1, lin, &tma);
+  tile_run<T, TX, TY, MODE, false, true, true>(smem_raw, v, c, mo, bx, by, z0, z1, lin, &tma);
 }
 
 template <typename T>
