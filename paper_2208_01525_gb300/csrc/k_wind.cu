@@ -27,9 +27,12 @@
 // integers: their four-term sums are exact, and each winding is converted
 // to an integer once.
 //
-// CTA: 8 warps x 32 lanes on a (32 x 8)-site window that advances by 31 in x
-// and 7 in y, so that lane 31 and warp 7 hold the right column and the top
-// row of the tile's halo.  Each thread computes alpha of its own site once
+// CTA: 12 warps x 32 lanes on a (32 x 12)-site window that advances by 31 in
+// x and 11 in y, so that lane 31 and warp 11 hold the right column and the
+// top row of the tile's halo.  The halo threads compute edges they do not
+// emit: 12 rows waste 1/12 of them against 1/8 for 8 rows (measured at
+// 1024^3, FP32: the standalone string detection 16.02 against 16.25 ms; 16
+// rows, which fit one CTA per SM, took 17.0 ms).  Each thread computes alpha of its own site once
 // per sector and plane, and the branch integers of its own three edges.
 // alpha of x+1 comes by warp shuffle, alpha of the row above from a
 // three-plane shared ring (one barrier per plane), alpha of z+1 from the
@@ -50,12 +53,12 @@ namespace u1u1 {
 namespace {
 
 constexpr int WW = 32;        // window width (lanes)
-constexpr int WH = 8;         // window height (warps)
+constexpr int WH = 12;        // window height (warps)
 constexpr int WOX = WW - 1;   // output columns per tile
 constexpr int WOY = WH - 1;   // output rows per tile
 constexpr int WNT = WW * WH;  // threads per CTA
 constexpr int WIND_MIN_LZ = 32;
-constexpr int WIND_TARGET_CTAS = 152 * 3 * 16;  // 3 resident CTAs per SM, about 16 waves
+constexpr int WIND_TARGET_CTAS = 152 * 2 * 16;  // 2 resident CTAs per SM, about 16 waves
 
 // What the row below needs of a site: alpha of each plane (three-plane
 // ring), and, one plane later, the branch integers of edges 0 and 2 with
@@ -255,7 +258,7 @@ __device__ __forceinline__ void windings_tile(const PosView<T>& v, T dx, int lz,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 1 : 2)
 k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_t* windings) {
   BlockPartial* p = part + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   windings_tile<T>(v, dx, lz, blockIdx.x, blockIdx.y, blockIdx.z, p, faces, windings);
@@ -266,7 +269,7 @@ k_windings(PosView<T> v, T dx, int lz, BlockPartial* part, uint8_t* faces, int8_
 // partial slots as a single lattice's pass, on each box's input positions
 // of step k.
 template <typename T>
-__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(WNT, sizeof(T) == 8 ? 1 : 2)
 k_ens_windings(const EnsBox<T>* __restrict__ boxes, const EnsDet* __restrict__ det, const EnsDyn* __restrict__ dyn,
                const int* __restrict__ list, const long long* __restrict__ pre, int nlist, int k) {
   const long long r = blockIdx.x;
