@@ -242,9 +242,10 @@ __device__ __forceinline__ void st_field(T* p, T x) {
 // evict-first in L2, which leaves L2 to the position planes that
 // neighbouring tiles re-read as halos.  Measured at 1024^3: the plain step
 // 27.59 against 28.18 ms, DRAM reads +2.0 % instead of +3.0 % over the
-// algorithmic bytes.  The ensemble kernels keep plain stores: with streaming
-// stores their 32-plane work items ran 2 % slower and 64-plane ones no
-// faster.
+// algorithmic bytes.  The measuring step keeps plain stores (35.5 against
+// 35.2 ms per launch with streaming stores), and so do the ensemble kernels:
+// with streaming stores their 32-plane work items ran 2 % slower and
+// 64-plane ones no faster.
 template <typename T, int TX, int TY, int MODE, bool COHERENT, bool HOOKS = true, bool STREAM = false>
 __device__ __forceinline__ void tile_run(unsigned char* smem_raw, const LatticeView<T>& v, const Coef<T>& c,
                                          const MeasureOut& mo, int bx, int by, int z0, int z1, int bid,
@@ -736,7 +737,7 @@ k_tiled(LatticeView<T> v, Coef<T> c, MeasureOut mo, int lz, int band_rows, const
   }
   const int z0 = bzc * lz;
   const int z1 = min(z0 + lz, v.nz);
-  tile_run<T, TX, TY, MODE, false, true, true>(smem_raw, v, c, mo, bx, by, z0, z1, lin, &tma);
+  tile_run<T, TX, TY, MODE, false, true, MODE == MODE_WRITE>(smem_raw, v, c, mo, bx, by, z0, z1, lin, &tma);
 }
 
 template <typename T>
