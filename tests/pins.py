@@ -412,6 +412,40 @@ def pin_winding_topology():
         assert int(C[s].astype(np.int64).sum()) == 2 * int(np.abs(W[s]).sum())
 
 
+def pin_branch_cut_flags():
+    """Branch-cut flags of the windings (Sec. III.A, with the reading that an
+    edge is flagged when its phase chi is within 1e-4 of pi, or when a field
+    at either end is exactly zero).  Zero links, phi_q = 1 and phi_p = 1
+    except at three sites: one of phase pi - 5e-5, one of phase pi - 1e-3 and
+    one of zero field.  Every edge touching the first or the third site has
+    pi - |chi| = 5e-5 or a zero product, so exactly the twelve plaquettes with
+    either site as a corner are flagged; the second site's edges sit 1e-3
+    from the cut and flag nothing.  The phase field is single-valued, so
+    every winding is zero."""
+    p = O.Params(6, 6, 6, m=0.0)
+    st = np.zeros((O.NFIELDS, 6, 6, 6))
+    st[0] = 1.0
+    st[2] = 1.0
+    near, far, zero = (1, 1, 1), (1, 1, 4), (4, 4, 1)  # (z, y, x)
+    for site, ph in ((near, math.pi - 5e-5), (far, math.pi - 1e-3)):
+        st[0][site], st[1][site] = math.cos(ph), math.sin(ph)
+    st[0][zero] = 0.0
+    W, F = O.windings(p, st)
+    assert not W.any()
+    expect = np.zeros(F.shape[1:], dtype=bool)
+    for k, (i, j) in enumerate(((0, 1), (0, 2), (1, 2))):  # plane k spans directions i < j (0 = x)
+        for corner in (near, zero):
+            for a in (0, 1):
+                for b in (0, 1):
+                    zyx = list(corner)
+                    zyx[2 - i] = (zyx[2 - i] - a) % 6
+                    zyx[2 - j] = (zyx[2 - j] - b) % 6
+                    expect[k][tuple(zyx)] = True
+    assert int(expect.sum()) == 24
+    assert np.array_equal(F[0].astype(bool), expect)
+    assert not F[1].any()
+
+
 def pin_planted_vortices():
     """Four planted straight strings (synth.vortex_map) are found at exactly
     the plaquettes and with the signs the map fixes, once per z-plane, with
@@ -762,4 +796,5 @@ ALL_PINS = [
     pin_kappa_decoupling, pin_winding_topology, pin_planted_vortices, pin_bruteforce_windings, pin_bruteforce_overlap,
     pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic, pin_components,
     pin_segments_planted, pin_unequal_tensions, pin_higher_winding_census, pin_cooling_homogeneous_flow,
+    pin_branch_cut_flags,
 ]

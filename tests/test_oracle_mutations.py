@@ -57,6 +57,27 @@ MUTATIONS = [
     ("self_potential_wrong_sector", "nadd(&acc[D_POT_P], c * 0.25 * p->lambda[0] * rp * rp);",
      "nadd(&acc[D_POT_P], c * 0.25 * p->lambda[1] * rp * rp);"),
     ("cool_step_sign", "st[f_phi(s, c) * V + site] += dt * work", "st[f_phi(s, c) * V + site] -= dt * work"),
+    ("scale_factor_inverted", "pow(eta / p->eta_ref, pm)", "pow(p->eta_ref / eta, pm)"),
+    ("expansion_exponent", "p->m / (1.0 - p->m)", "p->m / (1.0 + p->m)"),
+    ("laplacian_centre_factor", "lap.re += fwd.re + bwd.re - 2.0 * f.re;", "lap.re += fwd.re + bwd.re - 1.0 * f.re;"),
+    ("laplacian_dx_power", "double inv_dx2 = 1.0 / (p->dx * p->dx);", "double inv_dx2 = 1.0 / p->dx;"),
+    ("scalar_damping_denominator", "((1.0 - delta) * pi + p->deta * (lap.im - g * f.im)) / (1.0 + delta);",
+     "((1.0 - delta) * pi + p->deta * (lap.im - g * f.im)) / (1.0 - delta);"),
+    ("gauge_damping_denominator", "((1.0 - omega) * Eold + p->deta * (-curl + 2.0 * e2 * c * J)) / (1.0 + omega);",
+     "((1.0 - omega) * Eold + p->deta * (-curl + 2.0 * e2 * c * J)) / (1.0 - omega);"),
+    ("current_not_over_dx", "double J = t.im / p->dx;", "double J = t.im;"),
+    ("curl_not_over_dx", "curl += (plaq_F(p, st, s, i, j, site) - plaq_F(p, st, s, i, j, xmj)) / p->dx;",
+     "curl += (plaq_F(p, st, s, i, j, site) - plaq_F(p, st, s, i, j, xmj));"),
+    ("phi_drift_sign", "st[f_phi(s, c) * V + site] += p->deta * v;", "st[f_phi(s, c) * V + site] -= p->deta * v;"),
+    ("momentum_not_replaced", "st[f_pi(s, c) * V + site] = v;", "st[f_pi(s, c) * V + site] += 0.0 * v;"),
+    ("gauge_coupling_not_squared", "double e2 = p->e[s] * p->e[s];", "double e2 = p->e[s];"),
+    ("self_coupling_other_sector", "double g = c * (0.5 * p->lambda[s] * r_self",
+     "double g = c * (0.5 * p->lambda[o] * r_self"),
+    ("current_without_coupling_c", "(-curl + 2.0 * e2 * c * J)", "(-curl + 2.0 * e2 * J)"),
+    ("sector_streams_shared", "uint64_t x0 = p->seed ^ ((uint64_t)s << 62);", "uint64_t x0 = p->seed;"),
+    ("cut_threshold", "if (M_PI - fabs(chi) < 1e-4 ||", "if (M_PI - fabs(chi) < 1e-1 ||"),
+    ("cut_zero_field_ignored", "if (M_PI - fabs(chi) < 1e-4 || (t.re == 0.0 && t.im == 0.0)) *near_cut = 1;",
+     "if (M_PI - fabs(chi) < 1e-4) *near_cut = 1;"),
 ]
 
 
