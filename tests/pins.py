@@ -505,6 +505,23 @@ def pin_planted_vortices():
     assert math.isclose(res["xi_p"], math.sqrt(vol / lp), rel_tol=1e-14) and res["xi_q"] == math.inf
     assert res["xi_pq"] == math.inf and math.isclose(res["xi_w"], math.sqrt(vol / lp), rel_tol=1e-14)
     assert res["f_total"] == 0.0 and res["f_p"] == 0.0
+    # eight p strings (the map times itself shifted by nx/4, whose zero lines
+    # sit four cells from the first map's) and the four q strings of the map:
+    # four p strings are bound and four are not, so L_pq = L_p = 4 nz dx,
+    # L_q = 0, f_total = 1/2 (Eq. 34) and f_p = 1 (Eq. 35); 4 nz plaquettes
+    # are pierced in both sectors
+    st = O.new_state(p)
+    vp = vm * np.roll(vm, nx // 4, axis=2)
+    st[0], st[1] = vp.real, vp.imag
+    st[2], st[3] = vm.real, vm.imag
+    W, F = O.windings(p, st)
+    assert not F.any() and int(np.abs(W[0]).sum()) == 8 * nz and int(np.abs(W[1]).sum()) == 4 * nz
+    res = O.strings(p, st, tol=1)
+    L4 = 4 * nz * p.dx
+    assert res["n_pq_plaq"] == 4 * nz and res["n_pq_cell"] == 4 * nz
+    assert res["L_pq"] == L4 and res["L_p"] == L4 and res["L_q"] == 0.0
+    assert res["f_total"] == 0.5 and res["f_p"] == 1.0 and res["xi_q"] == math.inf
+    assert math.isclose(res["xi_w"], math.sqrt(vol / (2 * L4)), rel_tol=1e-14)
 
 
 def pin_bruteforce_windings():
@@ -562,6 +579,63 @@ def pin_velocity_closed_form():
         assert abs(d[k] - p.nsites * want) < 1e-12 * p.nsites * max(abs(want), 1e-3), (k, d[k], p.nsites * want)
     for s, sec in enumerate("pq"):
         assert abs(d["phi_min_" + sec] - r[s]) < 1e-14 and abs(d["phi_max_" + sec] - r[s]) < 1e-14
+    # kappa = 0: every V_int weight of Eq. 37 vanishes, so <v^2> weighted by
+    # V_int is undefined while the L-weighted one keeps its closed form
+    p0 = O.Params(nx, 4, 4, m=0.0, kappa=0.0, lam=(2.0, 1.6))
+    d0 = O.diagnostics(p0, st, 0)
+    num0 = sum(r[s] ** 2 * (v * v * khat2 + 0.5 * p0.deta ** 2
+                            * (khat2 + 0.5 * p0.lam[s] * (r[s] ** 2 - p0.sigma[s] ** 2)) ** 2) for s in range(2))
+    R0 = num0 / (khat2 * (r[0] ** 2 + r[1] ** 2))
+    assert abs(d0["R_l"] - R0) < 1e-11 * R0, (d0["R_l"], R0)
+    assert math.isnan(d0["R_pq"]) and math.isnan(d0["v2_pq"])
+
+
+def pin_homogeneous_energy_expanding():
+    """The lattice energy densities with their a^{2 beta} factors (the action
+    of Sec. II; V of Eq. 4) on a homogeneous state in an expanding background:
+    matter era (a ~ eta^2), beta = 1/2, eta = 2 eta_ref, so a = 4 and
+    c = a^{2 beta} = 4.  Uniform real phi_s = r_s off the vacuum, uniform
+    imaginary momenta pi_s = i u_s, A = 0 and a uniform electric field per
+    sector: no gradient, no current, no curl.  The kicks of Eqs. 17 and 20
+    then give pi_s^+ = ((1 - delta) pi_s^- - deta c g_s r_s) / (1 + delta)
+    with g_s = lambda_s/2 (r_s^2 - sigma_s^2) - kappa (r_o^2 - sigma_o^2),
+    and E^+ = (1 - omega) / (1 + omega) E^-, and every lattice sum is V times
+    the site value: kin_s = (|pi^-|^2 + |pi^+|^2) / 2,
+    el_s = sum_i (E_i^-2 + E_i^+2) / 2 / (2 e_s^2 c), pot = c V(r_p, r_q),
+    grad = mag = 0, L = sum (kin + el) - pot, H = sum (kin + el) + pot."""
+    p = O.Params(4, 4, 4, m=2.0 / 3.0, beta=0.5, eta0=2.0, eta_ref=1.0, kappa=0.3, lam=(2.0, 1.6),
+                 e=(1.0, 0.8), sigma=(1.0, 0.9))
+    cf = O.coeffs(p, 0)
+    c = (p.eta0 / p.eta_ref) ** (2.0 * p.beta * p.m / (1.0 - p.m))
+    assert abs(cf["a"] - 4.0) < 1e-14 and abs(cf["c"] - c) < 1e-14 * c and abs(c - 4.0) < 1e-14
+    delta, omega = cf["delta"], cf["omega"]
+    assert delta > 0.0 and omega > 0.0
+    r, u = (0.8, 1.2), (0.3, -0.2)
+    E = ((0.4, -0.1, 0.25), (-0.3, 0.2, 0.15))
+    st = O.new_state(p)
+    for s in range(2):
+        st[2 * s] = r[s]
+        st[11 + 2 * s] = u[s]
+        for i in range(3):
+            st[14 + 3 * s + i] = E[s][i]
+    d = O.diagnostics(p, st, 0)
+    V = p.nsites
+    rr = [r[s] ** 2 - p.sigma[s] ** 2 for s in range(2)]
+    q = (1.0 - omega) / (1.0 + omega)
+    kin, el = [], []
+    for s in range(2):
+        g = 0.5 * p.lam[s] * rr[s] - p.kappa * rr[1 - s]
+        pr_plus = -p.deta * c * g * r[s] / (1.0 + delta)
+        pi_plus = (1.0 - delta) * u[s] / (1.0 + delta)
+        kin.append(0.5 * (u[s] ** 2 + pr_plus ** 2 + pi_plus ** 2))
+        el.append(sum(x * x for x in E[s]) * (1.0 + q * q) / 2.0 / (2.0 * p.e[s] ** 2 * c))
+    pot = c * (p.lam[0] / 4 * rr[0] ** 2 + p.lam[1] / 4 * rr[1] ** 2 - p.kappa * rr[0] * rr[1])
+    want = dict(kin_p=kin[0], kin_q=kin[1], el_p=el[0], el_q=el[1], pot=pot,
+                lag=kin[0] + kin[1] + el[0] + el[1] - pot, energy=kin[0] + kin[1] + el[0] + el[1] + pot)
+    for k, w in want.items():
+        assert abs(d[k] - V * w) < 1e-12 * V * abs(w), (k, d[k], V * w)
+    for k in ("grad_p", "grad_q", "mag_p", "mag_q"):
+        assert d[k] == 0.0, (k, d[k])
 
 
 def pin_vacuum():
@@ -796,5 +870,5 @@ ALL_PINS = [
     pin_kappa_decoupling, pin_winding_topology, pin_planted_vortices, pin_bruteforce_windings, pin_bruteforce_overlap,
     pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic, pin_components,
     pin_segments_planted, pin_unequal_tensions, pin_higher_winding_census, pin_cooling_homogeneous_flow,
-    pin_branch_cut_flags,
+    pin_branch_cut_flags, pin_homogeneous_energy_expanding,
 ]

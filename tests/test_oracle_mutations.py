@@ -78,6 +78,23 @@ MUTATIONS = [
     ("cut_threshold", "if (M_PI - fabs(chi) < 1e-4 ||", "if (M_PI - fabs(chi) < 1e-1 ||"),
     ("cut_zero_field_ignored", "if (M_PI - fabs(chi) < 1e-4 || (t.re == 0.0 && t.im == 0.0)) *near_cut = 1;",
      "if (M_PI - fabs(chi) < 1e-4) *near_cut = 1;"),
+    ("energy_potential_sign", "+ (kin[1] + grad[1] + el[1] + mag[1]) + pot;",
+     "+ (kin[1] + grad[1] + el[1] + mag[1]) - pot;"),
+    ("energy_magnetic_sign", "double H = (kin[0] + grad[0] + el[0] + mag[0])",
+     "double H = (kin[0] + grad[0] + el[0] - mag[0])"),
+    ("electric_coupling_factor", "double g = 1.0 / (2.0 * p->e[s] * p->e[s] * c);",
+     "double g = 1.0 / (p->e[s] * p->e[s] * c);"),
+    ("electric_without_c", "double g = 1.0 / (2.0 * p->e[s] * p->e[s] * c);",
+     "double g = 1.0 / (2.0 * p->e[s] * p->e[s]);"),
+    ("rl_weight_energy", "nadd(&acc[D_RL_NUM], kt * L);", "nadd(&acc[D_RL_NUM], kt * H);"),
+    ("rpq_den_kinetic", "nadd(&acc[D_RPQ_DEN], gt * vint);", "nadd(&acc[D_RPQ_DEN], kt * vint);"),
+    ("potential_without_c", "double pot = c * V0;", "double pot = V0;"),
+    ("gauss_divergence_forward", "long xm = shift(p, site, i, -1);\n        div +=",
+     "long xm = shift(p, site, i, +1);\n        div +="),
+    ("phi_extremes_squared", "double mod = sqrt(mod2[s]);", "double mod = mod2[s];"),
+    ("charge_sign", "(fr * pi - fi * pr)", "(fi * pr - fr * pi)"),
+    ("gradient_conjugate_link", "cplx fwd = cmul(link_U(p, st, s, i, site), get_phi(p, st, s, xp));\n        cplx d",
+     "cplx fwd = cmul(cconj(link_U(p, st, s, i, site)), get_phi(p, st, s, xp));\n        cplx d"),
 ]
 
 
@@ -98,7 +115,7 @@ def test_mutation_is_caught(name, old, new, tmp_path):
 
 
 # Plausible mistakes in the oracle's host epilogue (oracle/__init__.py: the
-# estimators of Eqs. 31-37 formed from the lattice counts and sums).  Each
+# estimators of Eqs. 31-38 formed from the lattice counts, sums and segments).  Each
 # mutated copy of the module is executed on its own, and its functions stand
 # in for the oracle's while the pins run.
 PY_MUTATIONS = [
@@ -112,6 +129,13 @@ PY_MUTATIONS = [
     ("tension_sigma_not_squared", "mu = 2.0 * math.pi * p.sigma[0] ** 2", "mu = 2.0 * math.pi * p.sigma[0]"),
     ("sector_tension_sigma_not_squared", "_sqrt_ratio(-2.0 * math.pi * p.sigma[k] ** 2 * vol, lag_s)",
      "_sqrt_ratio(-2.0 * math.pi * p.sigma[k] * vol, lag_s)"),
+    ("segment_length_no_minus_one", "L = p.dx * float((sizes[keep] - 1).sum())", "L = p.dx * float(sizes[keep].sum())"),
+    ("segment_threshold_inclusive", "keep = sizes > min_cells", "keep = sizes >= min_cells"),
+    ("sector_lag_potential_sign", "- s[\"pot_\" + sec])", "+ s[\"pot_\" + sec])"),
+    ("f_p_over_total", "f_p=(L_pq / L_p)", "f_p=(L_pq / tot)"),
+    ("v2_pq_from_l_weights", "(\"pq\", \"rpq_num\", \"rpq_den\")", "(\"pq\", \"rl_num\", \"rl_den\")"),
+    ("L_pq_without_dx", "L_pq = dx * n_pq_cell", "L_pq = n_pq_cell"),
+    ("pq_plaquettes_or", "both = (W[0] != 0) & (W[1] != 0)", "both = (W[0] != 0) | (W[1] != 0)"),
 ]
 
 
@@ -128,7 +152,7 @@ def test_epilogue_mutation_is_caught(name, old, new, monkeypatch):
     monkeypatch.setitem(sys.modules, "oracle_mutant", mod)  # dataclasses look their module up here
     exec(compile(src.replace(old, new), path, "exec"), mod.__dict__)  # noqa: S102 - test of a planted mistake
     mod._lib = O.lib()  # the same compiled oracle
-    for fn in ("strings", "diagnostics"):
+    for fn in ("strings", "diagnostics", "segments"):
         monkeypatch.setattr(O, fn, getattr(mod, fn))
     caught = []
     for pin in pins.ALL_PINS:
