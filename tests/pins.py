@@ -412,6 +412,52 @@ def pin_winding_topology():
         assert int(C[s].astype(np.int64).sum()) == 2 * int(np.abs(W[s]).sum())
 
 
+def pin_cooling_ignores_background_and_momenta():
+    """The cooling flow (Eqs. 27-30) is a flow in flow time at a = 1 with no
+    damping and no momenta: cooling a rough state gives bit-identical
+    positions whatever the run's era, beta, initial time and time step, and
+    whatever its momenta hold."""
+    base = dict(lam=(2.0, 1.6), e=(1.0, 0.8), sigma=(1.0, 0.9), kappa=0.4)
+    pf = O.Params(6, 6, 6, m=0.0, **base)
+    pe = O.Params(6, 6, 6, m=2.0 / 3.0, beta=0.5, eta0=3.0, eta_ref=1.5, deta=0.05, **base)
+    st = synth.random_state(pf.shape, seed=7)
+    still = st.copy()
+    still[10:] = 0.0
+    outs = [O.cool(pf, still.copy(), 0.02, 12), O.cool(pe, still.copy(), 0.02, 12), O.cool(pf, st.copy(), 0.02, 12)]
+    assert not np.array_equal(outs[0][:10], still[:10])
+    for o in outs[1:]:
+        assert np.array_equal(o[:10], outs[0][:10])
+
+
+def pin_double_winding_plaquette():
+    """A plaquette of winding -2 (Sec. III.A definition; the census of
+    |W| >= 2 plaquettes and of cells of value >= 4).  phi = 1 in both
+    sectors and zero links, except the x-link at x0 and the y-link at
+    x0 + x of sector p, each of angle dx A = -2 pi + 0.1.  Each of these edges
+    has chi = -0.1 and branch integer k = rint((0 - dx A) / 2 pi) = 1, so the
+    (x, y) plaquette at x0, which holds both, has W = -(1 + 1) = -2, and each
+    of the three other plaquettes on either link has |W| = 1: one plaquette
+    of |W| = 2, six of |W| = 1, no flag.  The two cells on either side of the
+    W = -2 face also hold one |W| = 1 face of each link: value 4."""
+    p = O.Params(6, 6, 6, m=0.0)
+    st = O.new_state(p)
+    st[0] = 1.0
+    st[2] = 1.0
+    x0 = (2, 2, 2)  # (z, y, x)
+    xx = (2, 2, 3)
+    theta = -TWO_PI + 0.1
+    st[4][x0] = theta / p.dx
+    st[5][xx] = theta / p.dx
+    W, F = O.windings(p, st)
+    assert not F.any() and not W[1].any()
+    assert W[0, 0][x0] == -2
+    aw = np.abs(W[0].astype(np.int64))
+    assert int((aw == 2).sum()) == 1 and int((aw == 1).sum()) == 6 and int(aw.max()) == 2
+    res = O.strings(p, st, tol=1)
+    assert res["n_w2_p"] == 1 and res["n_w2_q"] == 0 and res["max_abs_w"] == 2
+    assert res["n_cells_ge4_p"] == 2 and res["n_cells_ge4_q"] == 0 and res["n_flagged"] == 0
+
+
 def pin_branch_cut_flags():
     """Branch-cut flags of the windings (Sec. III.A, with the reading that an
     edge is flagged when its phase chi is within 1e-4 of pi, or when a field
@@ -522,6 +568,16 @@ def pin_planted_vortices():
     assert res["L_pq"] == L4 and res["L_p"] == L4 and res["L_q"] == 0.0
     assert res["f_total"] == 0.5 and res["f_p"] == 1.0 and res["xi_q"] == math.inf
     assert math.isclose(res["xi_w"], math.sqrt(vol / (2 * L4)), rel_tol=1e-14)
+    # the same eight p strings against the four q strings of the map shifted
+    # by two cells: within two cells every p string has a q string, and each
+    # q string has two p strings, so the p-anchored count is 8 nz cells and
+    # the q-anchored one 4 nz (Sec. III.B); within one cell neither has any
+    vq = np.roll(vm, 2, axis=2)
+    st[2], st[3] = vq.real, vq.imag
+    res2 = O.strings(p, st, tol=2)
+    assert res2["n_pq_cell"] == 8 * nz and res2["n_pq_cell_q"] == 4 * nz
+    res1 = O.strings(p, st, tol=1)
+    assert res1["n_pq_cell"] == 0 and res1["n_pq_cell_q"] == 0
 
 
 def pin_bruteforce_windings():
@@ -870,5 +926,6 @@ ALL_PINS = [
     pin_kappa_decoupling, pin_winding_topology, pin_planted_vortices, pin_bruteforce_windings, pin_bruteforce_overlap,
     pin_velocity_closed_form, pin_vacuum, pin_string_tension, pin_random_phase_ic, pin_components,
     pin_segments_planted, pin_unequal_tensions, pin_higher_winding_census, pin_cooling_homogeneous_flow,
-    pin_branch_cut_flags, pin_homogeneous_energy_expanding,
+    pin_branch_cut_flags, pin_homogeneous_energy_expanding, pin_cooling_ignores_background_and_momenta,
+    pin_double_winding_plaquette,
 ]

@@ -95,7 +95,18 @@ MUTATIONS = [
     ("charge_sign", "(fr * pi - fi * pr)", "(fi * pr - fr * pi)"),
     ("gradient_conjugate_link", "cplx fwd = cmul(link_U(p, st, s, i, site), get_phi(p, st, s, xp));\n        cplx d",
      "cplx fwd = cmul(cconj(link_U(p, st, s, i, site)), get_phi(p, st, s, xp));\n        cplx d"),
+    ("cool_keeps_expansion", "  q.m = 0.0;\n", "  q.m = p->m;\n"),
+    ("cool_deta_not_unit", "  q.deta = 1.0;\n", "  q.deta = p->deta;\n"),
+    ("cool_keeps_momenta", "    memset(tmp + 10 * V, 0, sizeof(double) * 10 * (size_t)V);\n", "\n"),
+    ("cool_links_not_updated", "          st[f_A(s, i) * V + site] += dt * work[4 * V + (3 * s + i) * V + site];",
+     "          st[f_A(s, i) * V + site] += 0.0 * work[4 * V + (3 * s + i) * V + site];"),
+    ("component_label_neighbour", "              label[nb] = start;", "              label[nb] = c;"),
+    ("overlap_anchor_zero_skipped", "        if (anchor[sidx(p, x, y, z)] == 0) continue;",
+     "        if (anchor[sidx(p, x, y, z)] > 1) continue;"),
 ]
+# Not listed: keeping the run's beta in the cooling flow (q.beta = p->beta) is
+# an equivalent change, since the flow also sets m = 0, so a = 1 and delta = 0
+# whatever beta is.
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
@@ -136,6 +147,10 @@ PY_MUTATIONS = [
     ("v2_pq_from_l_weights", "(\"pq\", \"rpq_num\", \"rpq_den\")", "(\"pq\", \"rl_num\", \"rl_den\")"),
     ("L_pq_without_dx", "L_pq = dx * n_pq_cell", "L_pq = n_pq_cell"),
     ("pq_plaquettes_or", "both = (W[0] != 0) & (W[1] != 0)", "both = (W[0] != 0) | (W[1] != 0)"),
+    ("census_w2_strict", "n_w2_p=int((absW[0] >= 2).sum())", "n_w2_p=int((absW[0] > 2).sum())"),
+    ("census_cells_strict", "n_cells_ge4_p=int((C[0] >= 4).sum())", "n_cells_ge4_p=int((C[0] > 4).sum())"),
+    ("max_w_signed", "max_abs_w=int(absW.max())", "max_abs_w=int(W.max())"),
+    ("overlap_q_anchor_same", "n_pq_cell_q = overlap(p, C[1], C[0], tol)", "n_pq_cell_q = overlap(p, C[0], C[1], tol)"),
 ]
 
 
