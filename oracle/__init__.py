@@ -204,14 +204,14 @@ def init(p: Params) -> np.ndarray:
     return st
 
 
-def _work(p: Params) -> np.ndarray:
+def _scratch(p: Params) -> np.ndarray:
     return np.zeros((10,) + p.shape, dtype=np.float64)
 
 
 def step(p: Params, st: np.ndarray, n0: int, nsteps: int = 1) -> np.ndarray:
     """Advance st (in place) by nsteps leapfrog steps starting at step index n0."""
     assert st.shape == (NFIELDS,) + p.shape
-    lib().orc_step(ctypes.byref(p.c()), _dptr(st), int(n0), int(nsteps), _dptr(_work(p)))
+    lib().orc_step(ctypes.byref(p.c()), _dptr(st), int(n0), int(nsteps), _dptr(_scratch(p)))
     return st
 
 
@@ -226,7 +226,7 @@ def kicks(p: Params, st: np.ndarray, n: int):
 
 def cool(p: Params, st: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
     """Diffusive cooling flow of Eqs. 27-30 (forward Euler, in place)."""
-    lib().orc_cool(ctypes.byref(p.c()), _dptr(st), float(dt), int(nsteps), _dptr(_work(p)))
+    lib().orc_cool(ctypes.byref(p.c()), _dptr(st), float(dt), int(nsteps), _dptr(_scratch(p)))
     return st
 
 
@@ -292,7 +292,7 @@ def segments(p: Params, st: np.ndarray, tol: int = 1, min_cells: int = 41) -> di
 
 def diagnostic_sums(p: Params, st: np.ndarray, n: int) -> dict:
     out = np.zeros(len(DIAG_NAMES))
-    lib().orc_diagnostics(ctypes.byref(p.c()), _dptr(st), int(n), _dptr(out), _dptr(_work(p)))
+    lib().orc_diagnostics(ctypes.byref(p.c()), _dptr(st), int(n), _dptr(out), _dptr(_scratch(p)))
     return dict(zip(DIAG_NAMES, out.tolist()))
 
 
