@@ -25,6 +25,7 @@ def test_scaling_slopes_from_records():
         d.update(xi_l=0.19 * eta, xi_l_p=0.31 * eta, xi_l_q=0.29 * eta)
         recs.append((s, d))
     sl = A.scaling_slopes(recs, 12.0, 28.0)
-    for k, v in (("xi_p", 0.3), ("xi_q", 0.28), ("xi_pq", 2.0), ("xi_w", 0.2), ("xi_l", 0.19)):
+    for k, v in (("xi_p", 0.3), ("xi_q", 0.28), ("xi_pq", 2.0), ("xi_w", 0.2), ("xi_l", 0.19),
+                 ("xi_l_p", 0.31), ("xi_l_q", 0.29)):
         assert math.isclose(sl[k], v, rel_tol=1e-12), k
     assert math.isnan(A.slope([1.0], [2.0], 0, 5)[0])
