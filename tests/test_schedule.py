@@ -33,6 +33,44 @@ def test_growth_beta_reproduces_table3():
         assert abs((t["eta_end"] / row["eta_tr"]) ** pm / row["r_s_max"] - 1) < 0.011
 
 
+def test_schedule_phases_follow_table3():
+    """Every row of Table 3 (golden file): cooling from eta = -10 to 1 in steps
+    of 1/30; damping from eta = 1 to 5 at constant comoving width (beta = 0)
+    with the row's m_damp; then, for physical runs, core growth with the row's
+    beta_growth to eta_tr and beta = 1 to the end with a = 1 at the end, and
+    for constant-width runs beta = 0 to the end."""
+    t = table3()
+    de = 0.1
+    base = U.Params.cube(16, deta=de)
+    cool, damp = t["cooling"], t["damping"]
+    for row in t["rows"]:
+        era = "radiation" if row["m"] == 0.5 else "matter"
+        physical = row["beta"] == 1.0
+        ph = S.paper_schedule(base, era, physical=physical, eta_end=t["eta_end"],
+                              eta_tr=row["eta_tr"] if physical else 343.0)
+        assert ph[0].kind == "cool" and abs(ph[0].dt - cool["deta"]) < 1e-15
+        assert ph[0].nsteps == round((cool["eta_end"] - cool["eta_start"]) / cool["deta"])
+        d = ph[1]
+        assert d.kind == "leapfrog" and d.params.m == row["m_damp"] and d.params.beta == damp["beta"]
+        assert d.params.eta0 == damp["eta_start"] and d.nsteps == round((damp["eta_end"] - damp["eta_start"]) / de)
+        if physical:
+            g, f = ph[2], ph[3]
+            assert len(ph) == 4 and g.params.m == row["m"] and f.params.m == row["m"]
+            # r_max from continuity at eta_tr, (eta_end / eta_tr)^{m/(1-m)}, is
+            # within 1.1 % of the printed r_s_max, so beta_growth is within 1 %
+            pm = row["m"] / (1 - row["m"])
+            want = S.growth_beta(row["m"], (t["eta_end"] / row["eta_tr"]) ** pm, damp["eta_end"], row["eta_tr"])
+            assert g.params.beta == want
+            assert abs(g.params.beta - row["beta_growth"]) < 1e-2 * abs(row["beta_growth"])
+            assert g.params.eta0 == damp["eta_end"] and g.nsteps == round((row["eta_tr"] - damp["eta_end"]) / de)
+            assert f.params.beta == 1.0 and f.params.eta0 == row["eta_tr"] and f.params.eta_ref == t["eta_end"]
+            assert f.nsteps == round((t["eta_end"] - row["eta_tr"]) / de)
+        else:
+            f = ph[2]
+            assert len(ph) == 3 and f.params.m == row["m"] and f.params.beta == row["beta"] == 0.0
+            assert f.params.eta0 == damp["eta_end"] and f.nsteps == round((t["eta_end"] - damp["eta_end"]) / de)
+
+
 def test_schedule_phases_are_continuous():
     base = U.Params.cube(16, deta=0.1)
     ph = S.paper_schedule(base, "matter", physical=True, eta_end=20.0, eta_tr=12.0)
